@@ -1,0 +1,391 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-derives the oracle's formulas; each compares the oracle
+with a library routine, a closed form, an invariant or brute force.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import aplicur_oracle as O
+from oracle import rng as orng
+from paper_2604_05065_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand(m, n, seed):
+    return np.random.default_rng(seed).standard_normal((m, n))
+
+
+# ---------------------------------------------------------------- generator -----------
+
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            seed, *outs = map(int, line.split())
+            assert orng.splitmix64_sequence(seed, 3) == outs
+
+
+def test_vectorised_mix_matches_scalar():
+    idx = np.arange(50, dtype=np.uint64)
+    vec = orng._stream_state_np(99, 2, idx)
+    assert [int(v) for v in vec] == [orng.stream_state(99, 2, int(i)) for i in idx]
+
+
+def test_gaussian_w_statistics():
+    W = orng.gaussian_w(7, 4000, 10)
+    assert W.shape == (4000, 10)
+    assert abs(W.mean()) < 0.02 and abs(W.var() - 1.0) < 0.03
+    # fourth moment of N(0,1) is 3
+    assert abs(np.mean(W ** 4) - 3.0) < 0.15
+
+
+# ---------------------------------------------------------------- sketch --------------
+
+@pytest.mark.parametrize("s,xi", [(22, 8), (5, 5), (110, 8), (3, 1)])
+def test_sparse_sign_structure(s, xi):
+    rows, signs = orng.sparse_sign(11, s, 500, xi)
+    assert rows.shape == (500, xi)
+    assert rows.min() >= 0 and rows.max() < s
+    for i in range(500):
+        assert len(set(rows[i].tolist())) == xi
+    assert set(np.unique(signs).tolist()) <= {-1, 1}
+    S = O.dense_S(rows, signs, s)
+    nnz = np.count_nonzero(S, axis=0)
+    assert np.all(nnz == xi)
+    assert np.allclose(np.abs(S[S != 0]), 1.0 / math.sqrt(xi), rtol=0, atol=0)
+
+
+def test_sketch_equals_dense_S_product():
+    A = _rand(300, 40, 1)
+    rows, signs = orng.sparse_sign(3, 22, 300, 8)
+    Y = O.apply_sketch(A, rows, signs, 22)
+    S = O.dense_S(rows, signs, 22)
+    assert np.allclose(Y, S @ A, rtol=1e-13, atol=1e-13)
+
+
+def test_sketch_sparse_and_dense_bitwise_equal():
+    p = wl.small_sparse(400, 60, wl.BASE_SEED + 40, nnz_per_col=4)
+    rows, signs = orng.sparse_sign(5, 11, p.m, 8)
+    Ys = O.apply_sketch(p.to_scipy(), rows, signs, 11)
+    Yd = O.apply_sketch(p.to_dense64(), rows, signs, 11)
+    assert np.array_equal(Ys, Yd)
+
+
+def test_sketch_is_norm_preserving_in_expectation():
+    x = np.random.default_rng(2).standard_normal((200, 1))
+    vals = []
+    for seed in range(300):
+        rows, signs = orng.sparse_sign(seed, 11, 200, 8)
+        vals.append(float(np.sum(O.apply_sketch(x, rows, signs, 11) ** 2)))
+    assert abs(np.mean(vals) / float(np.sum(x * x)) - 1.0) < 0.05
+
+
+def test_sketch_rows_is_exact_ceiling():
+    for b in range(1, 400):
+        assert O.sketch_rows(b) == math.ceil(11 * b / 10)
+    assert O.sketch_rows(20) == 22 and O.sketch_rows(100) == 110 and O.sketch_rows(250) == 275
+
+
+# ---------------------------------------------------------------- LUPP ----------------
+
+def _lapack_perm(X):
+    _, piv = sla.lu_factor(X, check_finite=False)
+    perm = np.arange(X.shape[0])
+    for i, p in enumerate(piv):
+        perm[[i, p]] = perm[[p, i]]
+    return perm
+
+
+@pytest.mark.parametrize("shape,k", [((50, 10), 10), ((200, 30), 25), ((30, 30), 30),
+                                     ((1000, 7), 7)])
+def test_lupp_matches_lapack_getrf(shape, k):
+    X = _rand(*shape, seed=shape[0] + k)
+    res = O.lupp_pivots(X, k)
+    assert res.nz == k
+    assert np.array_equal(res.piv, _lapack_perm(X)[:k])
+
+
+def test_lupp_ties_follow_lapack():
+    X = np.array([[1.0, 2.0], [-1.0, 1.0], [1.0, 5.0], [0.5, -4.0]])
+    res = O.lupp_pivots(X, 2)
+    assert np.array_equal(res.piv, _lapack_perm(X)[:2])
+    assert res.piv[0] == 0
+
+
+def test_lupp_zero_pivot_stops():
+    X = np.zeros((6, 3))
+    X[2, 0] = 1.0
+    res = O.lupp_pivots(X, 3)
+    assert res.nz == 1 and res.piv.tolist() == [2]
+
+
+# ---------------------------------------------------------------- CUR -----------------
+
+def _cur_state(A, b, steps, seed=4):
+    m, n = A.shape
+    s = O.sketch_rows(b)
+    rows, signs = orng.sparse_sign(seed, s, m, O.sketch_xi(s))
+    Y = O.apply_sketch(A, rows, signs, s)
+    I = np.zeros(0, np.int64)
+    J = np.zeros(0, np.int64)
+    core = None
+    E = Y.copy()
+    for _ in range(steps):
+        Ip, Jp, _ = O.augment_cur(A, I, J, E, core, b)
+        I = np.concatenate([I, Ip])
+        J = np.concatenate([J, Jp])
+        core = O.Core(A, I, J)
+        E = O.sketched_residual(A, Y, I, J, core)
+    return Y, I, J, core, E
+
+
+def test_cur_cross_interpolation():
+    p = wl.small_dense(120, 40, 777, decay=4.0)
+    A = p.dense
+    Y, I, J, core, E = _cur_state(A, 5, 3)
+    assert len(I) == len(J) == 15 and len(set(I)) == 15 and len(set(J)) == 15
+    CUR = A[:, J] @ core.solve(A[I, :])
+    scale = np.abs(A).max()
+    assert np.allclose(CUR[I, :], A[I, :], atol=1e-10 * scale)
+    assert np.allclose(CUR[:, J], A[:, J], atol=1e-10 * scale)
+    # the sketched residual vanishes on the selected columns and equals S (A - CUR)
+    assert np.abs(E[:, J]).max() < 1e-10 * np.abs(Y).max()
+    s = O.sketch_rows(5)
+    rows, signs = orng.sparse_sign(4, s, A.shape[0], O.sketch_xi(s))
+    S = O.dense_S(rows, signs, s)
+    assert np.allclose(E, S @ (A - CUR), atol=1e-10 * np.abs(Y).max())
+
+
+def test_cur_column_residual_vanishes_on_selected_rows():
+    p = wl.small_dense(100, 30, 778, decay=3.0)
+    A = p.dense
+    Y, I, J, core, E = _cur_state(A, 4, 2)
+    Er = E.copy()
+    Er[:, J] = 0
+    Jp = O.lupp_pivots(Er.T, 4).piv
+    Ecol = A[:, Jp] - A[:, J] @ core.solve(A[np.ix_(I, Jp)])
+    assert np.abs(Ecol[I, :]).max() < 1e-11 * np.abs(A).max()
+
+
+def test_exact_low_rank_terminates_with_zero_residual():
+    p = wl.small_dense(90, 30, 779, rank=12, decay=2.0, mu=1e-6, sketch_dim=4)
+    res = O.aplicur(p.dense, p.b, p.mu, 4, O.Options(seed=3), tol=1e-9)
+    assert len(res.I) == 12
+    assert res.rank_steps[-1]["rho"] < 1e-9
+    assert res.converged
+
+
+def test_norm_estimate_bounds_two_norm():
+    E = _rand(30, 200, 12) * np.logspace(0, -3, 200)
+    W = orng.gaussian_w(1, 200, 10)
+    rho = O.norm_estimate(E, W)
+    assert rho >= np.linalg.norm(E, 2)
+    # ||E w|| <= ||E||_2 ||w||: the estimate is at most 10 sqrt(2/pi) ||E||_2 max ||w_i||
+    assert rho <= O.NORMEST_FACTOR * np.linalg.norm(E, 2) * np.linalg.norm(W, axis=0).max()
+
+
+# ---------------------------------------------------------------- augmentQR -----------
+
+def test_augment_qr_matches_householder():
+    X = _rand(80, 24, 21)
+    Q, T = O.augment_qr(None, None, X[:, :8])
+    Q, T = O.augment_qr(Q, T, X[:, 8:16])
+    Q, T = O.augment_qr(Q, T, X[:, 16:])
+    assert np.allclose(Q.T @ Q, np.eye(24), atol=1e-13)
+    assert np.allclose(np.triu(T), T)
+    assert np.allclose(Q @ T, X, atol=1e-12)
+    Qh, Rh = np.linalg.qr(X)
+    sg = np.sign(np.diag(Rh))
+    assert np.allclose(Q, Qh * sg, atol=1e-11)
+    assert np.allclose(T, Rh * sg[:, None], atol=1e-11)
+
+
+# ---------------------------------------------------------------- preconditioner ------
+
+def _cur_preconditioner(A, b, steps, delta):
+    Y, I, J, core, E = _cur_state(A, b, steps)
+    Q, T = None, None
+    for k in range(steps):
+        Q, T = O.augment_qr(Q, T, A[I[k * b:(k + 1) * b], :].T)
+    P = O.build_preconditioner(A[:, J], core, Q, T, delta)
+    return P, I, J, core
+
+
+def test_preconditioner_exact_spectrum_on_cur_approximation():
+    """Theorem (condition number bound), proof: the regularised CUR approximation times
+    P^{-1} has singular values sighat (ell times) and delta (n - ell times)."""
+    p = wl.small_dense(150, 40, 780, decay=5.0)
+    A = p.dense
+    delta = 1e-2
+    P, I, J, core = _cur_preconditioner(A, 5, 3, delta)
+    CUR = A[:, J] @ core.solve(A[I, :])
+    n = A.shape[1]
+    Pinv = np.column_stack([P.apply_inv(e) for e in np.eye(n)])
+    sv = np.linalg.svd(np.vstack([CUR, delta * np.eye(n)]) @ Pinv, compute_uv=False)
+    ell = P.ell
+    assert ell == 15
+    assert np.allclose(sv[:ell], P.sighat, rtol=1e-9)
+    assert np.allclose(sv[ell:], delta, rtol=1e-9)
+    # ||P^{-1}|| <= 1 and P P^{-1} = I
+    assert np.linalg.norm(Pinv, 2) <= 1 + 1e-12
+    PP = np.column_stack([P.apply(P.apply_inv(e)) for e in np.eye(n)])
+    assert np.allclose(PP, np.eye(n), atol=1e-12)
+    # the CUR singular values are those of the CUR approximation itself
+    assert np.allclose(P.sig, np.linalg.svd(CUR, compute_uv=False)[:ell], rtol=1e-8)
+
+
+def test_optimal_preconditioner_condition_number():
+    """Section 3.1: with Vhat = V_ell and target level sqrt(sigma_{ell+1}^2 + mu^2) the
+    condition number drops to sqrt((sigma_{ell+1}^2+mu^2)/(sigma_n^2+mu^2))."""
+    p = wl.small_dense(100, 30, 781, decay=6.0)
+    A = p.dense
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    ell, delta = 8, 1e-3
+    Lam = np.sqrt(s[:ell] ** 2 + delta ** 2)
+    sighat = math.sqrt(s[ell] ** 2 + delta ** 2)
+    P = O.Preconditioner(Vt[:ell].T, s[:ell], Lam, sighat, sighat / Lam - 1.0)
+    n = A.shape[1]
+    Pinv = np.column_stack([P.apply_inv(e) for e in np.eye(n)])
+    sv = np.linalg.svd(np.vstack([A, delta * np.eye(n)]) @ Pinv, compute_uv=False)
+    kappa = sv[0] / sv[-1]
+    assert kappa == pytest.approx(math.sqrt((s[ell] ** 2 + delta ** 2) / (s[-1] ** 2 + delta ** 2)),
+                                  rel=1e-9)
+
+
+# ---------------------------------------------------------------- LSQR ----------------
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_unpreconditioned_phase_equals_scipy_damped_lsqr(k):
+    """LSQR on [A; delta I] and Paige-Saunders damped LSQR minimise the same residual over
+    the same Krylov space, so their k-th iterates coincide."""
+    p = wl.small_dense(200, 50, 782, decay=2.0)
+    delta = 0.05
+    P = O.identity_preconditioner(50)
+    res = O.plsqr_phase(p.dense, p.b, delta, np.zeros(50), P, eps_lsqr=0.0, maxit=k)
+    ref = spla.lsqr(p.dense, p.b, damp=delta, atol=0, btol=0, conlim=0, iter_lim=k)[0]
+    assert res.iters == k
+    assert np.linalg.norm(res.x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_phibar_tracks_explicit_residual():
+    p = wl.small_dense(150, 40, 783, decay=3.0)
+    delta = 1e-2
+    P, *_ = _cur_preconditioner(p.dense, 5, 2, delta)
+    x0 = np.random.default_rng(5).standard_normal(40) * 0.1
+    for k in (1, 3, 6):
+        res = O.plsqr_phase(p.dense, p.b, delta, x0, P, eps_lsqr=0.0, maxit=k)
+        r = np.concatenate([p.b - p.dense @ res.x, -delta * res.x])
+        assert res.phibar[-1] == pytest.approx(np.linalg.norm(r), rel=1e-10)
+
+
+def test_preconditioned_phase_converges_to_ridge_solution():
+    p = wl.small_dense(200, 50, 784, decay=4.0, mu=1e-4)
+    delta = 1e-2
+    P, *_ = _cur_preconditioner(p.dense, 5, 3, delta)
+    res = O.plsqr_phase(p.dense, p.b, delta, np.zeros(50), P, eps_lsqr=1e-14, maxit=2000)
+    xd = O.ridge_direct(p.dense, p.b, p.mu)
+    assert np.linalg.norm(res.x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_ridge_direct_matches_normal_equations():
+    A = _rand(60, 20, 8)
+    b = np.random.default_rng(9).standard_normal(60)
+    mu = 0.3
+    x = O.ridge_direct(A, b, mu)
+    assert np.allclose(x, np.linalg.solve(A.T @ A + mu * np.eye(20), A.T @ b), rtol=1e-12)
+    assert np.allclose(O.ridge_direct(sp.csr_matrix(A), b, mu), x, rtol=1e-13)
+
+
+def test_dynamic_stop_rule():
+    # rate_1 = log 2; rate_j = log(1.001) -> ratio ~ 694 > 100
+    assert O.dynamic_stop(1.001, 1.0, math.log(2.0), 100.0, 0.0)
+    assert not O.dynamic_stop(2.0, 1.0, math.log(2.0), 100.0, 0.0)
+    # absolute drop below sigma_ell
+    assert O.dynamic_stop(2.0, 1.0, math.log(2.0), 100.0, 1.5)
+    # no progress counts as an infinite ratio; disabled in the final phase
+    assert O.dynamic_stop(1.0, 1.0, math.log(2.0), 100.0, 0.0)
+    assert not O.dynamic_stop(1.0, 1.0, math.log(2.0), math.inf, 5.0)
+
+
+# ---------------------------------------------------------------- driver --------------
+
+def test_aplicur_reaches_ridge_solution_and_residual_is_monotone():
+    p = wl.config1(scale=4)       # 500 x 50
+    res = O.aplicur(p.dense, p.b, p.mu, p.sketch_dim, O.Options(seed=2), tol=1e-11)
+    xd = O.ridge_direct(p.dense, p.b, p.mu)
+    assert res.converged
+    kappa = 1.0 / math.sqrt(p.mu)
+    assert np.linalg.norm(res.x - xd) <= kappa * 1e-10 * np.linalg.norm(xd) * 10
+    assert len(res.phases) >= 2
+    ne = [ph["ne_res"] for ph in res.phases]
+    assert ne[-1] <= 1e-11
+
+
+def test_aplicur_warm_restart_residual_nonincreasing():
+    p = wl.small_dense(300, 60, 785, decay=5.0, mu=1e-5, sketch_dim=5)
+    A = p.dense
+    delta = math.sqrt(p.mu)
+    res_norms = []
+    orig = O.plsqr_phase
+
+    def spy(A_, b_, d_, x0, P, **kw):
+        r = orig(A_, b_, d_, x0, P, **kw)
+        for xv in (x0, r.x):
+            res_norms.append(math.hypot(np.linalg.norm(b_ - A_ @ xv), d_ * np.linalg.norm(xv)))
+        return r
+
+    O.plsqr_phase = spy
+    try:
+        O.aplicur(A, p.b, p.mu, 5, O.Options(seed=4), tol=1e-10)
+    finally:
+        O.plsqr_phase = orig
+    assert len(res_norms) >= 4
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res_norms, res_norms[1:]))
+
+
+def test_replay_reproduces_free_run():
+    p = wl.small_dense(200, 40, 786, decay=5.0, mu=1e-5, sketch_dim=4)
+    free = O.aplicur(p.dense, p.b, p.mu, 4, O.Options(seed=5), tol=1e-10)
+    sched = {"phases": [ph["iters"] for ph in free.phases],
+             "rebuild": [st["rebuild"] for st in free.rank_steps]}
+    rep = O.aplicur(p.dense, p.b, p.mu, 4, O.Options(seed=5, replay=sched), tol=1e-10)
+    assert np.array_equal(rep.I, free.I) and np.array_equal(rep.J, free.J)
+    assert np.array_equal(rep.x, free.x)
+
+
+# ---------------------------------------------------------------- adjoint -------------
+
+def test_ridge_gradients_match_central_differences():
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((40, 12))
+    b = rng.standard_normal(40)
+    xt = rng.standard_normal(12)
+    mu = 0.05
+
+    def loss(A_, b_, mu_):
+        x = O.ridge_direct(A_, b_, mu_)
+        return 0.5 * float(np.sum((x - xt) ** 2))
+
+    x = O.ridge_direct(A, b, mu)
+    lam, gb, gmu, gA = O.ridge_gradients(A, b, mu, x, x - xt)
+    h = 1e-6
+    db = rng.standard_normal(40)
+    fd = (loss(A, b + h * db, mu) - loss(A, b - h * db, mu)) / (2 * h)
+    assert fd == pytest.approx(float(gb @ db), rel=1e-6)
+    hm = 1e-6 * mu
+    fd = (loss(A, b, mu + hm) - loss(A, b, mu - hm)) / (2 * hm)
+    assert fd == pytest.approx(gmu, rel=1e-6)
+    for (i, j) in [(0, 0), (5, 3), (39, 11), (17, 6)]:
+        E = np.zeros_like(A)
+        E[i, j] = 1.0
+        fd = (loss(A + h * E, b, mu) - loss(A - h * E, b, mu)) / (2 * h)
+        assert fd == pytest.approx(gA[i, j], rel=1e-5, abs=1e-9)
