@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Time-to-solution benchmark of the APLICUR hot path on one or more GB300s.
+
+One step = one complete solve of the workload through the C ABI: the one-time sketch
+S A, the CUR rank steps, the preconditioner builds and the warm-started
+preconditioned LSQR phases, until the relative normal-equation residual
+||A^T(b - A x) - mu x|| / ||A^T b|| <= 1e-8 (checked in FP64).  Inputs are resident
+in HBM for `value`; `e2e` copies A and b from pinned host memory and x back inside the
+timed region.  Under torchrun every rank solves its own replica (no collective on the
+data path: the method does not shard).  `--impl reference` times the CPU oracle.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 rel. residual; SpMV HBM GB/s %peak; batched solves/s vs plain LSQR"
+TOL = 1e-8
+WORKLOADS = {
+    # name: (generator, precision)
+    "rbf_fp32_20000x20000": ("config3", "mixed"),
+    "dense_fp64_2000x200": ("config1", "fp64"),
+    "sparse_csr_200000x20000": ("config2", "fp64"),
+}
+DEFAULT_WORKLOAD = "rbf_fp32_20000x20000"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--maxit", type=int, default=200000)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(name):
+    from paper_2604_05065_gb300 import workloads as wl
+    gen, prec = WORKLOADS[name]
+    return getattr(wl, gen)(), prec
+
+
+# ----------------------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            lines = [l.strip() for l in f if l.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm --
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p, prec = make_workload(args.workload)
+    precision = pkg.PREC_MIXED if prec == "mixed" else pkg.PREC_FP64
+    if p.fmt == "dense":
+        A_host = torch.from_numpy(p.dense).pin_memory()
+        A = A_host.to(dev, non_blocking=True)
+    else:
+        crow = torch.from_numpy(p.indptr.astype(np.int64))
+        col = torch.from_numpy(p.indices.astype(np.int64))
+        val = torch.from_numpy(p.data)
+        A_host = None
+        A = torch.sparse_csr_tensor(crow, col, val, size=(p.m, p.n)).to(dev)
+    b_host = torch.from_numpy(np.asarray(p.b, dtype=np.float64)).pin_memory()
+    b = b_host.to(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    opts = dict(precision=precision, profile=1, seed=1)
+
+    prof_tot = {"ms": [0.0] * 3, "launches": [0] * 3, "bytes": [0.0] * 3}
+    sched = {}
+
+    def one_solve(Adev, bdev, record=False):
+        s = pkg.Solver(Adev, bdev, p.mu, p.sketch_dim, **opts)
+        x = s.solve(TOL, args.maxit)
+        st = s.stats()
+        if record:
+            pr = s.profile()
+            for k in range(3):
+                prof_tot["ms"][k] += pr["ms"][k]
+                prof_tot["launches"][k] += pr["launches"][k]
+                prof_tot["bytes"][k] += pr["bytes"][k]
+            sched.update(steps=st["nsteps"], phases=st["nphases"], iters=st["iters"],
+                         ell=st["ell"], builds=sum(1 for q in s.steps() if q["rebuild"]),
+                         ne_res=st["ne_res"], converged=st["converged"])
+        s.close()
+        return x, st
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        one_solve(A, b)
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x, st = one_solve(A, b, record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = pkg.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # ---- end to end from pinned host buffers
+    e2e = None
+    if A_host is not None:
+        Ae = torch.empty_like(A)
+        be = torch.empty_like(b)
+        for _ in range(1):
+            Ae.copy_(A_host, non_blocking=True)
+            be.copy_(b_host, non_blocking=True)
+            xh = one_solve(Ae, be)[0].cpu()
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            Ae.copy_(A_host, non_blocking=True)
+            be.copy_(b_host, non_blocking=True)
+            xh = one_solve(Ae, be)[0].to("cpu")
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        et = torch.tensor([ems], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / (float(et.item()) / 1000.0), "unit": "solves/s",
+               "h2d_bytes_per_step": int(A_host.numel() * A_host.element_size() + b_host.numel() * 8),
+               "d2h_bytes_per_step": int(p.n * 8)}
+        del Ae, be
+
+    # ---- plain (unpreconditioned) LSQR on the same GPU, same kernels
+    plain = None
+    if not args.no_plain:
+        s = pkg.Solver(A, b, p.mu, p.sketch_dim, **opts)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        s.plain_lsqr(TOL, args.maxit)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        pst = s.stats()
+        plain = {"ms": g0.elapsed_time(g1), "iters": pst["iters"], "ne_res": pst["ne_res"],
+                 "converged": bool(pst["converged"])}
+        s.close()
+
+    # ---- roofline of the dominant hot-loop kernel
+    names = ["A z pass (k1)", "A^T u pass (k2)", "preconditioner passes (k3+k4)"]
+    k = max(range(3), key=lambda q: prof_tot["ms"][q])
+    peak, src = peaks()
+    roof = None
+    if prof_tot["launches"][k]:
+        avg_ms = prof_tot["ms"][k] / prof_tot["launches"][k]
+        bpl = prof_tot["bytes"][k] / prof_tot["launches"][k]
+        achieved = bpl / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_for(k, bpl),
+                "kernel": names[k], "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
+                if src == "measured" else "fallback 6800 GB/s",
+                "avg_launch_ms": round(avg_ms, 5), "bytes_per_launch": int(bpl),
+                "launches_timed": prof_tot["launches"][k],
+                "all_kernels": {names[q]: {"ms_total": round(prof_tot["ms"][q], 3),
+                                           "launches": prof_tot["launches"][q],
+                                           "GBps": round(prof_tot["bytes"][q] /
+                                                         max(prof_tot["ms"][q], 1e-9) / 1e6, 1)}
+                                for q in range(3)}}
+    return dict(value=value, ms=ms_max / args.steps, p=p, prec=prec, clocks=clk, e2e=e2e,
+                plain=plain, roof=roof, launches=launches, sched=sched, ne=st["ne_res"])
+
+
+def traffic_for(k, bpl):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch size,
+    or None when no capture of the current kernel source exists."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(str(k))
+        if not ent:
+            return None
+        import hashlib
+        src = open(os.path.join(ROOT, ent["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != ent["sha256"]:
+            return None
+        return int(ent["dram_bytes_per_algorithmic_byte"] * bpl)
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU arm --
+
+def oracle_sample(p, sched, iters_sample=6):
+    """Times the oracle on a bounded sample of the full workload and scales it to one
+    solve with the run's schedule (rank steps, preconditioner builds, LSQR iterations)."""
+    import numpy as np
+
+    from oracle import aplicur_oracle as O
+    from oracle import rng as orng
+
+    A = p.to_scipy() if p.fmt == "csr" else np.asarray(p.dense, dtype=np.float64)
+    b = np.asarray(p.b, dtype=np.float64)
+    s = O.sketch_rows(p.sketch_dim)
+    xi = O.sketch_xi(s)
+    t0 = time.perf_counter()
+    rows, signs = orng.sparse_sign(1, s, p.m, xi)
+    W = orng.gaussian_w(1, p.n, 10)
+    Y = O.apply_sketch(A, rows, signs, s)
+    t_sketch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    I0 = np.zeros(0, np.int64)
+    Ip, Jp, _ = O.augment_cur(A, I0, I0, Y, None, p.sketch_dim)
+    core = O.Core(A, Ip, Jp)
+    E = O.sketched_residual(A, Y, Ip, Jp, core)
+    O.norm_estimate(E, W)
+    Q, T = O.augment_qr(None, None, O.rows(A, Ip).T)
+    t_step = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P = O.build_preconditioner(O.cols(A, Jp), core, Q, T, math.sqrt(p.mu))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.plsqr_phase(A, b, math.sqrt(p.mu), np.zeros(p.n), P, eps_lsqr=0.0, maxit=iters_sample)
+    t_iter = (time.perf_counter() - t0) / iters_sample
+    est = (t_sketch + sched.get("steps", 1) * t_step + sched.get("builds", 1) * t_build
+           + sched.get("iters", 1) * t_iter)
+    sample = (f"oracle on the full workload: sketch, 1 rank step, 1 preconditioner build and "
+              f"{iters_sample} LSQR iterations ({t_sketch:.2f}+{t_step:.2f}+{t_build:.2f}+"
+              f"{iters_sample}x{t_iter:.3f} s), scaled to one solve by the schedule "
+              f"{sched.get('steps')} rank steps / {sched.get('builds')} builds / "
+              f"{sched.get('iters')} iterations")
+    return 1.0 / est, sample, t_sketch + t_step + t_build + iters_sample * t_iter
+
+
+def load_schedule(name):
+    path = os.path.join(ROOT, "tests", "golden", f"schedule_{name}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    p, prec = make_workload(args.workload)
+    sched = load_schedule(args.workload) or {"steps": 1, "builds": 1, "iters": 1}
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, sample, _ = oracle_sample(p, sched)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu,
+                       "sketch_dim": p.sketch_dim, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- main -----
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    r = gpu_arm(args, rank, world, local_rank)
+    if rank == 0:
+        p = r["p"]
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            sched = load_schedule(args.workload) or r["sched"]
+            v, sample, secs = oracle_sample(p, sched)
+            cpu = {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": sample, "sample_seconds": round(secs, 2)}
+        line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if r["prec"] == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu,
+                           "sketch_dim": p.sketch_dim, "tol": TOL,
+                           "precision": "fp32 products, fp64 scalars/core/refinement"
+                           if r["prec"] == "mixed" else "fp64",
+                           "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2" if p.nnz * p.dtype.itemsize > 129e6
+                           else "L2-resident inputs (no flush)"},
+                "time_to_tol_s": r["ms"] / 1000.0, "schedule": r["sched"],
+                "ne_res": r["ne"], "plain_lsqr": r["plain"], "clocks": r["clocks"],
+                "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roof"],
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * aplicur.h -- C ABI of the GB300 (sm_103a) APLICUR solver.
+ *
+ * APLICUR solves the regularized linear least-squares problem
+ *     min_x ||A x - b||_2^2 + mu ||x||_2^2,   A in R^{m x n}, m >= n,
+ * (Huh, Cartis, Nakatsukasa, "Adaptive LSQR Preconditioning from One Small
+ * Sketch", Eq. regularizedLLS) by LSQR on the augmented matrix
+ * [A; delta I], delta = sqrt(mu) (Eq. augLLS), right-preconditioned by the
+ * CUR-based spectral preconditioner of Eq. preconditioner2, which is refined
+ * between warm-started LSQR phases from one sparse-sign sketch S A
+ * (Algorithm "APLICUR: detailed implementation").
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device addresses on the current device; host
+ *    pointers are ordinary process memory.  Each argument says which.
+ *  - Dense matrices passed in are row-major with leading dimension `ld`
+ *    (elements); small dense outputs are column-major unless stated.
+ *  - Borrowed inputs (A, b) must stay alive and unmodified until
+ *    aplicur_destroy.  The library never frees caller memory.
+ *  - All work is issued on the stream given at creation (a cudaStream_t
+ *    passed as void*; NULL means the legacy default stream).  Calls that
+ *    return host results synchronise that stream.
+ *  - No C++ exception crosses this boundary.  Every call returns an
+ *    aplicur_status; on failure aplicur_last_error(h) holds a message.
+ *  - Calls on one handle are not thread-safe; distinct handles are.
+ */
+#ifndef APLICUR_H_
+#define APLICUR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APLICUR_OK = 0,
+  APLICUR_EINVAL = 1,      /* invalid argument (shape, pointer, option) */
+  APLICUR_ENOMEM = 2,      /* device or host allocation failed */
+  APLICUR_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  APLICUR_ENOTCONV = 4,    /* maxit reached before tol; x_out holds the best iterate */
+  APLICUR_EBREAKDOWN = 5,  /* a Cholesky factorisation met a non-positive pivot */
+  APLICUR_ETIMEOUT = 6     /* a bounded device wait gave up */
+} aplicur_status;
+
+enum { APLICUR_DENSE_ROWMAJOR = 0, APLICUR_CSR = 1 };
+enum { APLICUR_F64 = 0, APLICUR_F32 = 1 };
+/* Arithmetic of the products with A and with the preconditioner basis:
+ * FP64 = FP64 products and sums; MIXED = FP32 products with FP32 partial
+ * sums (FP64 across threads), FP32 preconditioner basis, FP64 scalars,
+ * FP64 core factorisations and an FP64 residual refinement at the end. */
+enum { APLICUR_PREC_FP64 = 0, APLICUR_PREC_MIXED = 1 };
+
+/* The matrix A (borrowed, device memory).
+ *  format = APLICUR_DENSE_ROWMAJOR: values -> m x n row-major, leading dim ld >= n.
+ *  format = APLICUR_CSR: rowptr (m+1 int32), colidx (nnz int32, column indices
+ *  of each row in increasing order), values (nnz).  dtype selects F64 or F32
+ *  values.  The library builds its own transposed (CSC) copy at creation. */
+typedef struct {
+  int32_t format;
+  int32_t dtype;
+  int64_t m, n, ld, nnz;
+  const void* values;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+} aplicur_matrix;
+
+/* Solver options; fill with aplicur_options_default() then override.
+ * Defaults follow the paper's Section 7 settings: eps_cur = 30 delta,
+ * nu_prec = 10, nu_lsqr = 100, eps_lsqr = 1e-10, xi = 8, r = 10. */
+typedef struct {
+  uint64_t seed;             /* drives S and W when they are not supplied */
+  double eps_cur_factor;     /* eps_cur = eps_cur_factor * sqrt(mu) */
+  double nu_prec;            /* re-preconditioning tolerance (Section 5.3.2) */
+  double nu_lsqr;            /* dynamic LSQR stopping tolerance (Section 5.3.2) */
+  double eps_lsqr;           /* Paige-Saunders stopping tolerance of each phase */
+  int32_t xi;                /* nonzeros per sketch column (capped at s) */
+  int32_t normest_r;         /* Gaussian vectors of Eq. 2normestimate */
+  int32_t check_gap;         /* LSQR iterations between explicit residual checks */
+  int32_t max_extra_phases;  /* warm restarts of the final phase */
+  int32_t precision;         /* APLICUR_PREC_FP64 or APLICUR_PREC_MIXED */
+  int32_t graph_iters;       /* LSQR iterations per captured CUDA graph (>=1) */
+  /* Optional host arrays that replace the seeded draws (parity testing):
+   * sketch_rows/sketch_signs: m*xi row indices in [0,s) and +-1 signs of the
+   * sparse sign embedding, row-major by column of S; normest_w: n*r Gaussian
+   * matrix, column-major.  Copied at creation. */
+  const int32_t* sketch_rows;
+  const int8_t* sketch_signs;
+  const double* normest_w;
+  /* Optional replay schedule (host arrays, copied at creation; see also
+   * aplicur_set_replay): phase k runs exactly replay_phases[k] LSQR iterations
+   * and rank step k rebuilds the preconditioner iff replay_rebuild[k] != 0.
+   * Used to run the exact schedule of another run (e.g. of a reference solve)
+   * so that iterates can be compared; explicit residual checks are off then. */
+  int32_t replay_nphases;
+  const int32_t* replay_phases;
+  int32_t replay_nsteps;
+  const int8_t* replay_rebuild;
+  /* Non-zero: record CUDA events around the hot-loop kernels inside every LSQR
+   * iteration and accumulate their device times (aplicur_get_profile). */
+  int32_t profile;
+} aplicur_options;
+
+/* Device time of the LSQR hot-loop kernels, accumulated over the solves since
+ * creation or the last aplicur_reset_profile (requires options.profile).
+ * Index 0: the A z pass, 1: the A^T u pass, 2: the preconditioner passes
+ * (Vhat^T w and the expansion). */
+typedef struct {
+  double ms[3];              /* summed event-to-event device time */
+  int64_t launches[3];       /* timed launches */
+  double bytes[3];           /* summed algorithmic bytes of the timed launches */
+  int64_t kernel_launches;   /* all kernels this process launched through the library */
+} aplicur_profile;
+
+typedef struct aplicur_ctx* aplicur_handle;
+
+typedef struct {
+  int64_t iters;        /* LSQR iterations over all phases */
+  int32_t ell;          /* final CUR rank */
+  int32_t nphases;      /* LSQR phases run */
+  int32_t nsteps;       /* rank steps taken */
+  int32_t converged;    /* explicit relative residual <= tol */
+  double ne_res;        /* ||A^T(b - A x) - mu x|| / ||A^T b|| at exit (FP64) */
+  double rho;           /* last norm estimate */
+  double time_setup_ms; /* sketch and creation work (device time) */
+  double time_solve_ms; /* aplicur_solve wall time */
+} aplicur_stats;
+
+/* Fill `opt` with the defaults above. */
+void aplicur_options_default(aplicur_options* opt);
+
+/* Create a solver for (A, b, mu) with block size b = sketch_dim and sketch
+ * rows s = ceil(1.1 b) (Algorithm "APLICUR: detailed implementation",
+ * Initialise), and compute the sketch Y = S A once (Section 5.1).
+ *  out        host: receives the handle.
+ *  A          host struct describing borrowed device memory (see above).
+ *  b          device: m doubles (borrowed).
+ *  mu         >= 0, coefficient of ||x||^2.
+ *  sketch_dim block size b, 1 <= b <= min(m, n).
+ *  opt        host, nullable (defaults).
+ *  stream     cudaStream_t as void*.
+ * Errors: EINVAL (m < n, bad pointers, sizes), ENOMEM, ECUDA. */
+aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, const double* b,
+                              double mu, int32_t sketch_dim, const aplicur_options* opt,
+                              void* stream);
+
+/* Run the adaptive solve (CUR rank steps, preconditioner updates, warm-started
+ * LSQR phases) until the relative normal-equation residual
+ * ||A^T(b - A x) - mu x|| / ||A^T b|| <= tol (checked in FP64) or maxit LSQR
+ * iterations.  Restarts from x = 0 and I = J = {} on every call.
+ *  x_out device: n doubles (caller-owned).
+ * Returns OK, ENOTCONV (x_out still written), EBREAKDOWN, ETIMEOUT, ECUDA. */
+aplicur_status aplicur_solve(aplicur_handle h, double tol, int64_t maxit, double* x_out);
+
+/* Replace the replay schedule (host arrays, copied).  nphases = nsteps = 0
+ * turns replay off. */
+aplicur_status aplicur_set_replay(aplicur_handle h, int32_t nphases, const int32_t* phases,
+                                  int32_t nsteps, const int8_t* rebuild);
+
+/* Plain (unpreconditioned) LSQR on [A; delta I] with the same kernels and the
+ * same stopping test: the comparison baseline.  x_out device n doubles. */
+aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, double* x_out);
+
+/* Adjoint of the last solve (not in the paper).  With g = dL/dx (device, n),
+ * solves (A^T A + mu I) lambda = g by preconditioned LSQR on
+ * min ||[A; delta I] lambda - [0; g/delta]|| with the final preconditioner, then
+ *   grad_b  = A lambda                    (device, m doubles, may be NULL)
+ *   grad_mu = -lambda^T x                 (host, 1 double, may be NULL)
+ *   grad_A  = r lambda^T - (A lambda) x^T (device, m x n row-major in A's dtype,
+ *             leading dim n; dense A only; may be NULL), r = b - A x.
+ * Requires mu > 0 and a previous aplicur_solve. */
+aplicur_status aplicur_backward(aplicur_handle h, const double* grad_x, double tol,
+                                int64_t maxit, double* grad_b, double* grad_mu, void* grad_A);
+
+/* Copy the CUR row and column indices (selection order) to host arrays of
+ * capacity min(m, n); *ell receives their count.  I or J may be NULL. */
+aplicur_status aplicur_get_indices(aplicur_handle h, int32_t* I, int32_t* J, int32_t* ell);
+
+/* Copy the sketch Y = S A (s x n, column-major, FP64) to device memory y_out;
+ * *s_out (host) receives s. */
+aplicur_status aplicur_get_sketch(aplicur_handle h, double* y_out, int32_t* s_out);
+
+/* Summary of the last solve (host struct). */
+aplicur_status aplicur_get_stats(aplicur_handle h, aplicur_stats* st);
+
+/* Per-phase record k of the last solve: CUR rank, LSQR iterations, stop reason
+ * (0 none, 1 exact, 2 replay, 3 Paige-Saunders test 2, 4 test 1, 5 dynamic,
+ * 6 tol, 7 maxit, 9 drift: the recurrence estimate passed tol but the FP64
+ * residual did not, so the phase ends and the next one restarts from an
+ * exactly formed residual), relative normal-equation residual at the phase end. */
+aplicur_status aplicur_get_phase(aplicur_handle h, int32_t k, int32_t* ell, int64_t* iters,
+                                 int32_t* reason, double* ne_res);
+
+/* Per-rank-step record k of the last solve: rank after the step, norm estimate
+ * rho (Eq. 2normestimate), whether the preconditioner was rebuilt, and the
+ * smallest relative LUPP pivot margin of the step (near-tie indicator). */
+aplicur_status aplicur_get_step(aplicur_handle h, int32_t k, int32_t* ell, double* rho,
+                                int32_t* rebuilt, double* margin);
+
+/* The current preconditioner: rank ell (host) and, when the pointers are not
+ * NULL, sigma (device ell doubles, singular values of the CUR approximation,
+ * descending) and its target level sigma-hat (host). */
+aplicur_status aplicur_get_preconditioner(aplicur_handle h, int32_t* ell, double* sigma,
+                                          double* sighat);
+
+/* Apply the current preconditioner: out = P^{-1} w (Eq. preconditioner2 inverted),
+ * w and out device n doubles.  ell = 0 gives the identity. */
+aplicur_status aplicur_apply_preconditioner(aplicur_handle h, const double* w, double* out);
+
+/* y = A x (trans = 0, x: n, y: m) or y = A^T x (trans = 1, x: m, y: n), device
+ * doubles, with the solver's kernels in its precision mode. */
+aplicur_status aplicur_matvec(aplicur_handle h, int32_t trans, const double* x, double* y);
+
+/* Hot-loop kernel times and the launch count (host struct). */
+aplicur_status aplicur_get_profile(aplicur_handle h, aplicur_profile* out);
+
+/* Zero the accumulated kernel times of h. */
+aplicur_status aplicur_reset_profile(aplicur_handle h);
+
+/* Kernels this process has launched through the library (every handle). */
+int64_t aplicur_launch_count(void);
+
+/* Message of the last failed call on h (never NULL). */
+const char* aplicur_last_error(aplicur_handle h);
+
+/* Static description of a status code (never NULL). */
+const char* aplicur_status_string(aplicur_status st);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void aplicur_destroy(aplicur_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APLICUR_H_ */

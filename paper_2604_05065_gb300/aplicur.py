@@ -1,0 +1,389 @@
+"""Python binding of the APLICUR C ABI (include/aplicur.h).
+
+Argument marshalling only: every numerical step runs in libaplicur.so.  PyTorch
+provides device memory and the current CUDA stream.  There is no CPU fallback:
+if the library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+REASONS = {0: "none", 1: "exact", 2: "replay", 3: "ps_test2", 4: "ps_test1", 5: "dynamic",
+           6: "tol", 7: "maxit", 9: "drift"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
+          6: "ETIMEOUT"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class AplicurError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Matrix(C.Structure):
+    _fields_ = [("format", C.c_int32), ("dtype", C.c_int32), ("m", C.c_int64), ("n", C.c_int64),
+                ("ld", C.c_int64), ("nnz", C.c_int64), ("values", C.c_void_p),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("eps_cur_factor", C.c_double), ("nu_prec", C.c_double),
+                ("nu_lsqr", C.c_double), ("eps_lsqr", C.c_double), ("xi", C.c_int32),
+                ("normest_r", C.c_int32), ("check_gap", C.c_int32),
+                ("max_extra_phases", C.c_int32), ("precision", C.c_int32),
+                ("graph_iters", C.c_int32), ("sketch_rows", C.c_void_p),
+                ("sketch_signs", C.c_void_p), ("normest_w", C.c_void_p),
+                ("replay_nphases", C.c_int32), ("replay_phases", C.c_void_p),
+                ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
+                ("profile", C.c_int32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 3), ("launches", C.c_int64 * 3), ("bytes", C.c_double * 3),
+                ("kernel_launches", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("ell", C.c_int32), ("nphases", C.c_int32),
+                ("nsteps", C.c_int32), ("converged", C.c_int32), ("ne_res", C.c_double),
+                ("rho", C.c_double), ("time_setup_ms", C.c_double),
+                ("time_solve_ms", C.c_double)]
+
+
+# every entry point of include/aplicur.h: name -> (restype, argtypes)
+_VP, _D, _I32, _I64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
+_PI32 = C.POINTER(C.c_int32)
+SIGNATURES = {
+    "aplicur_options_default": (None, [C.POINTER(Options)]),
+    "aplicur_create": (C.c_int, [C.POINTER(_VP), C.POINTER(Matrix), _VP, _D, _I32,
+                                 C.POINTER(Options), _VP]),
+    "aplicur_solve": (C.c_int, [_VP, _D, _I64, _VP]),
+    "aplicur_set_replay": (C.c_int, [_VP, _I32, _VP, _I32, _VP]),
+    "aplicur_plain_lsqr": (C.c_int, [_VP, _D, _I64, _VP]),
+    "aplicur_backward": (C.c_int, [_VP, _VP, _D, _I64, _VP, C.POINTER(_D), _VP]),
+    "aplicur_get_indices": (C.c_int, [_VP, _VP, _VP, _PI32]),
+    "aplicur_get_sketch": (C.c_int, [_VP, _VP, _PI32]),
+    "aplicur_get_stats": (C.c_int, [_VP, C.POINTER(Stats)]),
+    "aplicur_get_phase": (C.c_int, [_VP, _I32, _PI32, C.POINTER(_I64), _PI32, C.POINTER(_D)]),
+    "aplicur_get_step": (C.c_int, [_VP, _I32, _PI32, C.POINTER(_D), _PI32, C.POINTER(_D)]),
+    "aplicur_get_preconditioner": (C.c_int, [_VP, _PI32, _VP, C.POINTER(_D)]),
+    "aplicur_apply_preconditioner": (C.c_int, [_VP, _VP, _VP]),
+    "aplicur_matvec": (C.c_int, [_VP, _I32, _VP, _VP]),
+    "aplicur_get_profile": (C.c_int, [_VP, C.POINTER(Profile)]),
+    "aplicur_reset_profile": (C.c_int, [_VP]),
+    "aplicur_launch_count": (C.c_int64, []),
+    "aplicur_last_error": (C.c_char_p, [_VP]),
+    "aplicur_status_string": (C.c_char_p, [C.c_int]),
+    "aplicur_destroy": (None, [_VP]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> C.CDLL:
+    """Load libaplicur.so (in-tree).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run __graft_entry__.build() first")
+        _build.build_library()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def default_options() -> Options:
+    o = Options()
+    load().aplicur_options_default(C.byref(o))
+    return o
+
+
+def _check(lib, st, h=None):
+    if st != 0 and st != 4:
+        msg = lib.aplicur_last_error(h).decode() if h is not None else ""
+        raise AplicurError(st, msg)
+    return st
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("APLICUR needs a CUDA GPU")
+    return torch
+
+
+class Solver:
+    """One APLICUR problem min ||A x - b||^2 + mu ||x||^2 on the GPU.
+
+    A: a dense CUDA tensor (m x n, float64 or float32, row-major) or a
+    torch.sparse_csr_tensor on CUDA; b: CUDA tensor of m values (converted to
+    float64).  Options are fields of the C options struct."""
+
+    def __init__(self, A, b, mu: float, sketch_dim: int, *, sketch_rows=None, sketch_signs=None,
+                 normest_w=None, replay=None, **opts):
+        torch = _torch()
+        lib = load()
+        self._lib = lib
+        self._h = None
+        mat = Matrix()
+        if A.layout == torch.sparse_csr:
+            rowptr = A.crow_indices().to(torch.int32).contiguous()
+            colidx = A.col_indices().to(torch.int32).contiguous()
+            vals = A.values().contiguous()
+            self._keep = [rowptr, colidx, vals]
+            mat.format = 1
+            mat.nnz = vals.numel()
+            mat.values = vals.data_ptr()
+            mat.rowptr = rowptr.data_ptr()
+            mat.colidx = colidx.data_ptr()
+            mat.ld = A.shape[1]
+            dt = vals.dtype
+        else:
+            if A.stride(1) != 1:
+                A = A.contiguous()
+            self._keep = [A]
+            mat.format = 0
+            mat.ld = A.stride(0)
+            mat.nnz = A.shape[0] * A.shape[1]
+            mat.values = A.data_ptr()
+            dt = A.dtype
+        if dt == torch.float64:
+            mat.dtype = 0
+        elif dt == torch.float32:
+            mat.dtype = 1
+        else:
+            raise TypeError("A must be float64 or float32")
+        mat.m, mat.n = int(A.shape[0]), int(A.shape[1])
+        self.m, self.n = mat.m, mat.n
+        self.dtype = dt
+        self.device = b.device
+        b = b.to(torch.float64).contiguous()
+        self._keep.append(b)
+        self.b = b
+        o = default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        import numpy as np
+        host = []
+        if sketch_rows is not None:
+            r = np.ascontiguousarray(sketch_rows, dtype=np.int32)
+            s = np.ascontiguousarray(sketch_signs, dtype=np.int8)
+            host += [r, s]
+            o.sketch_rows = r.ctypes.data
+            o.sketch_signs = s.ctypes.data
+            o.xi = r.shape[1]
+        if normest_w is not None:
+            w = np.asfortranarray(normest_w, dtype=np.float64)
+            host.append(w)
+            o.normest_w = w.ctypes.data
+            o.normest_r = w.shape[1]
+        self.mu = float(mu)
+        self.sketch_dim = int(sketch_dim)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        h = C.c_void_p()
+        st = lib.aplicur_create(C.byref(h), C.byref(mat), b.data_ptr(), self.mu, self.sketch_dim,
+                                C.byref(o), C.c_void_p(stream))
+        if st != 0:
+            raise AplicurError(st, lib.aplicur_last_error(None).decode())
+        self._h = h
+        if replay is not None:
+            self.set_replay(replay)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.aplicur_destroy(self._h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    # ------------------------------------------------------------------ solves ------
+    def solve(self, tol: float = 1e-10, maxit: int = 100000):
+        torch = _torch()
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        st = self._lib.aplicur_solve(self._h, tol, maxit, x.data_ptr())
+        _check(self._lib, st, self._h)
+        self.last_status = st
+        return x
+
+    def plain_lsqr(self, tol: float = 1e-10, maxit: int = 100000):
+        torch = _torch()
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        st = self._lib.aplicur_plain_lsqr(self._h, tol, maxit, x.data_ptr())
+        _check(self._lib, st, self._h)
+        self.last_status = st
+        return x
+
+    def backward(self, grad_x, tol: float = 1e-10, maxit: int = 100000, want_A: bool = True):
+        torch = _torch()
+        g = grad_x.to(torch.float64).contiguous()
+        gb = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        gmu = C.c_double(0.0)
+        gA = None
+        if want_A:
+            gA = torch.empty(self.m, self.n, dtype=self.dtype, device=self.device)
+        st = self._lib.aplicur_backward(self._h, g.data_ptr(), tol, maxit, gb.data_ptr(),
+                                        C.byref(gmu), gA.data_ptr() if gA is not None else None)
+        _check(self._lib, st, self._h)
+        return gb, gmu.value, gA
+
+    def set_replay(self, replay: dict):
+        import numpy as np
+        ph = np.ascontiguousarray(replay.get("phases", []), dtype=np.int32)
+        rb = np.ascontiguousarray(replay.get("rebuild", []), dtype=np.int8)
+        st = self._lib.aplicur_set_replay(self._h, ph.size, ph.ctypes.data if ph.size else None,
+                                          rb.size, rb.ctypes.data if rb.size else None)
+        _check(self._lib, st, self._h)
+
+    # ------------------------------------------------------------------ queries -----
+    def indices(self):
+        import numpy as np
+        k = min(self.m, self.n)
+        I = np.zeros(k, dtype=np.int32)
+        J = np.zeros(k, dtype=np.int32)
+        ell = C.c_int32(0)
+        _check(self._lib, self._lib.aplicur_get_indices(self._h, I.ctypes.data, J.ctypes.data,
+                                                        C.byref(ell)), self._h)
+        return I[:ell.value].copy(), J[:ell.value].copy()
+
+    def sketch(self):
+        torch = _torch()
+        s = C.c_int32(0)
+        _check(self._lib, self._lib.aplicur_get_sketch(self._h, None, C.byref(s)), self._h)
+        Y = torch.empty(self.n, s.value, dtype=torch.float64, device=self.device)
+        _check(self._lib, self._lib.aplicur_get_sketch(self._h, Y.data_ptr(), C.byref(s)),
+               self._h)
+        return Y.T  # s x n
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._lib, self._lib.aplicur_get_stats(self._h, C.byref(st)), self._h)
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+    def phases(self) -> list:
+        out = []
+        for k in range(self.stats()["nphases"]):
+            ell, it, rs, ne = C.c_int32(), C.c_int64(), C.c_int32(), C.c_double()
+            _check(self._lib, self._lib.aplicur_get_phase(self._h, k, C.byref(ell), C.byref(it),
+                                                          C.byref(rs), C.byref(ne)), self._h)
+            out.append(dict(ell=ell.value, iters=it.value, reason=REASONS.get(rs.value),
+                            ne_res=ne.value))
+        return out
+
+    def steps(self) -> list:
+        out = []
+        for k in range(self.stats()["nsteps"]):
+            ell, rho, rb, mg = C.c_int32(), C.c_double(), C.c_int32(), C.c_double()
+            _check(self._lib, self._lib.aplicur_get_step(self._h, k, C.byref(ell), C.byref(rho),
+                                                         C.byref(rb), C.byref(mg)), self._h)
+            out.append(dict(ell=ell.value, rho=rho.value, rebuild=bool(rb.value),
+                            margin=mg.value))
+        return out
+
+    def preconditioner(self):
+        torch = _torch()
+        ell = C.c_int32(0)
+        sh = C.c_double(0.0)
+        _check(self._lib, self._lib.aplicur_get_preconditioner(self._h, C.byref(ell), None,
+                                                               C.byref(sh)), self._h)
+        sig = torch.empty(max(ell.value, 1), dtype=torch.float64, device=self.device)
+        _check(self._lib, self._lib.aplicur_get_preconditioner(self._h, C.byref(ell),
+                                                               sig.data_ptr(), C.byref(sh)),
+               self._h)
+        return sig[:ell.value], sh.value
+
+    def apply_preconditioner(self, w):
+        torch = _torch()
+        w = w.to(torch.float64).contiguous()
+        out = torch.empty_like(w)
+        _check(self._lib, self._lib.aplicur_apply_preconditioner(self._h, w.data_ptr(),
+                                                                 out.data_ptr()), self._h)
+        return out
+
+    def profile(self) -> dict:
+        pr = Profile()
+        _check(self._lib, self._lib.aplicur_get_profile(self._h, C.byref(pr)), self._h)
+        return {"ms": list(pr.ms), "launches": list(pr.launches), "bytes": list(pr.bytes),
+                "kernel_launches": pr.kernel_launches}
+
+    def matvec(self, x, trans: bool = False):
+        torch = _torch()
+        x = x.to(torch.float64).contiguous()
+        y = torch.empty(self.n if trans else self.m, dtype=torch.float64, device=self.device)
+        _check(self._lib, self._lib.aplicur_matvec(self._h, 1 if trans else 0, x.data_ptr(),
+                                                   y.data_ptr()), self._h)
+        return y
+
+
+def launch_count() -> int:
+    """Kernels launched through the library by this process so far."""
+    return int(load().aplicur_launch_count())
+
+
+def solve(A, b, mu, sketch_dim, tol=1e-10, maxit=100000, **opts):
+    """x = argmin ||A x - b||^2 + mu ||x||^2 by APLICUR on the GPU."""
+    s = Solver(A, b, mu, sketch_dim, **opts)
+    try:
+        return s.solve(tol, maxit)
+    finally:
+        s.close()
+
+
+def _autograd_function():
+    import torch
+
+    class APLICURSolve(torch.autograd.Function):
+        """x(A, b, mu) = argmin ||A x - b||^2 + mu ||x||^2 with gradients with respect to
+        A (dense), b and mu from the adjoint solve (A^T A + mu I) lambda = dL/dx."""
+
+        @staticmethod
+        def forward(ctx, A, b, mu, sketch_dim=100, tol=1e-10, maxit=100000, opts=None):
+            mu_v = float(mu.item()) if torch.is_tensor(mu) else float(mu)
+            s = Solver(A.detach(), b.detach(), mu_v, int(sketch_dim), **(opts or {}))
+            x = s.solve(tol, maxit)
+            ctx.solver = s
+            ctx.tol, ctx.maxit = tol, maxit
+            ctx.mu_is_tensor = torch.is_tensor(mu)
+            ctx.mu_dtype = mu.dtype if torch.is_tensor(mu) else None
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            s = ctx.solver
+            gb, gmu, gA = s.backward(gx, ctx.tol, ctx.maxit, want_A=ctx.needs_input_grad[0])
+            gmu_t = None
+            if ctx.needs_input_grad[2] and ctx.mu_is_tensor:
+                gmu_t = torch.tensor(gmu, dtype=ctx.mu_dtype, device=gx.device)
+            s.close()
+            return (gA if ctx.needs_input_grad[0] else None,
+                    gb if ctx.needs_input_grad[1] else None, gmu_t, None, None, None, None)
+
+    return APLICURSolve
+
+
+class _Lazy:
+    def __get__(self, obj, owner):
+        return _autograd_function()
+
+
+def aplicur_solve_fn():
+    """The torch.autograd.Function class (created lazily so that importing this module
+    does not import torch)."""
+    return _autograd_function()

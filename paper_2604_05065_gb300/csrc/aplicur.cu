@@ -1,0 +1,997 @@
+// APLICUR driver (Algorithm "APLICUR: detailed implementation") and the C ABI.
+// The host keeps the state machine (rank steps, rebuild decisions, phases); every
+// operation with an m- or n-sized extent runs in the library's kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/aplicur.h"
+#include "dense.cuh"
+#include "lsqr.cuh"
+
+using namespace apl;
+
+namespace {
+
+// ---- project random generator (SplitMix64, Steele, Lea & Flood 2014) ------------------
+constexpr uint64_t GOLDEN = 0x9E3779B97F4A7C15ULL;
+inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+inline uint64_t stream_state(uint64_t seed, uint64_t t, uint64_t i) {
+  return mix64(seed ^ ((t & 0xFFULL) << 56) ^ (i & ((1ULL << 56) - 1)));
+}
+
+// Sparse sign embedding (Section 5.1): column i holds xi distinct rows in [0, s).
+void draw_sketch(uint64_t seed, int s, int64_t m, int xi, std::vector<int>& rows,
+                 std::vector<int8_t>& signs) {
+  rows.assign((size_t)m * xi, 0);
+  signs.assign((size_t)m * xi, 1);
+  for (int64_t i = 0; i < m; ++i) {
+    uint64_t st = stream_state(seed, 1, (uint64_t)i);
+    int cnt = 0;
+    int* r = rows.data() + i * xi;
+    while (cnt < xi) {
+      st += GOLDEN;
+      const uint64_t z = mix64(st);
+      const int v = (int)(((z >> 32) * (uint64_t)s) >> 32);
+      bool taken = false;
+      for (int k = 0; k < cnt; ++k) taken = taken || r[k] == v;
+      if (!taken) r[cnt++] = v;
+    }
+    uint64_t ss = stream_state(seed, 2, (uint64_t)i);
+    for (int k = 0; k < xi; ++k) {
+      ss += GOLDEN;
+      signs[i * xi + k] = (mix64(ss) >> 63) == 0 ? 1 : -1;
+    }
+  }
+}
+
+// Gaussian n x r matrix (column-major) by Box-Muller on the generator's uniforms.
+void draw_gaussian(uint64_t seed, int64_t n, int r, std::vector<double>& W) {
+  W.resize((size_t)n * r);
+  const double two_pi = 2.0 * M_PI;
+  for (int64_t idx = 0; idx < n * r; ++idx) {
+    const uint64_t st = stream_state(seed, 3, (uint64_t)idx);
+    const uint64_t z1 = mix64(st + GOLDEN);
+    const uint64_t z2 = mix64(st + 2 * GOLDEN);
+    const double u1 = (double)((z1 >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+    W[idx] = std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+  }
+}
+
+// ---- small kernels local to the driver --------------------------------------------------
+__global__ void add2d_kernel(int64_t rows, int64_t cols, const double* src, int64_t lds,
+                             double* dst, int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e % rows, c = e / rows;
+  dst[r + c * ldd] += src[r + c * lds];
+}
+__global__ void to_f32_kernel(int64_t n, const double* s, float* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+__global__ void scale_kernel(int64_t n, const double* s, double a, double* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = a * s[i];
+}
+__global__ void dot_kernel(int64_t n, const double* a, const double* b, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+// grad_A(i, j) = r_i lambda_j - (A lambda)_i x_j, row-major, ld n.
+template <typename T>
+__global__ void rank2_kernel(int64_t m, int64_t n, const double* r, const double* lam,
+                             const double* al, const double* x, T* G) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    G[e] = (T)(r[i] * lam[j] - al[i] * x[j]);
+  }
+}
+
+struct StepRec { int ell; double rho; int rebuilt; double margin; };
+struct PhaseRec { int ell; long long iters; int reason; double ne; };
+
+}  // namespace
+
+struct aplicur_ctx {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  MatView A;
+  DBuf<int> colptr, rowidx;
+  DBuf<double> cv64;
+  DBuf<float> cv32;
+  const double* b = nullptr;
+  double mu = 0, delta = 0, eps_cur = 0;
+  int bsize = 0, s = 0, xi = 0, r = 0;
+  int64_t m = 0, n = 0, kmax = 0;
+  aplicur_options opt{};
+  std::vector<int> rp_phases;
+  std::vector<int8_t> rp_rebuild;
+  bool replay = false;
+  // sketch
+  DBuf<int> srows, tptr, ti;
+  DBuf<signed char> ssign, tsgn;
+  DBuf<double> Y, E, W, T, scal;
+  // CUR state
+  int ell = 0, cap = 0;
+  std::vector<int> I, J;
+  DBuf<int> I_d, J_d, Jp_d, Ip_d, colpos, colpos_plus, rowpos;
+  DBuf<double> LU, QR, TR, TC, Cbuf, Rbuf;
+  DBuf<double> Ecol, Xb, U12, L21, Gb, Cp, Zb, P2b, work;
+  DBuf<int> info;
+  LuppWork lw;
+  // preconditioner
+  DBuf<double> Mb, VM, sigma, V64, coef, coef2;
+  DBuf<float> V32;
+  PrecondDev P;
+  double sighat = 1.0;
+  std::vector<double> sig_host;
+  // solve
+  LsqrEngine eng;
+  DBuf<double> x, tmp_m, tmp_n, tmp_n2, lam;
+  double norm_Atb = 0;
+  bool solved = false;
+  std::vector<StepRec> steps;
+  std::vector<PhaseRec> phases;
+  aplicur_stats stats{};
+  std::string err;
+  float setup_ms = 0;
+};
+
+namespace {
+
+void ctx_grow(aplicur_ctx* h, int need) {
+  if (need <= h->cap) return;
+  cudaStream_t st = h->st;
+  const int64_t kmax = h->kmax;
+  int nc = (int)std::min<int64_t>(kmax, std::max<int64_t>(std::max(2 * h->cap, need), 64));
+  const int64_t oc = h->cap;
+  auto regrow_sq = [&](DBuf<double>& B) {
+    DBuf<double> nb;
+    nb.alloc((size_t)nc * nc, st);
+    nb.zero(st);
+    if (oc > 0 && B.p) dcopy2d(st, oc, oc, B.p, oc, nb.p, nc, false);
+    B.swap(nb);
+  };
+  regrow_sq(h->LU);
+  regrow_sq(h->TR);
+  regrow_sq(h->TC);
+  auto regrow_cols = [&](DBuf<double>& B, int64_t rows) {
+    DBuf<double> nb;
+    nb.alloc((size_t)rows * nc, st);
+    if (oc > 0 && B.p)
+      APL_CUDA(cudaMemcpyAsync(nb.p, B.p, (size_t)rows * oc * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+    B.swap(nb);
+  };
+  regrow_cols(h->QR, h->n);
+  if (h->A.fmt == 0) {
+    regrow_cols(h->Cbuf, h->m);
+    DBuf<double> nb;
+    nb.alloc((size_t)nc * h->n, st);
+    if (oc > 0 && h->Rbuf.p) dcopy2d(st, oc, h->n, h->Rbuf.p, oc, nb.p, nc, false);
+    h->Rbuf.swap(nb);
+  }
+  const int bs = h->bsize;
+  h->Xb.alloc((size_t)nc * bs, st);
+  h->U12.alloc((size_t)nc * bs, st);
+  h->L21.alloc((size_t)nc * bs, st);
+  h->Gb.alloc((size_t)nc * bs, st);
+  h->P2b.alloc((size_t)nc * bs, st);
+  h->Zb.alloc((size_t)h->s * nc, st);
+  h->cap = nc;
+  APL_CUDA(cudaStreamSynchronize(st));
+}
+
+void build_csc(aplicur_ctx* h) {
+  const int64_t m = h->m, n = h->n, nnz = h->A.nnz;
+  cudaStream_t st = h->st;
+  std::vector<int> rp(m + 1), ci(nnz);
+  APL_CUDA(cudaMemcpyAsync(rp.data(), h->A.rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (nnz)
+    APL_CUDA(cudaMemcpyAsync(ci.data(), h->A.colidx, nnz * sizeof(int), cudaMemcpyDeviceToHost, st));
+  const size_t vs = h->A.dtype == 0 ? 8 : 4;
+  std::vector<char> vals(nnz * vs), cvals(nnz * vs);
+  if (nnz)
+    APL_CUDA(cudaMemcpyAsync(vals.data(), h->A.vals, nnz * vs, cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaStreamSynchronize(st));
+  APL_REQUIRE(rp[0] == 0 && rp[m] == nnz, "CSR rowptr inconsistent with nnz");
+  std::vector<int> cp(n + 1, 0), ri(nnz);
+  for (int64_t e = 0; e < nnz; ++e) {
+    APL_REQUIRE(ci[e] >= 0 && ci[e] < n, "CSR column index out of range");
+    cp[ci[e] + 1]++;
+  }
+  for (int64_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+  std::vector<int> cur(cp.begin(), cp.end() - 1);
+  for (int64_t i = 0; i < m; ++i) {
+    APL_REQUIRE(rp[i + 1] >= rp[i], "CSR rowptr not monotone");
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int p = cur[ci[e]]++;
+      ri[p] = (int)i;
+      std::memcpy(&cvals[p * vs], &vals[e * vs], vs);
+    }
+  }
+  h->colptr.alloc(n + 1, st);
+  h->rowidx.alloc(std::max<int64_t>(nnz, 1), st);
+  APL_CUDA(cudaMemcpyAsync(h->colptr.p, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (nnz)
+    APL_CUDA(cudaMemcpyAsync(h->rowidx.p, ri.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (h->A.dtype == 0) {
+    h->cv64.alloc(std::max<int64_t>(nnz, 1), st);
+    if (nnz) APL_CUDA(cudaMemcpyAsync(h->cv64.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
+    h->A.cvals = h->cv64.p;
+  } else {
+    h->cv32.alloc(std::max<int64_t>(nnz, 1), st);
+    if (nnz) APL_CUDA(cudaMemcpyAsync(h->cv32.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
+    h->A.cvals = h->cv32.p;
+  }
+  h->A.colptr = h->colptr.p;
+  h->A.rowidx = h->rowidx.p;
+  APL_CUDA(cudaStreamSynchronize(st));
+}
+
+void upload_sketch(aplicur_ctx* h, const std::vector<int>& rows, const std::vector<int8_t>& sg) {
+  const int64_t m = h->m;
+  const int xi = h->xi, s = h->s;
+  cudaStream_t st = h->st;
+  for (size_t e = 0; e < rows.size(); ++e)
+    APL_REQUIRE(rows[e] >= 0 && rows[e] < s, "sketch row index out of range");
+  // transposed lists: rows i of A for each sketch row r, ascending i
+  std::vector<int> tp(s + 1, 0), tl((size_t)m * xi);
+  std::vector<int8_t> ts((size_t)m * xi);
+  for (size_t e = 0; e < rows.size(); ++e) tp[rows[e] + 1]++;
+  for (int r = 0; r < s; ++r) tp[r + 1] += tp[r];
+  std::vector<int> cur(tp.begin(), tp.end() - 1);
+  for (int64_t i = 0; i < m; ++i)
+    for (int k = 0; k < xi; ++k) {
+      const int r = rows[i * xi + k];
+      const int p = cur[r]++;
+      tl[p] = (int)i;
+      ts[p] = sg[i * xi + k];
+    }
+  h->srows.alloc(rows.size(), st);
+  h->ssign.alloc(rows.size(), st);
+  h->tptr.alloc(s + 1, st);
+  h->ti.alloc(rows.size(), st);
+  h->tsgn.alloc(rows.size(), st);
+  APL_CUDA(cudaMemcpyAsync(h->srows.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(h->ssign.p, sg.data(), sg.size(), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(h->tptr.p, tp.data(), (s + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(h->ti.p, tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(h->tsgn.p, ts.data(), ts.size(), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaStreamSynchronize(st));
+}
+
+void reset_cur(aplicur_ctx* h) {
+  cudaStream_t st = h->st;
+  h->ell = 0;
+  h->I.clear();
+  h->J.clear();
+  fill_int(st, h->colpos.p, h->n, -1);
+  fill_int(st, h->colpos_plus.p, h->n, -1);
+  fill_int(st, h->rowpos.p, h->m, -1);
+  APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)h->s * h->n * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
+  if (h->LU.p) h->LU.zero(st);
+  if (h->TR.p) h->TR.zero(st);
+  if (h->TC.p) h->TC.zero(st);
+  h->P = PrecondDev{};
+  h->steps.clear();
+  h->phases.clear();
+}
+
+// One rank step (Part 1 and Part 2 of the driver).  Returns the number of new indices;
+// *exhausted is set when LUPP met a zero pivot before the block was complete.
+int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) {
+  cudaStream_t st = h->st;
+  const int64_t m = h->m, n = h->n;
+  const int s = h->s;
+  const int ell = h->ell;
+  const int kj = (int)std::min<int64_t>(h->bsize, h->kmax - ell);
+  // capacity for the whole step before any ell-sized block is written
+  ctx_grow(h, (int)std::min<int64_t>(h->kmax, ell + std::max(kj, 1)));
+  // ---- column selection: LUPP on E_row^T with the chosen columns zeroed
+  zero_cols_cm(st, h->E.p, s, s, h->J_d.p, ell);
+  std::vector<int> Jp, Ip;
+  double mJ = INFINITY, mI = INFINITY;
+  const int nzJ = lupp_select(st, n, s, h->E.p, s, 1, kj, h->lw, Jp, &mJ);
+  int k = 0;
+  if (nzJ > 0) {
+    APL_CUDA(cudaMemcpyAsync(h->Jp_d.p, Jp.data(), nzJ * sizeof(int), cudaMemcpyHostToDevice, st));
+    set_map(st, h->colpos_plus.p, h->Jp_d.p, nzJ, 0);
+    // ---- column residual E_col = A(:, J+) - C U R(:, J+)
+    if (ell > 0) {
+      gather_cross(st, h->A, h->I_d.p, ell, h->Jp_d.p, nzJ, h->colpos_plus.p, h->U12.p, h->cap);
+      dtrsm(st, true, 'L', false, true, ell, nzJ, h->LU.p, h->cap, h->U12.p, h->cap);
+      dcopy2d(st, ell, nzJ, h->U12.p, h->cap, h->Xb.p, h->cap, false);
+      dtrsm(st, true, 'U', false, false, ell, nzJ, h->LU.p, h->cap, h->Xb.p, h->cap);
+    }
+    if (h->A.fmt == 0) {
+      gather_cols(st, h->A, h->Jp_d.p, nzJ, nullptr, h->Ecol.p, m);
+      if (ell > 0) {
+        dgemm(st, 0, 0, m, nzJ, ell, -1.0, h->Cbuf.p, m, h->Xb.p, h->cap, 1.0, h->Ecol.p, m);
+        zero_rows_cm(st, h->Ecol.p, m, nzJ, h->I_d.p, ell);
+      }
+    } else {
+      ecol_csr(st, h->A, h->colpos.p, h->colpos_plus.p, h->rowpos.p, h->Xb.p, h->cap, nzJ,
+               h->Ecol.p);
+    }
+    // ---- row selection: LUPP on E_col
+    const int nzI = lupp_select(st, m, nzJ, h->Ecol.p, 1, m, nzJ, h->lw, Ip, &mI);
+    k = std::min(nzJ, nzI);
+    if (k < nzJ) {
+      // drop the columns whose rows could not be matched
+      fill_int(st, h->colpos_plus.p, n, -1);
+      set_map(st, h->colpos_plus.p, h->Jp_d.p, k, 0);
+      Jp.resize(k);
+    }
+  }
+  *exhausted = k < std::min<int64_t>(h->bsize, h->kmax - ell);
+  *margin = std::min(mJ, mI);
+  if (k > 0) {
+    const int cap = h->cap;
+    APL_CUDA(cudaMemcpyAsync(h->Ip_d.p, Ip.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
+    // ---- bordered LU of A(I, J): [L11 0; L21 L22][U11 U12; 0 U22]
+    if (ell > 0) {
+      dcopy2d(st, ell, k, h->U12.p, cap, h->LU.p + (int64_t)ell * cap, cap, false);
+      if (h->A.fmt == 0) gather_rows_cm(st, h->Cbuf.p, m, ell, h->Ip_d.p, k, h->L21.p, k);
+      else gather_cross(st, h->A, h->Ip_d.p, k, h->J_d.p, ell, h->colpos.p, h->L21.p, k);
+      dtrsm(st, false, 'U', false, false, k, ell, h->LU.p, cap, h->L21.p, k);
+      dcopy2d(st, k, ell, h->L21.p, k, h->LU.p + ell, cap, false);
+    }
+    // the pivot rows of the E_col elimination hold L22 \ U22
+    gather_rows_cm(st, h->Ecol.p, m, k, h->Ip_d.p, k, h->LU.p + ell + (int64_t)ell * cap, cap);
+    // ---- Gram of the new columns for T_C (before the maps change)
+    APL_CUDA(cudaMemcpyAsync(h->J_d.p + ell, Jp.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
+    APL_CUDA(cudaMemcpyAsync(h->I_d.p + ell, Ip.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
+    const int ln = ell + k;
+    if (h->A.fmt == 0) {
+      gather_cols(st, h->A, h->Jp_d.p, k, nullptr, h->Cbuf.p + (int64_t)ell * m, m);
+      append_rows(st, h->A, h->Ip_d.p, k, h->Rbuf.p, cap, ell);
+      dgemm(st, 1, 0, ln, k, m, 1.0, h->Cbuf.p, m, h->Cbuf.p + (int64_t)ell * m, m, 0.0, h->Gb.p, cap);
+    } else {
+      gather_cols(st, h->A, h->Jp_d.p, k, h->colpos_plus.p, h->Cp.p, m);
+      gram_csr(st, h->A, h->J_d.p, ln, h->Cp.p, k, h->Gb.p, cap);
+    }
+    set_map(st, h->rowpos.p, h->Ip_d.p, k, ell);
+    set_map(st, h->colpos.p, h->Jp_d.p, k, ell);
+    fill_int(st, h->colpos_plus.p, n, -1);
+    // ---- T_C: bordered Cholesky of C^T C
+    if (ell > 0) {
+      dtrsm(st, true, 'U', true, false, ell, k, h->TC.p, cap, h->Gb.p, cap);
+      dcopy2d(st, ell, k, h->Gb.p, cap, h->TC.p + (int64_t)ell * cap, cap, false);
+      dgemm(st, 1, 0, k, k, ell, -1.0, h->Gb.p, cap, h->Gb.p, cap, 1.0, h->Gb.p + ell, cap);
+    }
+    double* T22 = h->TC.p + ell + (int64_t)ell * cap;
+    dcopy2d(st, k, k, h->Gb.p + ell, cap, T22, cap, false);
+    dpotrf_upper(st, k, T22, cap, h->info.p);
+    int info = 0;
+    APL_CUDA(cudaMemcpyAsync(&info, h->info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    APL_CUDA(cudaStreamSynchronize(st));
+    if (info) throw Error(ST_EBREAKDOWN, "Cholesky of C^T C met a non-positive pivot");
+    // ---- augmentQR(Q_R, T_R, A(I+, :)^T) with two Gram-Schmidt passes
+    double* Cn = h->QR.p + (int64_t)ell * n;
+    gather_rows_T(st, h->A, h->Ip_d.p, k, Cn, n);
+    if (ell > 0) {
+      double* P1 = h->TR.p + (int64_t)ell * cap;
+      dgemm(st, 1, 0, ell, k, n, 1.0, h->QR.p, n, Cn, n, 0.0, P1, cap);
+      dgemm(st, 0, 0, n, k, ell, -1.0, h->QR.p, n, P1, cap, 1.0, Cn, n);
+      dgemm(st, 1, 0, ell, k, n, 1.0, h->QR.p, n, Cn, n, 0.0, h->P2b.p, cap);
+      dgemm(st, 0, 0, n, k, ell, -1.0, h->QR.p, n, h->P2b.p, cap, 1.0, Cn, n);
+      add2d_kernel<<<(unsigned)cdiv((int64_t)ell * k, 256), 256, 0, st>>>(ell, k, h->P2b.p, cap, P1, cap);
+      APL_LAUNCH_CHECK();
+    }
+    h->work.alloc((size_t)2 * k * k + 16, st);
+    if (!cholqr2(st, n, k, Cn, n, h->TR.p + ell + (int64_t)ell * cap, cap, h->work.p, h->info.p))
+      throw Error(ST_EBREAKDOWN, "Cholesky QR of the new rows of R met a non-positive pivot");
+    h->I.insert(h->I.end(), Ip.begin(), Ip.begin() + k);
+    h->J.insert(h->J.end(), Jp.begin(), Jp.begin() + k);
+    h->ell = ln;
+  }
+  // ---- sketched residual E_row = Y - Y(:, J) A(I, J)^{-1} A(I, :)
+  const int L = h->ell;
+  if (L > 0) {
+    const int cap = h->cap;
+    dgather_cols(st, s, h->Y.p, s, h->J_d.p, L, h->Zb.p, s);
+    dtrsm(st, false, 'U', false, false, s, L, h->LU.p, cap, h->Zb.p, s);
+    dtrsm(st, false, 'L', false, true, s, L, h->LU.p, cap, h->Zb.p, s);
+    if (h->A.fmt == 0) {
+      APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)s * n * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+      dgemm(st, 0, 0, s, n, L, -1.0, h->Zb.p, s, h->Rbuf.p, cap, 1.0, h->E.p, s);
+    } else {
+      erow_csr(st, h->A, h->rowpos.p, h->Zb.p, s, h->Y.p, h->E.p);
+    }
+  } else {
+    APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)s * n * sizeof(double),
+                             cudaMemcpyDeviceToDevice, st));
+  }
+  // ---- rho = 10 sqrt(2/pi) max_i ||E_row w_i||  (Eq. 2normestimate)
+  dgemm(st, 0, 0, s, h->r, n, 1.0, h->E.p, s, h->W.p, n, 0.0, h->T.p, s);
+  colnorm_max(st, h->T.p, s, h->r, 10.0 * std::sqrt(2.0 / M_PI), h->scal.p);
+  APL_CUDA(cudaMemcpyAsync(rho_out, h->scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaStreamSynchronize(st));
+  return k;
+}
+
+// CURPreconditioner Part 2: M = T_C U T_R^T, SVD, Vhat = Q_R V_M, coefficients.
+void build_preconditioner(aplicur_ctx* h) {
+  cudaStream_t st = h->st;
+  const int L = h->ell, cap = h->cap;
+  const int64_t n = h->n;
+  h->Mb.alloc((size_t)L * L, st);
+  h->VM.alloc((size_t)L * L, st);
+  h->sigma.alloc(L, st);
+  h->work.alloc((size_t)L * L + L + 16, st);
+  double* X = h->work.p;
+  // X = A(I,J)^{-1} T_R^T
+  dcopy2d(st, L, L, h->TR.p, cap, X, L, true);
+  dtrsm(st, true, 'L', false, true, L, L, h->LU.p, cap, X, L);
+  dtrsm(st, true, 'U', false, false, L, L, h->LU.p, cap, X, L);
+  dgemm(st, 0, 0, L, L, L, 1.0, h->TC.p, cap, X, L, 0.0, h->Mb.p, L);
+  jacobi_svd(st, L, h->Mb.p, L, h->VM.p, L, h->sigma.p, h->work.p, h->info.p);
+  // Vhat^T (L x n col-major) = V_M^T Q_R^T  ->  Vhat row-major n x L
+  h->V64.alloc((size_t)n * L, st);
+  dgemm(st, 1, 1, L, n, L, 1.0, h->VM.p, L, h->QR.p, n, 0.0, h->V64.p, L);
+  h->sig_host.resize(L);
+  APL_CUDA(cudaMemcpyAsync(h->sig_host.data(), h->sigma.p, L * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaStreamSynchronize(st));
+  const double d2 = h->delta * h->delta;
+  const double sl = h->sig_host[L - 1];
+  h->sighat = std::sqrt(sl * sl + d2);
+  std::vector<double> c1(L), c2(L);
+  for (int k = 0; k < L; ++k) {
+    const double lam2 = h->sig_host[k] * h->sig_host[k] + d2;
+    const double lam = std::sqrt(lam2);
+    c1[k] = h->sighat / lam - 1.0;
+    c2[k] = (h->sighat * h->sighat) / lam2 - 1.0;
+  }
+  h->coef.alloc(L, st);
+  h->coef2.alloc(L, st);
+  APL_CUDA(cudaMemcpyAsync(h->coef.p, c1.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(h->coef2.p, c2.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  PrecondDev P;
+  P.ell = L;
+  P.ldv = L;
+  P.coef = h->coef.p;
+  P.coef2 = h->coef2.p;
+  P.normP = std::sqrt(h->sig_host[0] * h->sig_host[0] + d2) / h->sighat;
+  P.sig_ell = sl;
+  if (h->opt.precision == APLICUR_PREC_MIXED) {
+    h->V32.alloc((size_t)n * L, st);
+    to_f32_kernel<<<(unsigned)cdiv(n * L, 256), 256, 0, st>>>(n * L, h->V64.p, h->V32.p);
+    APL_LAUNCH_CHECK();
+    P.fp32 = 1;
+    P.V32 = h->V32.p;
+  } else {
+    P.V64 = h->V64.p;
+  }
+  h->P = P;
+  APL_CUDA(cudaStreamSynchronize(st));
+}
+
+double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fixed, long long* it,
+                 int* reason) {
+  PhaseArgs a;
+  a.rhs_top = h->b;
+  a.x = h->x.p;
+  a.eps = h->opt.eps_lsqr;
+  a.nu = nu;
+  a.tol = h->replay ? 0.0 : tol;
+  a.norm_ref = h->norm_Atb;
+  a.mu = h->mu;
+  a.fixed_len = fixed;
+  a.maxit = maxit;
+  a.check_gap = h->opt.check_gap;
+  PhaseResult r = h->eng.run_phase(h->P, a);
+  const double ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
+  h->phases.push_back(PhaseRec{h->P.ell, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
+  *it = r.iters;
+  *reason = r.reason;
+  return ne;
+}
+
+int do_solve(aplicur_ctx* h, double tol, long long maxit) {
+  cudaStream_t st = h->st;
+  reset_cur(h);
+  h->x.zero(st);
+  long long total = 0;
+  size_t rp_ph = 0, rp_rb = 0;
+  auto next_fixed = [&]() -> int {
+    if (!h->replay) return -1;
+    return rp_ph < h->rp_phases.size() ? h->rp_phases[rp_ph++] : 0;
+  };
+  double ne = INFINITY;
+  auto finish = [&](double ne_) {
+    h->stats.iters = total;
+    h->stats.ell = h->ell;
+    h->stats.nphases = (int)h->phases.size();
+    h->stats.nsteps = (int)h->steps.size();
+    h->stats.ne_res = ne_;
+    h->stats.converged = ne_ <= tol ? 1 : 0;
+    h->solved = true;
+    return (ne_ <= tol || h->replay) ? ST_OK : ST_ENOTCONV;
+  };
+  if (h->norm_Atb == 0.0) return finish(0.0);
+  double d_cur = INFINITY;
+  while (true) {
+    double rho = 0, margin = INFINITY;
+    bool exhausted = false;
+    rank_step(h, &rho, &exhausted, &margin);
+    h->stats.rho = rho;
+    const bool full = h->ell >= h->kmax;
+    const double rho_eff = exhausted ? 0.0 : rho;
+    const bool last = rho_eff <= h->eps_cur || full || exhausted;
+    bool rebuild;
+    if (h->replay) {
+      rebuild = rp_rb < h->rp_rebuild.size() ? h->rp_rebuild[rp_rb++] != 0 : last;
+    } else {
+      const double gap = rho_eff - h->eps_cur;
+      rebuild = last || (gap > 0.0 && d_cur / gap >= h->opt.nu_prec);
+    }
+    h->steps.push_back(StepRec{h->ell, rho, rebuild ? 1 : 0, margin});
+    if (rebuild && h->ell > 0) {
+      build_preconditioner(h);
+      long long it = 0;
+      int reason = 0;
+      ne = run_phase(h, last ? INFINITY : h->opt.nu_lsqr, tol, std::max(0LL, maxit - total),
+                     next_fixed(), &it, &reason);
+      total += it;
+      if (!h->replay && ne <= tol) return finish(ne);
+      d_cur = rho_eff - h->eps_cur;
+    }
+    if (last) break;
+    if (total >= maxit) return finish(h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb));
+  }
+  if (!h->phases.empty()) ne = h->phases.back().ne;
+  else ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
+  int extra = 0;
+  while ((h->replay && rp_ph < h->rp_phases.size()) ||
+         (!h->replay && ne > tol && total < maxit && extra < h->opt.max_extra_phases)) {
+    const double prev = ne;
+    long long it = 0;
+    int reason = 0;
+    ne = run_phase(h, INFINITY, tol, std::max(0LL, maxit - total), next_fixed(), &it, &reason);
+    total += it;
+    ++extra;
+    if (!h->replay && (it == 0 || ne > 0.5 * prev)) break;
+  }
+  return finish(ne);
+}
+
+aplicur_status fail(aplicur_ctx* h, const Error& e) {
+  if (h) h->err = e.what();
+  return (aplicur_status)e.code;
+}
+
+template <typename F>
+aplicur_status guarded(aplicur_ctx* h, F&& f) {
+  try {
+    return (aplicur_status)f();
+  } catch (const Error& e) {
+    return fail(h, e);
+  } catch (const std::exception& e) {
+    if (h) h->err = e.what();
+    return APLICUR_ECUDA;
+  } catch (...) {
+    if (h) h->err = "unknown failure";
+    return APLICUR_ECUDA;
+  }
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+void aplicur_options_default(aplicur_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->seed = 1;
+  o->eps_cur_factor = 30.0;
+  o->nu_prec = 10.0;
+  o->nu_lsqr = 100.0;
+  o->eps_lsqr = 1e-10;
+  o->xi = 8;
+  o->normest_r = 10;
+  o->check_gap = 10;
+  o->max_extra_phases = 8;
+  o->precision = APLICUR_PREC_FP64;
+  o->graph_iters = 16;
+}
+
+static thread_local std::string g_create_err;
+
+aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, const double* b,
+                              double mu, int32_t sketch_dim, const aplicur_options* opt,
+                              void* stream) {
+  if (!out || !A || !b) { g_create_err = "null argument"; return APLICUR_EINVAL; }
+  *out = nullptr;
+  aplicur_ctx* h = new (std::nothrow) aplicur_ctx();
+  if (!h) return APLICUR_ENOMEM;
+  aplicur_status stt = guarded(h, [&]() -> int {
+    APL_REQUIRE(A->format == APLICUR_DENSE_ROWMAJOR || A->format == APLICUR_CSR, "bad format");
+    APL_REQUIRE(A->dtype == APLICUR_F64 || A->dtype == APLICUR_F32, "bad dtype");
+    APL_REQUIRE(A->m >= 1 && A->n >= 1 && A->m >= A->n, "need m >= n >= 1");
+    APL_REQUIRE(A->m < (1LL << 31) && A->n < (1LL << 31), "dimensions exceed int32 indexing");
+    APL_REQUIRE(A->values != nullptr, "A values NULL");
+    APL_REQUIRE(mu >= 0.0 && std::isfinite(mu), "mu must be finite and >= 0");
+    APL_REQUIRE(sketch_dim >= 1 && sketch_dim <= A->n, "need 1 <= sketch_dim <= n");
+    if (A->format == APLICUR_DENSE_ROWMAJOR) APL_REQUIRE(A->ld >= A->n, "ld < n");
+    else APL_REQUIRE(A->rowptr && A->colidx && A->nnz >= 0 && A->nnz < (1LL << 31), "bad CSR");
+    if (opt) h->opt = *opt; else aplicur_options_default(&h->opt);
+    if (h->opt.replay_phases && h->opt.replay_nphases > 0)
+      h->rp_phases.assign(h->opt.replay_phases, h->opt.replay_phases + h->opt.replay_nphases);
+    else h->opt.replay_nphases = 0;
+    if (h->opt.replay_rebuild && h->opt.replay_nsteps > 0)
+      h->rp_rebuild.assign(h->opt.replay_rebuild, h->opt.replay_rebuild + h->opt.replay_nsteps);
+    else h->opt.replay_nsteps = 0;
+    APL_REQUIRE(h->opt.xi >= 1 && h->opt.normest_r >= 1 && h->opt.check_gap >= 1, "bad options");
+    APL_REQUIRE(h->opt.graph_iters >= 0 && h->opt.graph_iters <= 4096, "bad graph_iters");
+    if (stream) h->st = (cudaStream_t)stream;
+    else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
+    cudaStream_t st = h->st;
+    h->m = A->m; h->n = A->n; h->kmax = std::min(h->m, h->n);
+    h->A.fmt = A->format; h->A.dtype = A->dtype; h->A.m = A->m; h->A.n = A->n; h->A.ld = A->ld;
+    h->A.nnz = A->format == APLICUR_CSR ? A->nnz : A->m * A->n;
+    h->A.vals = A->values; h->A.rowptr = A->rowptr; h->A.colidx = A->colidx;
+    h->b = b;
+    h->mu = mu;
+    h->delta = std::sqrt(mu);
+    h->eps_cur = h->opt.eps_cur_factor * h->delta;
+    h->bsize = sketch_dim;
+    h->s = (11 * sketch_dim + 9) / 10;
+    h->xi = std::min(h->opt.xi, h->s);
+    h->r = h->opt.normest_r;
+    if (h->A.fmt == 1) build_csc(h);
+    // sketch and norm-estimate draws
+    std::vector<int> rows;
+    std::vector<int8_t> sg;
+    if (h->opt.sketch_rows && h->opt.sketch_signs) {
+      rows.assign(h->opt.sketch_rows, h->opt.sketch_rows + h->m * h->xi);
+      sg.assign(h->opt.sketch_signs, h->opt.sketch_signs + h->m * h->xi);
+    } else {
+      draw_sketch(h->opt.seed, h->s, h->m, h->xi, rows, sg);
+    }
+    upload_sketch(h, rows, sg);
+    std::vector<double> W;
+    if (h->opt.normest_w) W.assign(h->opt.normest_w, h->opt.normest_w + h->n * h->r);
+    else draw_gaussian(h->opt.seed, h->n, h->r, W);
+    h->W.alloc(W.size(), st);
+    APL_CUDA(cudaMemcpyAsync(h->W.p, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    h->opt.sketch_rows = nullptr; h->opt.sketch_signs = nullptr; h->opt.normest_w = nullptr;
+    h->opt.replay_phases = nullptr; h->opt.replay_rebuild = nullptr;
+    // buffers
+    const int64_t m = h->m, n = h->n;
+    h->Y.alloc((size_t)h->s * n, st);
+    h->E.alloc((size_t)h->s * n, st);
+    h->T.alloc((size_t)h->s * h->r, st);
+    h->scal.alloc(4, st);
+    h->info.alloc(4, st);
+    h->I_d.alloc(h->kmax, st); h->J_d.alloc(h->kmax, st);
+    h->Jp_d.alloc(h->bsize, st); h->Ip_d.alloc(h->bsize, st);
+    h->colpos.alloc(n, st); h->colpos_plus.alloc(n, st); h->rowpos.alloc(m, st);
+    h->Ecol.alloc((size_t)m * h->bsize, st);
+    if (h->A.fmt == 1) h->Cp.alloc((size_t)m * h->bsize, st);
+    h->x.alloc(n, st); h->tmp_m.alloc(m, st); h->tmp_n.alloc(n, st); h->tmp_n2.alloc(n, st);
+    h->lam.alloc(n, st);
+    // the one-time sketch Y = S A
+    cudaEvent_t e0, e1;
+    APL_CUDA(cudaEventCreate(&e0));
+    APL_CUDA(cudaEventCreate(&e1));
+    APL_CUDA(cudaEventRecord(e0, st));
+    sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
+           1.0 / std::sqrt((double)h->xi), h->Y.p);
+    APL_CUDA(cudaEventRecord(e1, st));
+    APL_CUDA(cudaEventSynchronize(e1));
+    APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->eng.setup(st, h->A, h->opt.precision == APLICUR_PREC_MIXED ? 1 : 0, h->opt.graph_iters);
+    h->eng.set_profile(h->opt.profile != 0);
+    // ||A^T b|| in FP64
+    h->eng.matvec(1, b, h->tmp_n.p, 1.0, 0.0, true);
+    h->norm_Atb = h->eng.norm2(h->tmp_n.p, n);
+    h->stats.time_setup_ms = h->setup_ms;
+    return ST_OK;
+  });
+  if (stt != APLICUR_OK) {
+    g_create_err = h->err;
+    aplicur_destroy(h);
+    return stt;
+  }
+  *out = h;
+  return APLICUR_OK;
+}
+
+static void load_replay(aplicur_ctx* h) {
+  h->replay = h->opt.replay_nphases > 0 || h->opt.replay_nsteps > 0;
+}
+
+aplicur_status aplicur_solve(aplicur_handle h, double tol, int64_t maxit, double* x_out) {
+  if (!h) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    APL_REQUIRE(x_out != nullptr, "x_out NULL");
+    APL_REQUIRE(tol >= 0.0 && maxit >= 0, "tol and maxit must be >= 0");
+    load_replay(h);
+    auto t0 = std::chrono::steady_clock::now();
+    const int rc = do_solve(h, tol, maxit);
+    APL_CUDA(cudaMemcpyAsync(x_out, h->x.p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    APL_CUDA(cudaStreamSynchronize(h->st));
+    h->stats.time_solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+  });
+}
+
+aplicur_status aplicur_set_replay(aplicur_handle h, int32_t nph, const int32_t* ph, int32_t nst,
+                                  const int8_t* rb) {
+  if (!h) return APLICUR_EINVAL;
+  h->rp_phases.assign(ph, ph + (ph ? nph : 0));
+  h->rp_rebuild.assign(rb, rb + (rb ? nst : 0));
+  h->opt.replay_nphases = nph;
+  h->opt.replay_nsteps = nst;
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, double* x_out) {
+  if (!h) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    APL_REQUIRE(x_out != nullptr, "x_out NULL");
+    auto t0 = std::chrono::steady_clock::now();
+    h->x.zero(h->st);
+    h->phases.clear();
+    PrecondDev I;
+    PhaseArgs a;
+    a.rhs_top = h->b;
+    a.x = h->x.p;
+    a.eps = 0.0;
+    a.nu = INFINITY;
+    a.tol = tol;
+    a.norm_ref = h->norm_Atb;
+    a.mu = h->mu;
+    a.maxit = maxit;
+    a.check_gap = h->opt.check_gap;
+    long long total = 0;
+    double ne = INFINITY;
+    for (int rep = 0; rep <= h->opt.max_extra_phases && total < maxit; ++rep) {
+      a.maxit = maxit - total;
+      PhaseResult r = h->eng.run_phase(I, a);
+      total += r.iters;
+      ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
+      h->phases.push_back(PhaseRec{0, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
+      if (r.reason != R_DRIFT || ne <= tol) break;
+    }
+    h->stats.iters = total;
+    h->stats.ne_res = ne;
+    h->stats.converged = ne <= tol;
+    h->stats.nphases = (int)h->phases.size();
+    APL_CUDA(cudaMemcpyAsync(x_out, h->x.p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    APL_CUDA(cudaStreamSynchronize(h->st));
+    h->stats.time_solve_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return ne <= tol ? ST_OK : ST_ENOTCONV;
+  });
+}
+
+aplicur_status aplicur_backward(aplicur_handle h, const double* grad_x, double tol, int64_t maxit,
+                                double* grad_b, double* grad_mu, void* grad_A) {
+  if (!h) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    APL_REQUIRE(grad_x != nullptr, "grad_x NULL");
+    APL_REQUIRE(h->solved, "aplicur_backward needs a previous aplicur_solve");
+    APL_REQUIRE(h->mu > 0.0, "aplicur_backward needs mu > 0");
+    APL_REQUIRE(!grad_A || h->A.fmt == 0, "grad_A is only produced for dense A");
+    cudaStream_t st = h->st;
+    const int64_t m = h->m, n = h->n;
+    // rhs = [0; g / delta];  A_delta^T rhs = g
+    scale_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, grad_x, 1.0 / h->delta, h->tmp_n2.p);
+    APL_LAUNCH_CHECK();
+    APL_CUDA(cudaMemsetAsync(h->tmp_m.p, 0, m * sizeof(double), st));
+    const double gnorm = h->eng.norm2(grad_x, n);
+    h->lam.zero(st);
+    double ne = 0.0;
+    if (gnorm > 0.0) {
+      PhaseArgs a;
+      a.rhs_top = h->tmp_m.p;
+      a.rhs_bot = h->tmp_n2.p;
+      a.x = h->lam.p;
+      a.eps = h->opt.eps_lsqr;
+      a.nu = INFINITY;
+      a.tol = tol;
+      a.norm_ref = gnorm;
+      a.mu = h->mu;
+      a.check_gap = h->opt.check_gap;
+      long long total = 0;
+      ne = INFINITY;
+      for (int rep = 0; rep <= h->opt.max_extra_phases && total < maxit; ++rep) {
+        a.maxit = maxit - total;
+        PhaseResult r = h->eng.run_phase(h->P, a);
+        total += r.iters;
+        const double prev = ne;
+        ne = h->eng.ne_residual(h->tmp_m.p, h->tmp_n2.p, h->lam.p, h->delta, gnorm);
+        if (ne <= tol || r.iters == 0 || ne > 0.5 * prev) break;
+      }
+    }
+    // grad_b = A lambda ; grad_mu = -lambda^T x ; grad_A = r lambda^T - (A lambda) x^T
+    h->eng.matvec(0, h->lam.p, h->tmp_m.p, 1.0, 0.0, true);
+    if (grad_b)
+      APL_CUDA(cudaMemcpyAsync(grad_b, h->tmp_m.p, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (grad_mu) {
+      dot_kernel<<<1, 256, 0, st>>>(n, h->lam.p, h->x.p, h->scal.p);
+      APL_LAUNCH_CHECK();
+      double v = 0.0;
+      APL_CUDA(cudaMemcpyAsync(&v, h->scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+      APL_CUDA(cudaStreamSynchronize(st));
+      *grad_mu = -v;
+    }
+    if (grad_A) {
+      DBuf<double> r;
+      r.alloc(m, st);
+      APL_CUDA(cudaMemcpyAsync(r.p, h->b, m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      h->eng.matvec(0, h->x.p, r.p, -1.0, 1.0, true);
+      const unsigned grid = (unsigned)std::min<int64_t>(cdiv(m * n, 256), 152 * 16);
+      if (h->A.dtype == 0)
+        rank2_kernel<double><<<grid, 256, 0, st>>>(m, n, r.p, h->lam.p, h->tmp_m.p, h->x.p,
+                                                   (double*)grad_A);
+      else
+        rank2_kernel<float><<<grid, 256, 0, st>>>(m, n, r.p, h->lam.p, h->tmp_m.p, h->x.p,
+                                                  (float*)grad_A);
+      APL_LAUNCH_CHECK();
+    }
+    APL_CUDA(cudaStreamSynchronize(st));
+    return ne <= tol ? ST_OK : ST_ENOTCONV;
+  });
+}
+
+aplicur_status aplicur_get_indices(aplicur_handle h, int32_t* I, int32_t* J, int32_t* ell) {
+  if (!h) return APLICUR_EINVAL;
+  if (ell) *ell = h->ell;
+  if (I && h->ell) std::memcpy(I, h->I.data(), h->ell * sizeof(int));
+  if (J && h->ell) std::memcpy(J, h->J.data(), h->ell * sizeof(int));
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_get_sketch(aplicur_handle h, double* y_out, int32_t* s_out) {
+  if (!h) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    if (s_out) *s_out = h->s;
+    if (y_out) {
+      APL_CUDA(cudaMemcpyAsync(y_out, h->Y.p, (size_t)h->s * h->n * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->st));
+      APL_CUDA(cudaStreamSynchronize(h->st));
+    }
+    return ST_OK;
+  });
+}
+
+aplicur_status aplicur_get_stats(aplicur_handle h, aplicur_stats* st) {
+  if (!h || !st) return APLICUR_EINVAL;
+  *st = h->stats;
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_get_phase(aplicur_handle h, int32_t k, int32_t* ell, int64_t* iters,
+                                 int32_t* reason, double* ne_res) {
+  if (!h || k < 0 || k >= (int)h->phases.size()) return APLICUR_EINVAL;
+  const PhaseRec& p = h->phases[k];
+  if (ell) *ell = p.ell;
+  if (iters) *iters = p.iters;
+  if (reason) *reason = p.reason;
+  if (ne_res) *ne_res = p.ne;
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_get_step(aplicur_handle h, int32_t k, int32_t* ell, double* rho,
+                                int32_t* rebuilt, double* margin) {
+  if (!h || k < 0 || k >= (int)h->steps.size()) return APLICUR_EINVAL;
+  const StepRec& s = h->steps[k];
+  if (ell) *ell = s.ell;
+  if (rho) *rho = s.rho;
+  if (rebuilt) *rebuilt = s.rebuilt;
+  if (margin) *margin = s.margin;
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_get_preconditioner(aplicur_handle h, int32_t* ell, double* sigma,
+                                          double* sighat) {
+  if (!h) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    if (ell) *ell = h->P.ell;
+    if (sighat) *sighat = h->P.ell ? h->sighat : 1.0;
+    if (sigma && h->P.ell) {
+      APL_CUDA(cudaMemcpyAsync(sigma, h->sigma.p, h->P.ell * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->st));
+      APL_CUDA(cudaStreamSynchronize(h->st));
+    }
+    return ST_OK;
+  });
+}
+
+aplicur_status aplicur_apply_preconditioner(aplicur_handle h, const double* w, double* out) {
+  if (!h || !w || !out) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    h->eng.apply_precond(h->P, w, out, nullptr);
+    APL_CUDA(cudaStreamSynchronize(h->st));
+    return ST_OK;
+  });
+}
+
+aplicur_status aplicur_matvec(aplicur_handle h, int32_t trans, const double* x, double* y) {
+  if (!h || !x || !y) return APLICUR_EINVAL;
+  return guarded(h, [&]() -> int {
+    h->eng.matvec(trans ? 1 : 0, x, y, 1.0, 0.0, h->opt.precision != APLICUR_PREC_MIXED);
+    APL_CUDA(cudaStreamSynchronize(h->st));
+    return ST_OK;
+  });
+}
+
+aplicur_status aplicur_get_profile(aplicur_handle h, aplicur_profile* out) {
+  if (!h || !out) return APLICUR_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    out->ms[k] = h->eng.prof.ms[k];
+    out->launches[k] = h->eng.prof.launches[k];
+    out->bytes[k] = h->eng.prof.bytes_total[k];
+  }
+  out->kernel_launches = launch_count();
+  return APLICUR_OK;
+}
+
+int64_t aplicur_launch_count(void) { return launch_count(); }
+
+aplicur_status aplicur_reset_profile(aplicur_handle h) {
+  if (!h) return APLICUR_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    h->eng.prof.ms[k] = 0;
+    h->eng.prof.launches[k] = 0;
+    h->eng.prof.bytes_total[k] = 0;
+  }
+  return APLICUR_OK;
+}
+
+const char* aplicur_last_error(aplicur_handle h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+const char* aplicur_status_string(aplicur_status s) {
+  switch (s) {
+    case APLICUR_OK: return "ok";
+    case APLICUR_EINVAL: return "invalid argument";
+    case APLICUR_ENOMEM: return "out of memory";
+    case APLICUR_ECUDA: return "CUDA error";
+    case APLICUR_ENOTCONV: return "not converged within maxit";
+    case APLICUR_EBREAKDOWN: return "factorisation breakdown";
+    case APLICUR_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+void aplicur_destroy(aplicur_handle h) {
+  if (!h) return;
+  cudaStream_t st = h->st;
+  bool own = h->own_stream;
+  if (st) cudaStreamSynchronize(st);
+  delete h;
+  if (own && st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Shared helpers of the APLICUR CUDA library: error handling, device buffers,
+// deterministic reductions and the "last block finishes" pattern.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace apl {
+
+// Internal failures are C++ exceptions; the C ABI layer converts them to status codes.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOTCONV = 4,
+       ST_EBREAKDOWN = 5, ST_ETIMEOUT = 6 };
+
+#define APL_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::apl::Error(e_ == cudaErrorMemoryAllocation ? ::apl::ST_ENOMEM : ::apl::ST_ECUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+// Kernel launch accounting: every launch site calls APL_LAUNCH_CHECK; launches made
+// while a graph is being captured are counted when the graph is replayed instead.
+void note_launch();
+void add_launches(long long n);
+long long launch_count();
+struct CaptureScope {
+  CaptureScope();
+  ~CaptureScope();
+};
+
+#define APL_LAUNCH_CHECK()            \
+  do {                                \
+    APL_CUDA(cudaGetLastError());     \
+    ::apl::note_launch();             \
+  } while (0)
+
+#define APL_REQUIRE(cond, msg)                                         \
+  do {                                                                 \
+    if (!(cond)) throw ::apl::Error(::apl::ST_EINVAL, (msg));          \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device buffer owned by the library (stream-ordered allocation).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t st = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    n = 0;
+  }
+  // (Re)allocate to hold `count` elements; contents are not kept.
+  void alloc(size_t count, cudaStream_t s) {
+    st = s;
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    APL_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), s));
+    n = count;
+  }
+  void zero(cudaStream_t s) {
+    if (p && n) APL_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  T* get() const { return p; }
+  void swap(DBuf& o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    std::swap(st, o.st);
+  }
+};
+
+// ---- device reductions (fixed order -> bitwise reproducible) -------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum; result valid in thread 0.  `sh` needs blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = (lane < nw) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Returns true in every thread of the block that finished last among all blocks of
+// the grid.  Writers must have stored their partial results before calling.
+// The counter is reset by the last block so graphs can replay the kernel.
+__device__ __forceinline__ bool last_block_done(unsigned int* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int total = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int t = atomicAdd(counter, 1u);
+    is_last = (t == total - 1);
+    if (is_last) *counter = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// Sum of n partials in fixed order by one block; result in thread 0.
+__device__ __forceinline__ double block_sum_partials(const double* part, int n, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+  return block_sum(v, sh);
+}
+
+template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+}  // namespace apl

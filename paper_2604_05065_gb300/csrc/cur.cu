@@ -1,0 +1,575 @@
+// Sketch and CUR-refinement kernels.
+#include <climits>
+
+#include "cur.cuh"
+
+namespace apl {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ double ld_val(const void* p, int64_t i) {
+  return (double)(reinterpret_cast<const T*>(p)[i]);
+}
+
+// ---- sketch ---------------------------------------------------------------------------
+
+// Dense: thread (r, j) sums the rows of A listed for sketch row r, ascending.
+template <typename T>
+__global__ void sketch_dense_kernel(int64_t n, int64_t ld, const T* __restrict__ A, int s,
+                                    const int* __restrict__ tptr, const int* __restrict__ ti,
+                                    const signed char* __restrict__ tsgn, double scale,
+                                    double* __restrict__ Y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= n) return;
+  double acc = 0.0;
+  const int e0 = tptr[r], e1 = tptr[r + 1];
+  for (int e = e0; e < e1; ++e) {
+    const double a = (double)A[(int64_t)ti[e] * ld + j];
+    acc = tsgn[e] > 0 ? acc + a : acc - a;
+  }
+  Y[r + j * (int64_t)s] = acc * scale;
+}
+
+// CSR: thread (r, j) walks column j (ascending rows) and keeps entries whose row maps to r.
+template <typename T>
+__global__ void sketch_csc_kernel(int64_t n, const int* __restrict__ colptr,
+                                  const int* __restrict__ rowidx, const T* __restrict__ cvals,
+                                  int s, int xi, const int* __restrict__ srows,
+                                  const signed char* __restrict__ ssign, double scale,
+                                  double* __restrict__ Y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int e = colptr[j]; e < colptr[j + 1]; ++e) {
+    const int64_t i = rowidx[e];
+    const int* rr = srows + i * xi;
+    for (int k = 0; k < xi; ++k) {
+      if (rr[k] == r) {
+        const double a = (double)cvals[e];
+        acc = ssign[i * xi + k] > 0 ? acc + a : acc - a;
+      }
+    }
+  }
+  Y[r + j * (int64_t)s] = acc * scale;
+}
+
+// ---- LUPP -----------------------------------------------------------------------------
+
+struct Cand {
+  double v;   // |value| of the best candidate, -1 if none
+  int pos;    // its position in the current row order
+  double sec; // second-best |value|, -1 if none
+};
+
+__device__ __forceinline__ bool cand_better(double v1, int p1, double v2, int p2) {
+  return v1 > v2 || (v1 == v2 && p1 < p2);
+}
+
+__device__ __forceinline__ Cand cand_merge(Cand a, Cand b) {
+  Cand r;
+  if (cand_better(a.v, a.pos, b.v, b.pos)) {
+    r.v = a.v; r.pos = a.pos; r.sec = fmax(a.sec, b.v);
+  } else {
+    r.v = b.v; r.pos = b.pos; r.sec = fmax(b.sec, a.v);
+  }
+  return r;
+}
+
+__device__ __forceinline__ Cand warp_cand(Cand c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Cand d;
+    d.v = __shfl_down_sync(0xffffffffu, c.v, o);
+    d.pos = __shfl_down_sync(0xffffffffu, c.pos, o);
+    d.sec = __shfl_down_sync(0xffffffffu, c.sec, o);
+    c = cand_merge(c, d);
+  }
+  return c;
+}
+
+__device__ Cand block_cand(Cand c) {
+  __shared__ double sv[32], ss[32];
+  __shared__ int sp[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  c = warp_cand(c);
+  if (lane == 0) { sv[wid] = c.v; sp[wid] = c.pos; ss[wid] = c.sec; }
+  __syncthreads();
+  Cand r{-1.0, INT_MAX, -1.0};
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane < nw) { r.v = sv[lane]; r.pos = sp[lane]; r.sec = ss[lane]; }
+    r = warp_cand(r);
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(256) lupp_step_kernel(
+    int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int j,
+    int* __restrict__ pos_of, int* __restrict__ row_at, int* __restrict__ piv,
+    double* __restrict__ pval, int* __restrict__ ppos, double* __restrict__ psec,
+    unsigned int* counter, double* margin, int* iscal) {
+  extern __shared__ double prow[];  // pivot row values for columns j-1 .. K-1
+  if (iscal[1]) return;             // selection already stopped at a zero pivot
+  const int p = j > 0 ? piv[j - 1] : -1;
+  if (j > 0) {
+    for (int64_t c = j - 1 + threadIdx.x; c < K; c += blockDim.x)
+      prow[c - (j - 1)] = X[(int64_t)p * rs + c * cs];
+  }
+  __syncthreads();
+  Cand mine{-1.0, INT_MAX, -1.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pos = pos_of[i];
+    if (pos < j) continue;  // already a pivot row
+    double* xi = X + i * rs;
+    if (j > 0) {
+      const double l = xi[(j - 1) * cs] / prow[0];
+      xi[(j - 1) * cs] = l;
+      for (int64_t c = j; c < K; ++c) xi[c * cs] = xi[c * cs] - l * prow[c - (j - 1)];
+    }
+    if (j < K) {
+      Cand c{fabs(xi[(int64_t)j * cs]), pos, -1.0};
+      mine = cand_merge(mine, c);
+    }
+  }
+  Cand b = block_cand(mine);
+  if (threadIdx.x == 0) {
+    pval[blockIdx.x] = b.v;
+    ppos[blockIdx.x] = b.pos;
+    psec[blockIdx.x] = b.sec;
+  }
+  if (!last_block_done(counter)) return;
+  Cand t{-1.0, INT_MAX, -1.0};
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+    Cand c{__ldcg(pval + q), __ldcg(ppos + q), __ldcg(psec + q)};
+    t = cand_merge(t, c);
+  }
+  t = block_cand(t);
+  if (threadIdx.x == 0) {
+    if (!(t.v > 0.0)) {
+      iscal[1] = 1;  // zero pivot (or no candidates): rank exhausted
+    } else {
+      const int pr = row_at[t.pos];
+      const int q = row_at[j];
+      row_at[t.pos] = q;
+      pos_of[q] = t.pos;
+      row_at[j] = pr;
+      pos_of[pr] = j;
+      piv[j] = pr;
+      iscal[0] = j + 1;
+      if (t.sec >= 0.0) *margin = fmin(*margin, (t.v - t.sec) / t.v);
+    }
+  }
+}
+
+__global__ void lupp_init_kernel(int64_t N, int* pos_of, int* row_at, double* margin, int* iscal,
+                                 unsigned int* counter) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) { pos_of[i] = (int)i; row_at[i] = (int)i; }
+  if (i == 0) { *margin = INFINITY; iscal[0] = 0; iscal[1] = 0; *counter = 0u; }
+}
+
+// ---- gathers --------------------------------------------------------------------------
+
+template <typename T>
+__global__ void gather_cols_dense_kernel(int64_t m, int64_t ld, const T* __restrict__ A,
+                                         const int* __restrict__ idx, int k, double* out,
+                                         int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * k) return;
+  const int64_t q = e / m, i = e % m;
+  out[i + q * ldo] = (double)A[i * ld + idx[q]];
+}
+
+template <typename T>
+__global__ void gather_cols_csr_kernel(int64_t m, const int* __restrict__ rowptr,
+                                       const int* __restrict__ colidx, const T* __restrict__ v,
+                                       const int* __restrict__ colmap, int k, double* out,
+                                       int64_t ldo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int q = 0; q < k; ++q) out[i + q * ldo] = 0.0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int q = colmap[colidx[e]];
+    if (q >= 0 && q < k) out[i + q * ldo] = (double)v[e];
+  }
+}
+
+template <typename T>
+__global__ void gather_rows_T_dense_kernel(int64_t n, int64_t ld, const T* __restrict__ A,
+                                           const int* __restrict__ idx, int k, double* out,
+                                           int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t q = e / n, j = e % n;
+  out[j + q * ldo] = (double)A[(int64_t)idx[q] * ld + j];
+}
+
+template <typename T>
+__global__ void gather_rows_T_csr_kernel(int64_t n, const int* __restrict__ rowptr,
+                                         const int* __restrict__ colidx, const T* __restrict__ v,
+                                         const int* __restrict__ idx, double* out, int64_t ldo) {
+  const int q = blockIdx.x;
+  const int64_t i = idx[q];
+  for (int e = rowptr[i] + threadIdx.x; e < rowptr[i + 1]; e += blockDim.x)
+    out[(int64_t)colidx[e] + q * ldo] = (double)v[e];
+}
+
+template <typename T>
+__global__ void append_rows_kernel(int64_t n, int64_t ld, const T* __restrict__ A,
+                                   const int* __restrict__ idx, int k, double* R, int64_t ldr,
+                                   int64_t r0) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t q = e / n, j = e % n;
+  R[(r0 + q) + j * ldr] = (double)A[(int64_t)idx[q] * ld + j];
+}
+
+template <typename T>
+__global__ void cross_dense_kernel(int64_t ld, const T* __restrict__ A, const int* rI, int nI,
+                                   const int* cJ, int nJ, double* out, int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nI * nJ) return;
+  const int64_t a = e % nI, c = e / nI;
+  out[a + c * ldo] = (double)A[(int64_t)rI[a] * ld + cJ[c]];
+}
+
+template <typename T>
+__global__ void cross_csr_kernel(const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                                 const T* __restrict__ v, const int* rI, int nI,
+                                 const int* __restrict__ colmap, int nJ, double* out,
+                                 int64_t ldo) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nI) return;
+  for (int c = 0; c < nJ; ++c) out[a + c * ldo] = 0.0;
+  const int64_t i = rI[a];
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int c = colmap[colidx[e]];
+    if (c >= 0 && c < nJ) out[a + c * ldo] = (double)v[e];
+  }
+}
+
+__global__ void gather_rows_cm_kernel(const double* B, int64_t ldb, int64_t ncols,
+                                      const int* idx, int k, double* out, int64_t ldo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncols * k) return;
+  const int64_t a = e % k, c = e / k;
+  out[a + c * ldo] = B[(int64_t)idx[a] + c * ldb];
+}
+
+// ---- residuals for CSR ----------------------------------------------------------------
+
+template <typename T>
+__global__ void ecol_csr_kernel(int64_t m, const int* __restrict__ rowptr,
+                                const int* __restrict__ colidx, const T* __restrict__ v,
+                                const int* __restrict__ colpos,
+                                const int* __restrict__ colpos_plus,
+                                const int* __restrict__ rowpos, const double* __restrict__ X,
+                                int64_t ldx, int kb, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int k = 0; k < kb; ++k) out[i + k * m] = 0.0;
+  if (rowpos[i] >= 0) return;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int c = colidx[e];
+    const double a = (double)v[e];
+    const int jp = colpos_plus[c];
+    if (jp >= 0) out[i + jp * m] += a;
+    const int q = colpos[c];
+    if (q >= 0) {
+      for (int k = 0; k < kb; ++k) out[i + k * m] -= a * X[q + k * ldx];
+    }
+  }
+}
+
+template <typename T>
+__global__ void erow_csr_kernel(int64_t n, const int* __restrict__ colptr,
+                                const int* __restrict__ rowidx, const T* __restrict__ cv,
+                                const int* __restrict__ rowpos, const double* __restrict__ Z,
+                                int s, const double* __restrict__ Y, double* __restrict__ E) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  for (int r = lane; r < s; r += 32) {
+    double e = Y[r + j * s];
+    for (int p = colptr[j]; p < colptr[j + 1]; ++p) {
+      const int q = rowpos[rowidx[p]];
+      if (q >= 0) e -= (double)cv[p] * Z[r + (int64_t)q * s];
+    }
+    E[r + j * s] = e;
+  }
+}
+
+template <typename T>
+__global__ void gram_csr_kernel(int64_t m, const int* __restrict__ colptr,
+                                const int* __restrict__ rowidx, const T* __restrict__ cv,
+                                const int* __restrict__ Jall, int nq, const double* __restrict__ Cp,
+                                int kb, double* __restrict__ G, int64_t ldg) {
+  const int q = blockIdx.x;
+  if (q >= nq) return;
+  const int64_t col = Jall[q];
+  for (int k = threadIdx.x; k < kb; k += blockDim.x) {
+    double acc = 0.0;
+    for (int p = colptr[col]; p < colptr[col + 1]; ++p)
+      acc += (double)cv[p] * Cp[(int64_t)rowidx[p] + (int64_t)k * m];
+    G[q + k * ldg] = acc;
+  }
+}
+
+// ---- small helpers --------------------------------------------------------------------
+
+__global__ void zero_cols_kernel(double* E, int64_t ldE, int64_t rows, const int* cols, int k) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * k) return;
+  E[e % rows + (int64_t)cols[e / rows] * ldE] = 0.0;
+}
+__global__ void zero_rows_kernel(double* E, int64_t ldE, int64_t ncols, const int* rows, int k) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncols * k) return;
+  E[(int64_t)rows[e % k] + (e / k) * ldE] = 0.0;
+}
+__global__ void colnorm_max_kernel(const double* T, int s, int r, double factor, double* out) {
+  __shared__ double sh[32];
+  double best = 0.0;
+  for (int q = 0; q < r; ++q) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) v = fma(T[i + q * s], T[i + q * s], v);
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) best = fmax(best, sqrt(v));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = factor * best;
+}
+__global__ void set_map_kernel(int* map, const int* idx, int k, int base) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < k) map[idx[q]] = base + q;
+}
+__global__ void fill_int_kernel(int* p, int64_t n, int v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+
+void sketch(cudaStream_t st, const MatView& A, int s, int xi, const int* tptr, const int* ti,
+            const signed char* tsgn, const int* srows, const signed char* ssign, double scale,
+            double* Y) {
+  dim3 grid((unsigned)cdiv(A.n, 128), (unsigned)s);
+  if (A.fmt == 0) {
+    if (A.dtype == 0)
+      sketch_dense_kernel<double><<<grid, 128, 0, st>>>(A.n, A.ld, (const double*)A.vals, s, tptr,
+                                                        ti, tsgn, scale, Y);
+    else
+      sketch_dense_kernel<float><<<grid, 128, 0, st>>>(A.n, A.ld, (const float*)A.vals, s, tptr,
+                                                       ti, tsgn, scale, Y);
+  } else {
+    if (A.dtype == 0)
+      sketch_csc_kernel<double><<<grid, 128, 0, st>>>(A.n, A.colptr, A.rowidx,
+                                                      (const double*)A.cvals, s, xi, srows,
+                                                      ssign, scale, Y);
+    else
+      sketch_csc_kernel<float><<<grid, 128, 0, st>>>(A.n, A.colptr, A.rowidx,
+                                                     (const float*)A.cvals, s, xi, srows, ssign,
+                                                     scale, Y);
+  }
+  APL_LAUNCH_CHECK();
+}
+
+int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, int64_t cs, int k,
+                LuppWork& w, std::vector<int>& piv_host, double* margin) {
+  piv_host.clear();
+  *margin = INFINITY;
+  if (k <= 0 || N <= 0) return 0;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>(cdiv(N, threads), 2048);
+  w.pos_of.alloc(N, st);
+  w.row_at.alloc(N, st);
+  w.piv.alloc(k, st);
+  w.pval.alloc(blocks, st);
+  w.psec.alloc(blocks, st);
+  w.ppos.alloc(blocks, st);
+  w.counter.alloc(1, st);
+  w.scal.alloc(1, st);
+  w.iscal.alloc(2, st);
+  lupp_init_kernel<<<(unsigned)cdiv(N, 256), 256, 0, st>>>(N, w.pos_of.p, w.row_at.p, w.scal.p,
+                                                          w.iscal.p, w.counter.p);
+  APL_LAUNCH_CHECK();
+  const size_t shm = (size_t)(K + 1) * sizeof(double);
+  for (int j = 0; j < k; ++j) {
+    lupp_step_kernel<<<blocks, threads, shm, st>>>(N, K, X, rs, cs, j, w.pos_of.p, w.row_at.p,
+                                                   w.piv.p, w.pval.p, w.ppos.p, w.psec.p,
+                                                   w.counter.p, w.scal.p, w.iscal.p);
+  }
+  APL_LAUNCH_CHECK();
+  int isc[2];
+  APL_CUDA(cudaMemcpyAsync(isc, w.iscal.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaMemcpyAsync(margin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaStreamSynchronize(st));
+  const int nz = isc[0];
+  piv_host.resize(nz);
+  if (nz)
+    APL_CUDA(cudaMemcpyAsync(piv_host.data(), w.piv.p, nz * sizeof(int), cudaMemcpyDeviceToHost,
+                             st));
+  APL_CUDA(cudaStreamSynchronize(st));
+  return nz;
+}
+
+void gather_cols(cudaStream_t st, const MatView& A, const int* idx, int k, const int* colmap,
+                 double* out, int64_t ldo) {
+  if (k <= 0) return;
+  if (A.fmt == 0) {
+    const unsigned g = (unsigned)cdiv(A.m * k, 256);
+    if (A.dtype == 0)
+      gather_cols_dense_kernel<double><<<g, 256, 0, st>>>(A.m, A.ld, (const double*)A.vals, idx,
+                                                          k, out, ldo);
+    else
+      gather_cols_dense_kernel<float><<<g, 256, 0, st>>>(A.m, A.ld, (const float*)A.vals, idx, k,
+                                                         out, ldo);
+  } else {
+    const unsigned g = (unsigned)cdiv(A.m, 256);
+    if (A.dtype == 0)
+      gather_cols_csr_kernel<double><<<g, 256, 0, st>>>(A.m, A.rowptr, A.colidx,
+                                                        (const double*)A.vals, colmap, k, out,
+                                                        ldo);
+    else
+      gather_cols_csr_kernel<float><<<g, 256, 0, st>>>(A.m, A.rowptr, A.colidx,
+                                                       (const float*)A.vals, colmap, k, out, ldo);
+  }
+  APL_LAUNCH_CHECK();
+}
+
+void gather_rows_T(cudaStream_t st, const MatView& A, const int* idx, int k, double* out,
+                   int64_t ldo) {
+  if (k <= 0) return;
+  if (A.fmt == 0) {
+    const unsigned g = (unsigned)cdiv(A.n * k, 256);
+    if (A.dtype == 0)
+      gather_rows_T_dense_kernel<double><<<g, 256, 0, st>>>(A.n, A.ld, (const double*)A.vals, idx,
+                                                            k, out, ldo);
+    else
+      gather_rows_T_dense_kernel<float><<<g, 256, 0, st>>>(A.n, A.ld, (const float*)A.vals, idx,
+                                                           k, out, ldo);
+  } else {
+    for (int q = 0; q < k; ++q)
+      APL_CUDA(cudaMemsetAsync(out + q * ldo, 0, A.n * sizeof(double), st));
+    if (A.dtype == 0)
+      gather_rows_T_csr_kernel<double><<<k, 128, 0, st>>>(A.n, A.rowptr, A.colidx,
+                                                          (const double*)A.vals, idx, out, ldo);
+    else
+      gather_rows_T_csr_kernel<float><<<k, 128, 0, st>>>(A.n, A.rowptr, A.colidx,
+                                                         (const float*)A.vals, idx, out, ldo);
+  }
+  APL_LAUNCH_CHECK();
+}
+
+void append_rows(cudaStream_t st, const MatView& A, const int* idx, int k, double* R, int64_t ldr,
+                 int64_t r0) {
+  if (k <= 0) return;
+  const unsigned g = (unsigned)cdiv(A.n * k, 256);
+  if (A.dtype == 0)
+    append_rows_kernel<double><<<g, 256, 0, st>>>(A.n, A.ld, (const double*)A.vals, idx, k, R,
+                                                  ldr, r0);
+  else
+    append_rows_kernel<float><<<g, 256, 0, st>>>(A.n, A.ld, (const float*)A.vals, idx, k, R, ldr,
+                                                 r0);
+  APL_LAUNCH_CHECK();
+}
+
+void gather_cross(cudaStream_t st, const MatView& A, const int* rI, int nI, const int* cJ, int nJ,
+                  const int* colmap, double* out, int64_t ldo) {
+  if (nI <= 0 || nJ <= 0) return;
+  if (A.fmt == 0) {
+    const unsigned g = (unsigned)cdiv((int64_t)nI * nJ, 256);
+    if (A.dtype == 0)
+      cross_dense_kernel<double><<<g, 256, 0, st>>>(A.ld, (const double*)A.vals, rI, nI, cJ, nJ,
+                                                    out, ldo);
+    else
+      cross_dense_kernel<float><<<g, 256, 0, st>>>(A.ld, (const float*)A.vals, rI, nI, cJ, nJ, out,
+                                                   ldo);
+  } else {
+    const unsigned g = (unsigned)cdiv(nI, 128);
+    if (A.dtype == 0)
+      cross_csr_kernel<double><<<g, 128, 0, st>>>(A.rowptr, A.colidx, (const double*)A.vals, rI,
+                                                  nI, colmap, nJ, out, ldo);
+    else
+      cross_csr_kernel<float><<<g, 128, 0, st>>>(A.rowptr, A.colidx, (const float*)A.vals, rI, nI,
+                                                 colmap, nJ, out, ldo);
+  }
+  APL_LAUNCH_CHECK();
+}
+
+void gather_rows_cm(cudaStream_t st, const double* B, int64_t ldb, int64_t ncols, const int* idx,
+                    int k, double* out, int64_t ldo) {
+  if (k <= 0 || ncols <= 0) return;
+  gather_rows_cm_kernel<<<(unsigned)cdiv(ncols * k, 256), 256, 0, st>>>(B, ldb, ncols, idx, k,
+                                                                        out, ldo);
+  APL_LAUNCH_CHECK();
+}
+
+void ecol_csr(cudaStream_t st, const MatView& A, const int* colpos, const int* colpos_plus,
+              const int* rowpos, const double* X, int64_t ldx, int kb, double* out) {
+  const unsigned g = (unsigned)cdiv(A.m, 128);
+  if (A.dtype == 0)
+    ecol_csr_kernel<double><<<g, 128, 0, st>>>(A.m, A.rowptr, A.colidx, (const double*)A.vals,
+                                               colpos, colpos_plus, rowpos, X, ldx, kb, out);
+  else
+    ecol_csr_kernel<float><<<g, 128, 0, st>>>(A.m, A.rowptr, A.colidx, (const float*)A.vals,
+                                              colpos, colpos_plus, rowpos, X, ldx, kb, out);
+  APL_LAUNCH_CHECK();
+}
+
+void erow_csr(cudaStream_t st, const MatView& A, const int* rowpos, const double* Z, int s,
+              const double* Y, double* E) {
+  const unsigned g = (unsigned)cdiv(A.n * 32, 256);
+  if (A.dtype == 0)
+    erow_csr_kernel<double><<<g, 256, 0, st>>>(A.n, A.colptr, A.rowidx, (const double*)A.cvals,
+                                               rowpos, Z, s, Y, E);
+  else
+    erow_csr_kernel<float><<<g, 256, 0, st>>>(A.n, A.colptr, A.rowidx, (const float*)A.cvals,
+                                              rowpos, Z, s, Y, E);
+  APL_LAUNCH_CHECK();
+}
+
+void gram_csr(cudaStream_t st, const MatView& A, const int* Jall, int nq, const double* Cp, int kb,
+              double* G, int64_t ldg) {
+  if (nq <= 0 || kb <= 0) return;
+  if (A.dtype == 0)
+    gram_csr_kernel<double><<<nq, 128, 0, st>>>(A.m, A.colptr, A.rowidx, (const double*)A.cvals,
+                                                Jall, nq, Cp, kb, G, ldg);
+  else
+    gram_csr_kernel<float><<<nq, 128, 0, st>>>(A.m, A.colptr, A.rowidx, (const float*)A.cvals,
+                                               Jall, nq, Cp, kb, G, ldg);
+  APL_LAUNCH_CHECK();
+}
+
+void zero_cols_cm(cudaStream_t st, double* E, int64_t ldE, int64_t rows, const int* cols, int k) {
+  if (k <= 0 || rows <= 0) return;
+  zero_cols_kernel<<<(unsigned)cdiv(rows * k, 256), 256, 0, st>>>(E, ldE, rows, cols, k);
+  APL_LAUNCH_CHECK();
+}
+void zero_rows_cm(cudaStream_t st, double* E, int64_t ldE, int64_t ncols, const int* rows, int k) {
+  if (k <= 0 || ncols <= 0) return;
+  zero_rows_kernel<<<(unsigned)cdiv(ncols * k, 256), 256, 0, st>>>(E, ldE, ncols, rows, k);
+  APL_LAUNCH_CHECK();
+}
+void colnorm_max(cudaStream_t st, const double* T, int s, int r, double factor, double* out) {
+  colnorm_max_kernel<<<1, 256, 0, st>>>(T, s, r, factor, out);
+  APL_LAUNCH_CHECK();
+}
+void set_map(cudaStream_t st, int* map, const int* idx, int k, int base) {
+  if (k <= 0) return;
+  set_map_kernel<<<(unsigned)cdiv(k, 256), 256, 0, st>>>(map, idx, k, base);
+  APL_LAUNCH_CHECK();
+}
+void fill_int(cudaStream_t st, int* p, int64_t n, int v) {
+  if (n <= 0) return;
+  fill_int_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(p, n, v);
+  APL_LAUNCH_CHECK();
+}
+
+}  // namespace apl

@@ -1,0 +1,41 @@
+// Small dense FP64 linear algebra used by the CUR and preconditioner steps.
+// All matrices here are column-major with explicit leading dimensions.
+#pragma once
+#include "common.cuh"
+
+namespace apl {
+
+// C = alpha op(A) op(B) + beta C  (op = transpose when trans != 0), C is M x N.
+void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
+           double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+           double beta, double* C, int64_t ldc);
+
+// Solve op(A) X = B (left) or X op(A) = B (right) in place of B (M x N).
+// uplo: 'L' or 'U' as stored; unit: unit diagonal assumed.
+void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t M, int64_t N,
+           const double* A, int64_t lda, double* B, int64_t ldb);
+
+// In-place upper Cholesky of the n x n matrix A (upper triangle read, lower part
+// zeroed).  Writes 0 to *info_dev on success, k+1 when pivot k is not positive.
+void dpotrf_upper(cudaStream_t st, int64_t n, double* A, int64_t lda, int* info_dev);
+
+// Thin QR of E (n x k) by Cholesky QR twice: E <- Q, R (k x k, ldr) upper.
+// Returns false if a Cholesky step broke down.
+bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, double* R,
+             int64_t ldr, double* work, int* info_dev);
+
+// One-sided Jacobi SVD of the square M (l x l, in place): on return the columns of M
+// are U Sigma and V (l x l) holds the right singular vectors; sigma gets the column
+// norms.  Columns are sorted by descending sigma.  Returns the sweep count.
+int jacobi_svd(cudaStream_t st, int64_t l, double* M, int64_t ldm, double* V, int64_t ldv,
+               double* sigma, double* work, int* flag_dev);
+
+// Elementwise helpers.
+void dcopy2d(cudaStream_t st, int64_t rows, int64_t cols, const double* src, int64_t lds,
+             double* dst, int64_t ldd, bool transpose);
+void dset2d(cudaStream_t st, int64_t rows, int64_t cols, double v, double* dst, int64_t ldd);
+void dzero_lower(cudaStream_t st, int64_t n, double* A, int64_t lda);
+void dgather_cols(cudaStream_t st, int64_t rows, const double* src, int64_t lds,
+                  const int* idx, int64_t k, double* dst, int64_t ldd);
+
+}  // namespace apl

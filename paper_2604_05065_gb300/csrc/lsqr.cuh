@@ -1,0 +1,111 @@
+// Preconditioned LSQR phase on the GPU (Section 2.2, warm start of Section 3.2, stopping
+// rules of Section 5.3.2): Golub-Kahan bidiagonalisation of [A; delta I] P^{-1} with an
+// explicit (m+n)-vector u, all scalars resident in device memory.
+#pragma once
+#include "cur.cuh"
+
+namespace apl {
+
+enum StopReason { R_NONE = 0, R_EXACT = 1, R_REPLAY = 2, R_PS2 = 3, R_PS1 = 4, R_DYNAMIC = 5,
+                  R_TOL = 6, R_MAXIT = 7, R_CHECK = 8, R_DRIFT = 9 };
+
+// Per-kernel device time of the hot loop, collected with CUDA events recorded inside the
+// captured iteration graphs when profiling is on.
+struct KernelProfile {
+  double ms[3] = {0, 0, 0};        // 0: A z pass (K1), 1: A^T u pass (K2), 2: Vhat passes
+  long long launches[3] = {0, 0, 0};
+  double bytes[3] = {0, 0, 0};     // algorithmic bytes of one launch (current phase)
+  double bytes_total[3] = {0, 0, 0};  // summed over the timed launches
+  int broken = 0;                    // event timing failed; numbers incomplete
+};
+
+// Device-resident LSQR state and phase parameters.
+struct LsqrCtl {
+  double alpha, beta, rhobar, phibar, phibar_prev, beta1, anorm2, rate1;
+  double us;        // scale of the stored u (1/beta)
+  double zs;        // scale of the stored v' and z' (1/alpha)
+  double xc, dc;    // pending update x += xc d ; d = z - dc d
+  double cabs;
+  int pending;      // 0 none, 1 d = z, 2 x and d update, 3 d update only
+  int it, done, reason, init;
+  int next_check, fixed_len, use_p, pad;
+  double delta, eps, nu, sig_ell, tol, normP, norm_ref;
+  long long maxit;
+  unsigned int counter[8];
+};
+
+// The preconditioner P^{-1} = I + Vhat diag(coef) Vhat^T (Eq. preconditioner2), with
+// Vhat stored row-major n x ell (ld ldv) in FP64 or FP32; coef2 gives P^{-2}.
+struct PrecondDev {
+  int ell = 0;
+  int64_t ldv = 0;
+  int fp32 = 0;
+  const double* V64 = nullptr;
+  const float* V32 = nullptr;
+  const double* coef = nullptr;
+  const double* coef2 = nullptr;
+  double normP = 1.0;    // ||P||_2
+  double sig_ell = 0.0;  // smallest CUR singular value
+};
+
+struct PhaseArgs {
+  const double* rhs_top = nullptr;  // m
+  const double* rhs_bot = nullptr;  // n, NULL = zeros
+  double* x = nullptr;              // n, in: x0, out: x
+  double eps = 1e-10, nu = INFINITY, tol = 0.0, norm_ref = 1.0, mu = 0.0;
+  int fixed_len = -1;
+  long long maxit = 1000000;
+  int check_gap = 10;
+};
+
+struct PhaseResult {
+  long long iters = 0;
+  int reason = R_NONE;
+  int checks = 0;
+  double ne_res = -1.0;  // last explicit check, -1 if none
+};
+
+class LsqrEngine {
+ public:
+  void setup(cudaStream_t st, const MatView& A, int mixed, int graph_iters);
+  void set_profile(bool on) { profile_ = on; }
+  KernelProfile prof;
+  PhaseResult run_phase(const PrecondDev& P, const PhaseArgs& a);
+  // ||A_delta^T (rhs - A_delta x)|| / norm_ref in FP64 (rhs_bot NULL = 0).
+  double ne_residual(const double* rhs_top, const double* rhs_bot, const double* x, double delta,
+                     double norm_ref);
+  // y = alpha A x + beta y (trans 0) or y = A^T x (trans 1), FP64 or mixed products.
+  void matvec(int trans, const double* x, double* y, double alpha, double beta, bool fp64);
+  double norm2(const double* v, int64_t n);
+  // out = P^{-1} w (and P^{-2} w in out2 when not NULL)
+  void apply_precond(const PrecondDev& P, const double* w, double* out, double* out2);
+  cudaStream_t stream() const { return st_; }
+
+ private:
+  void launch_iteration(const PrecondDev& P, bool init);
+  void launch_k1(bool init, const double* z);
+  void launch_k2(bool init, bool fused_v);
+  void launch_pre(const PrecondDev& P, const double* w, double* o1, double* o2, bool in_phase,
+                  bool init);
+  void flush_x();
+
+  cudaStream_t st_ = nullptr;
+  MatView A_;
+  int mixed_ = 0, graph_iters_ = 16;
+  int64_t m_ = 0, n_ = 0;
+  int k1_blocks_ = 0, k2_blocks_ = 0, k2_rchunks_ = 1, red_cap_ = 0;
+  DBuf<LsqrCtl> ctl_;
+  DBuf<double> u_, v_, z_, g_, d_, red_, part_, tpart_, ct_, c2t_, r_, q_;
+  DBuf<double> scal_;
+  DBuf<unsigned int> cnt_;
+  double* x_ = nullptr;
+  int tchunks_ = 1, tcap_ = 0;
+  bool profile_ = false;
+  std::vector<cudaEvent_t> ev_;
+  int kernels_per_iter_ = 0;
+  void record(int slot);
+  void ensure_events(int n);
+  void harvest(int iters, int ell);
+};
+
+}  // namespace apl

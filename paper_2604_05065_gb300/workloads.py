@@ -101,9 +101,9 @@ def config1(scale: int = 1) -> Problem:
 
 
 def sparse_colscaled(m=200000, n=20000, nnz_per_col=10, mu=1e-6, sketch_dim=100, index=2,
-                     dtype=np.float64, name=None) -> Problem:
+                     dtype=np.float64, name=None, col_decay=6.0) -> Problem:
     """Each column holds nnz_per_col N(0,1) values at distinct uniform rows; column j is
-    scaled by 10^(-6 j/(n-1)); b ~ N(0,1)."""
+    scaled by 10^(-col_decay j/(n-1)); b ~ N(0,1)."""
     rng = _rng(index)
     k = nnz_per_col
     rows = rng.integers(0, m, size=(n, k))
@@ -116,7 +116,7 @@ def sparse_colscaled(m=200000, n=20000, nnz_per_col=10, mu=1e-6, sketch_dim=100,
         bad = np.nonzero(dup)[0]
         rows[bad] = rng.integers(0, m, size=(bad.size, k))
     vals = rng.standard_normal((n, k))
-    colscale = 10.0 ** (-6.0 * np.arange(n) / max(n - 1, 1))
+    colscale = 10.0 ** (-col_decay * np.arange(n) / max(n - 1, 1))
     vals = vals * colscale[:, None]
     cols = np.repeat(np.arange(n), k)
     rows = rows.reshape(-1)
@@ -150,7 +150,11 @@ def rbf_kernel(npts=20000, dim=8, mu=1e-3, sketch_dim=250, index=3, chunk=2048) 
         np.maximum(d2, 0.0, out=d2)
         A[r0:r1] = np.exp(-0.5 * d2).astype(np.float32)
     w = rng.standard_normal(npts)
-    b = A.astype(np.float64) @ w + 1e-2 * rng.standard_normal(npts)
+    b = np.empty(npts)
+    for r0 in range(0, npts, chunk):
+        r1 = min(npts, r0 + chunk)
+        b[r0:r1] = A[r0:r1].astype(np.float64) @ w
+    b += 1e-2 * rng.standard_normal(npts)
     return Problem(f"rbf_fp32_{npts}x{npts}", npts, npts, "dense", np.dtype(np.float32), mu,
                    sketch_dim, b, dense=A, extra={"points": p})
 
@@ -185,10 +189,12 @@ def small_dense(m, n, seed, decay=6.0, mu=1e-4, sketch_dim=4, noise=1e-3, rank=N
                    b, dense=A, extra={"sigma": s})
 
 
-def small_sparse(m, n, seed, nnz_per_col=3, mu=1e-4, sketch_dim=4, dtype=np.float64) -> Problem:
+def small_sparse(m, n, seed, nnz_per_col=3, mu=1e-4, sketch_dim=4, dtype=np.float64,
+                 col_decay=6.0) -> Problem:
     rng_seed = seed - BASE_SEED
     return sparse_colscaled(m=m, n=n, nnz_per_col=nnz_per_col, mu=mu, sketch_dim=sketch_dim,
-                            index=rng_seed, dtype=dtype, name=f"small_sparse_{m}x{n}")
+                            index=rng_seed, dtype=dtype, name=f"small_sparse_{m}x{n}",
+                            col_decay=col_decay)
 
 
 def by_name(name: str, scale: int = 1) -> Problem:

@@ -1,0 +1,280 @@
+"""CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances: CUR indices and the sketch are compared exactly; FP64 solutions to a
+relative error of 1e-10 (in replay mode the GPU runs the oracle's phase schedule);
+FP32-storage mixed runs to 1e-5 against the oracle on the same rounded matrix."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import aplicur_oracle as O
+from paper_2604_05065_gb300 import workloads as wl
+
+from gpu_helpers import draws, oracle_matrix, rel, schedule, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(p, rows, signs, W, **kw):
+    import paper_2604_05065_gb300 as pkg
+    A, b = to_device(p)
+    return pkg.Solver(A, b, p.mu, p.sketch_dim, sketch_rows=rows, sketch_signs=signs,
+                      normest_w=W, **kw)
+
+
+def _problems():
+    return {
+        "dense64": wl.config1(scale=4),
+        "dense64_full": wl.config1(),
+        "sparse64": wl.small_sparse(3000, 300, wl.BASE_SEED + 50, nnz_per_col=6, mu=1e-5,
+                                    sketch_dim=10),
+        "dense32": wl.dense_lowrank(m=600, n=120, mu=1e-4, sketch_dim=8, index=60,
+                                    dtype=np.float32, name="dense32"),
+        "sparse32": wl.small_sparse(2500, 250, wl.BASE_SEED + 51, nnz_per_col=5, mu=1e-5,
+                                    sketch_dim=10, dtype=np.float32),
+    }
+
+
+PROBS = _problems()
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_sketch_is_bit_exact(name):
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    s = _solver(p, rows, signs, W)
+    Y = s.sketch().cpu().numpy()
+    Yo = O.apply_sketch(oracle_matrix(p), rows, signs, O.sketch_rows(p.sketch_dim))
+    assert Y.shape == Yo.shape
+    assert np.array_equal(Y, Yo)
+
+
+@pytest.mark.parametrize("name", ["dense64", "sparse64"])
+def test_seeded_draws_match_oracle_generator(name):
+    """Library and oracle implement the same counter-based generator independently."""
+    import paper_2604_05065_gb300 as pkg
+    p = PROBS[name]
+    A, b = to_device(p)
+    s = pkg.Solver(A, b, p.mu, p.sketch_dim, seed=12345)
+    Y = s.sketch().cpu().numpy()
+    srow = O.sketch_rows(p.sketch_dim)
+    from oracle import rng as orng
+    rows, signs = orng.sparse_sign(12345, srow, p.m, O.sketch_xi(srow))
+    assert np.array_equal(Y, O.apply_sketch(oracle_matrix(p), rows, signs, srow))
+    ref = O.aplicur(oracle_matrix(p), p.b, p.mu, p.sketch_dim, O.Options(seed=12345), tol=1e-10)
+    s.set_replay(schedule(ref))
+    s.solve(1e-10)
+    I, J = s.indices()
+    assert np.array_equal(I, ref.I) and np.array_equal(J, ref.J)
+
+
+@pytest.mark.parametrize("name", ["dense64", "sparse64", "dense32"])
+def test_matvec(name):
+    import torch
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    s = _solver(p, rows, signs, W)
+    A = oracle_matrix(p)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(p.n)
+    y = rng.standard_normal(p.m)
+    Ax = s.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    Aty = s.matvec(torch.from_numpy(y).cuda(), trans=True).cpu().numpy()
+    assert rel(Ax, A @ x) < 1e-13
+    assert rel(Aty, A.T @ y) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["dense64", "dense64_full", "sparse64"])
+def test_replay_solve_matches_oracle(name):
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)
+    ref = O.aplicur(A, p.b, p.mu, p.sketch_dim, tol=1e-10, srows=rows, signs=signs, W=W)
+    s = _solver(p, rows, signs, W, replay=schedule(ref))
+    x = s.solve(1e-10).cpu().numpy()
+    I, J = s.indices()
+    assert np.array_equal(I, ref.I)
+    assert np.array_equal(J, ref.J)
+    assert rel(x, ref.x) <= 1e-10
+    ph = s.phases()
+    assert [q["iters"] for q in ph] == [q["iters"] for q in ref.phases]
+    st = s.steps()
+    for a, b_ in zip(st, ref.rank_steps):
+        assert a["ell"] == b_["ell"]
+        assert a["rho"] == pytest.approx(b_["rho"], rel=1e-9)
+
+
+@pytest.mark.parametrize("name", ["dense64_full", "sparse64"])
+def test_free_run_matches_oracle(name):
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)
+    ref = O.aplicur(A, p.b, p.mu, p.sketch_dim, tol=1e-10, srows=rows, signs=signs, W=W)
+    s = _solver(p, rows, signs, W)
+    x = s.solve(1e-10).cpu().numpy()
+    st = s.stats()
+    assert st["converged"] == 1 and st["ne_res"] <= 1e-10
+    I, J = s.indices()
+    assert np.array_equal(I, ref.I) and np.array_equal(J, ref.J)
+    # both converged to the same minimiser: error bounded by the residual tolerance
+    xd = O.ridge_direct(A, p.b, p.mu) if p.n <= 400 else ref.x
+    kappa = 1.0 / math.sqrt(p.mu)
+    assert rel(x, xd) <= max(1e-10, 10 * kappa * 1e-10)
+
+
+def test_preconditioner_matches_oracle():
+    import torch
+    p = PROBS["dense64"]
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)
+    ref = O.aplicur(A, p.b, p.mu, p.sketch_dim, tol=1e-10, srows=rows, signs=signs, W=W)
+    s = _solver(p, rows, signs, W, replay=schedule(ref))
+    s.solve(1e-10)
+    sig, sighat = s.preconditioner()
+    P = ref.last_P
+    assert sig.numel() == P.ell
+    assert rel(sig.cpu().numpy(), P.sig) <= 1e-10
+    assert sighat == pytest.approx(P.sighat, rel=1e-12)
+    w = np.random.default_rng(4).standard_normal(p.n)
+    out = s.apply_preconditioner(torch.from_numpy(w).cuda()).cpu().numpy()
+    assert rel(out, P.apply_inv(w)) <= 1e-10
+
+
+WELLCOND = {
+    "dense": lambda: wl.small_dense(400, 60, 904, decay=1.0, mu=1e-3, sketch_dim=4),
+    "sparse": lambda: wl.small_sparse(3000, 300, wl.BASE_SEED + 52, nnz_per_col=6, mu=1e-3,
+                                      sketch_dim=10, col_decay=0.5),
+}
+
+
+@pytest.mark.parametrize("name", ["dense", "sparse"])
+@pytest.mark.parametrize("k", [1, 5, 12])
+def test_plain_lsqr_iterates(name, k):
+    """Early iterates on well-conditioned problems, before the Golub-Kahan basis loses
+    orthogonality (later iterates of any two LSQR implementations differ by rounding
+    amplification, then reconverge; see test_plain_lsqr_converged)."""
+    p = WELLCOND[name]()
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)
+    ref = O.plsqr_phase(A, p.b, math.sqrt(p.mu), np.zeros(p.n), O.identity_preconditioner(p.n),
+                        eps_lsqr=0.0, maxit=k)
+    s = _solver(p, rows, signs, W)
+    x = s.plain_lsqr(0.0, k).cpu().numpy()
+    assert s.phases()[0]["iters"] == k
+    assert rel(x, ref.x) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["dense64", "sparse64"])
+def test_plain_lsqr_converged(name):
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)
+    s = _solver(p, rows, signs, W)
+    x = s.plain_lsqr(1e-12, 200000).cpu().numpy()
+    assert s.stats()["ne_res"] <= 1e-12
+    xd = O.ridge_direct(A, p.b, p.mu) if p.fmt == "dense" else O.plain_lsqr(
+        A, p.b, p.mu, tol=1e-13).x
+    assert rel(x, xd) <= 1e-8
+
+
+def test_adjoint_gradients_match_oracle():
+    import torch
+    p = wl.small_dense(300, 40, 901, decay=3.0, mu=1e-3, sketch_dim=5)
+    rows, signs, W = draws(p)
+    A = p.dense
+    s = _solver(p, rows, signs, W)
+    x = s.solve(1e-12).cpu().numpy()
+    xt = np.random.default_rng(6).standard_normal(p.n)
+    g = x - xt
+    gb, gmu, gA = s.backward(torch.from_numpy(g).cuda(), tol=1e-12)
+    xd = O.ridge_direct(A, p.b, p.mu)
+    lam, gb_o, gmu_o, gA_o = O.ridge_gradients(A, p.b, p.mu, xd, xd - xt)
+    assert rel(gb.cpu().numpy(), gb_o) <= 1e-8
+    assert gmu == pytest.approx(gmu_o, rel=1e-8)
+    assert rel(gA.cpu().numpy(), gA_o) <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["dense32", "sparse32"])
+def test_mixed_precision_against_same_rounded_problem(name):
+    import paper_2604_05065_gb300 as pkg
+    p = PROBS[name]
+    rows, signs, W = draws(p)
+    A = oracle_matrix(p)  # the FP32 values promoted exactly
+    xd = O.ridge_direct(A, p.b, p.mu)
+    s = _solver(p, rows, signs, W, precision=pkg.PREC_MIXED)
+    x = s.solve(1e-10).cpu().numpy()
+    assert rel(x, xd) <= 1e-5
+    assert s.stats()["ne_res"] <= 1e-10
+
+
+def test_invalid_arguments_are_rejected():
+    import torch
+    import paper_2604_05065_gb300 as pkg
+    A = torch.zeros(10, 20, dtype=torch.float64, device="cuda")  # m < n
+    b = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.AplicurError) as e:
+        pkg.Solver(A, b, 1e-4, 2)
+    assert e.value.status == 1
+    A = torch.randn(30, 10, dtype=torch.float64, device="cuda")
+    b = torch.randn(30, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.AplicurError):
+        pkg.Solver(A, b, -1.0, 2)
+    with pytest.raises(pkg.AplicurError):
+        pkg.Solver(A, b, 1e-4, 0)
+    with pytest.raises(pkg.AplicurError):
+        pkg.Solver(A, b, 1e-4, 11)
+
+
+def test_zero_rhs_and_exact_low_rank():
+    import torch
+    import paper_2604_05065_gb300 as pkg
+    p = wl.small_dense(200, 30, 902, rank=12, decay=2.0, mu=1e-6, sketch_dim=4)
+    A, b = to_device(p)
+    s = pkg.Solver(A, torch.zeros_like(b), p.mu, 4, seed=2)
+    x = s.solve(1e-10)
+    assert float(x.abs().max()) == 0.0
+    rows, signs, W = draws(p)
+    ref = O.aplicur(p.dense, p.b, p.mu, 4, tol=1e-9, srows=rows, signs=signs, W=W)
+    s2 = _solver(p, rows, signs, W)
+    x2 = s2.solve(1e-9).cpu().numpy()
+    I, J = s2.indices()
+    assert len(I) == len(ref.I) == 12
+    assert np.array_equal(I, ref.I) and np.array_equal(J, ref.J)
+    assert rel(x2, O.ridge_direct(p.dense, p.b, p.mu)) <= 1e-6
+
+
+def test_rank_beyond_exact_rank_breaks_down_like_the_oracle():
+    """Exact rank 9 with blocks of 4: the third block adds columns from rounding noise,
+    C^T C is numerically singular and the Cholesky of the preconditioner build fails on
+    both sides (the oracle raises, the library returns EBREAKDOWN)."""
+    import paper_2604_05065_gb300 as pkg
+    p = wl.small_dense(200, 30, 902, rank=9, decay=2.0, mu=1e-6, sketch_dim=4)
+    rows, signs, W = draws(p)
+    with pytest.raises(np.linalg.LinAlgError):
+        O.aplicur(p.dense, p.b, p.mu, 4, tol=1e-9, srows=rows, signs=signs, W=W)
+    s = _solver(p, rows, signs, W)
+    with pytest.raises(pkg.AplicurError) as e:
+        s.solve(1e-9)
+    assert e.value.status == 5
+
+
+def test_square_and_full_block():
+    """m == n and a block that spans all columns (rank reaches min(m, n))."""
+    p = wl.small_dense(48, 48, 903, decay=3.0, mu=1e-4, sketch_dim=16)
+    rows, signs, W = draws(p)
+    ref = O.aplicur(p.dense, p.b, p.mu, 16, tol=1e-10, srows=rows, signs=signs, W=W)
+    s = _solver(p, rows, signs, W, replay=schedule(ref))
+    x = s.solve(1e-10).cpu().numpy()
+    I, J = s.indices()
+    assert np.array_equal(I, ref.I) and np.array_equal(J, ref.J)
+    assert rel(x, ref.x) <= 1e-10
+
+
+def test_deterministic_bitwise_rerun():
+    p = PROBS["sparse64"]
+    rows, signs, W = draws(p)
+    s = _solver(p, rows, signs, W)
+    x1 = s.solve(1e-10).cpu().numpy()
+    x2 = s.solve(1e-10).cpu().numpy()
+    assert np.array_equal(x1, x2)
