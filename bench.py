@@ -30,7 +30,7 @@ METRIC = "time-to-1e-8 rel. residual; SpMV HBM GB/s %peak; batched solves/s vs p
 TOL = 1e-8
 WORKLOADS = {
     # name: (generator, precision)
-    "rbf_fp32_20000x20000": ("config3", "mixed"),
+    "rbf_fp32_20000x20000": ("config3", "df32"),
     "dense_fp64_2000x200": ("config1", "fp64"),
     "sparse_csr_200000x20000": ("config2", "fp64"),
 }
@@ -131,7 +131,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     p, prec = make_workload(args.workload)
-    precision = pkg.PREC_MIXED if prec == "mixed" else pkg.PREC_FP64
+    precision = {"mixed": pkg.PREC_MIXED, "df32": pkg.PREC_DF32}.get(prec, pkg.PREC_FP64)
     if p.fmt == "dense":
         A_host = torch.from_numpy(p.dense).pin_memory()
         A = A_host.to(dev, non_blocking=True)
@@ -161,7 +161,10 @@ def gpu_arm(args, rank, world, local_rank):
                 prof_tot["bytes"][k] += pr["bytes"][k]
             sched.update(steps=st["nsteps"], phases=st["nphases"], iters=st["iters"],
                          ell=st["ell"], builds=sum(1 for q in s.steps() if q["rebuild"]),
-                         ne_res=st["ne_res"], converged=st["converged"])
+                         ne_res=st["ne_res"], converged=st["converged"],
+                         ms_rank=round(st["time_rank_ms"], 1), ms_build=round(st["time_build_ms"], 1),
+                         ms_lsqr=round(st["time_lsqr_ms"], 1), ms_setup=round(st["time_setup_ms"], 2),
+                         phase_log=s.phases())
         s.close()
         return x, st
 
@@ -386,11 +389,12 @@ def main():
         line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if r["prec"] == "mixed" else "f64", "data": "synthetic",
+                "dtype": "f32" if r["prec"] in ("mixed", "df32") else "f64", "data": "synthetic",
                 "config": {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu,
                            "sketch_dim": p.sketch_dim, "tol": TOL,
-                           "precision": "fp32 products, fp64 scalars/core/refinement"
-                           if r["prec"] == "mixed" else "fp64",
+                           "precision": {"mixed": "fp32 products and sums, fp64 scalars/core/refinement",
+                                         "df32": "fp32 storage, compensated fp32 products and sums (hi/lo split), fp64 scalars/core/preconditioner",
+                                         }.get(r["prec"], "fp64"),
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2" if p.nnz * p.dtype.itemsize > 129e6
                            else "L2-resident inputs (no flush)"},

@@ -46,11 +46,18 @@ typedef enum {
 
 enum { APLICUR_DENSE_ROWMAJOR = 0, APLICUR_CSR = 1 };
 enum { APLICUR_F64 = 0, APLICUR_F32 = 1 };
-/* Arithmetic of the products with A and with the preconditioner basis:
- * FP64 = FP64 products and sums; MIXED = FP32 products with FP32 partial
- * sums (FP64 across threads), FP32 preconditioner basis, FP64 scalars,
- * FP64 core factorisations and an FP64 residual refinement at the end. */
-enum { APLICUR_PREC_FP64 = 0, APLICUR_PREC_MIXED = 1 };
+/* Arithmetic of the products with an FP32-stored A (FP64-stored A always uses FP64):
+ *  FP64  products and sums in FP64 (values promoted exactly);
+ *  MIXED FP32 products with FP32 sums per thread, FP64 across threads; each LSQR phase
+ *        is an inner solve of an FP64 iterative refinement: every phase starts from
+ *        a residual formed in FP64 and ends once its estimate of ||Abar^T rbar|| fell
+ *        by 1e-4, or when an FP64 check shows the residual no longer falling;
+ *  DF32  compensated FP32: operand vectors split into FP32 hi + lo parts, exact
+ *        products by FMA residuals and two-term sums, i.e. FP64-level accuracy from
+ *        FP32 instructions only.
+ * In every mode the preconditioner basis, all LSQR scalars and the CUR core
+ * factorisations are FP64. */
+enum { APLICUR_PREC_FP64 = 0, APLICUR_PREC_MIXED = 1, APLICUR_PREC_DF32 = 2 };
 
 /* The matrix A (borrowed, device memory).
  *  format = APLICUR_DENSE_ROWMAJOR: values -> m x n row-major, leading dim ld >= n.
@@ -79,7 +86,7 @@ typedef struct {
   int32_t normest_r;         /* Gaussian vectors of Eq. 2normestimate */
   int32_t check_gap;         /* LSQR iterations between explicit residual checks */
   int32_t max_extra_phases;  /* warm restarts of the final phase */
-  int32_t precision;         /* APLICUR_PREC_FP64 or APLICUR_PREC_MIXED */
+  int32_t precision;         /* APLICUR_PREC_FP64, _MIXED or _DF32 */
   int32_t graph_iters;       /* LSQR iterations per captured CUDA graph (>=1) */
   /* Optional host arrays that replace the seeded draws (parity testing):
    * sketch_rows/sketch_signs: m*xi row indices in [0,s) and +-1 signs of the
@@ -125,6 +132,9 @@ typedef struct {
   double rho;           /* last norm estimate */
   double time_setup_ms; /* sketch and creation work (device time) */
   double time_solve_ms; /* aplicur_solve wall time */
+  double time_rank_ms;  /* of which: CUR rank steps (Parts 1 and 2) */
+  double time_build_ms; /*           preconditioner builds */
+  double time_lsqr_ms;  /*           LSQR phases and residual checks */
 } aplicur_stats;
 
 /* Fill `opt` with the defaults above. */
@@ -188,7 +198,8 @@ aplicur_status aplicur_get_stats(aplicur_handle h, aplicur_stats* st);
  * (0 none, 1 exact, 2 replay, 3 Paige-Saunders test 2, 4 test 1, 5 dynamic,
  * 6 tol, 7 maxit, 9 drift: the recurrence estimate passed tol but the FP64
  * residual did not, so the phase ends and the next one restarts from an
- * exactly formed residual), relative normal-equation residual at the phase end. */
+ * exactly formed residual; 10 inner: FP32-sum inner solve reduced its residual
+ * estimate by 1e-4), relative normal-equation residual at the phase end. */
 aplicur_status aplicur_get_phase(aplicur_handle h, int32_t k, int32_t* ell, int64_t* iters,
                                  int32_t* reason, double* ne_res);
 

@@ -12,10 +12,10 @@ import os
 from . import build as _build
 
 REASONS = {0: "none", 1: "exact", 2: "replay", 3: "ps_test2", 4: "ps_test1", 5: "dynamic",
-           6: "tol", 7: "maxit", 9: "drift"}
+           6: "tol", 7: "maxit", 9: "drift", 10: "inner"}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
           6: "ETIMEOUT"}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF32 = 0, 1, 2
 
 
 class AplicurError(RuntimeError):
@@ -51,7 +51,8 @@ class Stats(C.Structure):
     _fields_ = [("iters", C.c_int64), ("ell", C.c_int32), ("nphases", C.c_int32),
                 ("nsteps", C.c_int32), ("converged", C.c_int32), ("ne_res", C.c_double),
                 ("rho", C.c_double), ("time_setup_ms", C.c_double),
-                ("time_solve_ms", C.c_double)]
+                ("time_solve_ms", C.c_double), ("time_rank_ms", C.c_double),
+                ("time_build_ms", C.c_double), ("time_lsqr_ms", C.c_double)]
 
 
 # every entry point of include/aplicur.h: name -> (restype, argtypes)

@@ -74,10 +74,6 @@ __global__ void add2d_kernel(int64_t rows, int64_t cols, const double* src, int6
   const int64_t r = e % rows, c = e / rows;
   dst[r + c * ldd] += src[r + c * lds];
 }
-__global__ void to_f32_kernel(int64_t n, const double* s, float* d) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = (float)s[i];
-}
 __global__ void scale_kernel(int64_t n, const double* s, double a, double* d) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = a * s[i];
@@ -134,7 +130,6 @@ struct aplicur_ctx {
   LuppWork lw;
   // preconditioner
   DBuf<double> Mb, VM, sigma, V64, coef, coef2;
-  DBuf<float> V32;
   PrecondDev P;
   double sighat = 1.0;
   std::vector<double> sig_host;
@@ -470,15 +465,7 @@ void build_preconditioner(aplicur_ctx* h) {
   P.coef2 = h->coef2.p;
   P.normP = std::sqrt(h->sig_host[0] * h->sig_host[0] + d2) / h->sighat;
   P.sig_ell = sl;
-  if (h->opt.precision == APLICUR_PREC_MIXED) {
-    h->V32.alloc((size_t)n * L, st);
-    to_f32_kernel<<<(unsigned)cdiv(n * L, 256), 256, 0, st>>>(n * L, h->V64.p, h->V32.p);
-    APL_LAUNCH_CHECK();
-    P.fp32 = 1;
-    P.V32 = h->V32.p;
-  } else {
-    P.V64 = h->V64.p;
-  }
+  P.V64 = h->V64.p;
   h->P = P;
   APL_CUDA(cudaStreamSynchronize(st));
 }
@@ -527,10 +514,17 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
   };
   if (h->norm_Atb == 0.0) return finish(0.0);
   double d_cur = INFINITY;
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t0) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  };
+  h->stats.time_rank_ms = h->stats.time_build_ms = h->stats.time_lsqr_ms = 0.0;
   while (true) {
     double rho = 0, margin = INFINITY;
     bool exhausted = false;
+    auto t0 = clk::now();
     rank_step(h, &rho, &exhausted, &margin);
+    h->stats.time_rank_ms += ms_since(t0);
     h->stats.rho = rho;
     const bool full = h->ell >= h->kmax;
     const double rho_eff = exhausted ? 0.0 : rho;
@@ -544,11 +538,15 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
     }
     h->steps.push_back(StepRec{h->ell, rho, rebuild ? 1 : 0, margin});
     if (rebuild && h->ell > 0) {
+      t0 = clk::now();
       build_preconditioner(h);
+      h->stats.time_build_ms += ms_since(t0);
       long long it = 0;
       int reason = 0;
+      t0 = clk::now();
       ne = run_phase(h, last ? INFINITY : h->opt.nu_lsqr, tol, std::max(0LL, maxit - total),
                      next_fixed(), &it, &reason);
+      h->stats.time_lsqr_ms += ms_since(t0);
       total += it;
       if (!h->replay && ne <= tol) return finish(ne);
       d_cur = rho_eff - h->eps_cur;
@@ -564,7 +562,9 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
     const double prev = ne;
     long long it = 0;
     int reason = 0;
+    auto t1 = clk::now();
     ne = run_phase(h, INFINITY, tol, std::max(0LL, maxit - total), next_fixed(), &it, &reason);
+    h->stats.time_lsqr_ms += ms_since(t1);
     total += it;
     ++extra;
     if (!h->replay && (it == 0 || ne > 0.5 * prev)) break;
@@ -643,6 +643,8 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
     else h->opt.replay_nsteps = 0;
     APL_REQUIRE(h->opt.xi >= 1 && h->opt.normest_r >= 1 && h->opt.check_gap >= 1, "bad options");
     APL_REQUIRE(h->opt.graph_iters >= 0 && h->opt.graph_iters <= 4096, "bad graph_iters");
+    APL_REQUIRE(h->opt.precision >= APLICUR_PREC_FP64 && h->opt.precision <= APLICUR_PREC_DF32,
+                "bad precision");
     if (stream) h->st = (cudaStream_t)stream;
     else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
     cudaStream_t st = h->st;
@@ -702,7 +704,7 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
     APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->eng.setup(st, h->A, h->opt.precision == APLICUR_PREC_MIXED ? 1 : 0, h->opt.graph_iters);
+    h->eng.setup(st, h->A, h->opt.precision, h->opt.graph_iters);
     h->eng.set_profile(h->opt.profile != 0);
     // ||A^T b|| in FP64
     h->eng.matvec(1, b, h->tmp_n.p, 1.0, 0.0, true);
@@ -775,7 +777,7 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
       total += r.iters;
       ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
       h->phases.push_back(PhaseRec{0, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
-      if (r.reason != R_DRIFT || ne <= tol) break;
+      if ((r.reason != R_DRIFT && r.reason != R_INNER) || ne <= tol) break;
     }
     h->stats.iters = total;
     h->stats.ne_res = ne;
@@ -935,7 +937,7 @@ aplicur_status aplicur_apply_preconditioner(aplicur_handle h, const double* w, d
 aplicur_status aplicur_matvec(aplicur_handle h, int32_t trans, const double* x, double* y) {
   if (!h || !x || !y) return APLICUR_EINVAL;
   return guarded(h, [&]() -> int {
-    h->eng.matvec(trans ? 1 : 0, x, y, 1.0, 0.0, h->opt.precision != APLICUR_PREC_MIXED);
+    h->eng.matvec(trans ? 1 : 0, x, y, 1.0, 0.0, h->opt.precision == APLICUR_PREC_FP64);
     APL_CUDA(cudaStreamSynchronize(h->st));
     return ST_OK;
   });

@@ -8,6 +8,14 @@
 // in the device-resident control block, so no extra pass rescales them.  The last
 // block of each reducing kernel finishes the scalar recurrences (Givens rotation,
 // Paige-Saunders and dynamic stopping tests) on the device.
+//
+// Products with A come in three modes:
+//   0  FP64 products and sums (FP32-stored values are promoted exactly);
+//   1  FP32 products and FP32 sums per thread (FP64 across threads);
+//   2  compensated FP32: each operand vector is split into FP32 hi + lo parts once per
+//      iteration; a * hi is made exact by an FMA residual, the running sum is kept as an
+//      unevaluated pair (Knuth's TwoSum), so the result is accurate to about 2^-44
+//      relative to sum |a_i z_i| while every instruction is an FP32 one.
 #include <cstddef>
 #include <vector>
 
@@ -18,6 +26,32 @@ namespace apl {
 namespace {
 
 constexpr int NT = 256;
+
+// ---- compensated FP32 accumulation ----------------------------------------------------
+
+struct DF {
+  float s, c;
+};
+
+// s + c += a * (h + l): exact product a*h = p + e by FMA, TwoSum of s and p.  Explicit
+// round-to-nearest intrinsics keep the compiler from contracting the error terms.
+__device__ __forceinline__ void df_fma(DF& acc, float a, float h, float l) {
+  const float p = __fmul_rn(a, h);
+  const float e = __fmaf_rn(a, h, -p);
+  const float t = __fadd_rn(acc.s, p);
+  const float bv = __fsub_rn(t, acc.s);
+  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  acc.s = t;
+  acc.c = __fmaf_rn(a, l, __fadd_rn(acc.c, __fadd_rn(err, e)));
+}
+
+__device__ __forceinline__ double df_val(const DF& a) { return (double)a.s + (double)a.c; }
+
+__device__ __forceinline__ void split(double v, float* hi, float* lo, int64_t i) {
+  const float h = __double2float_rn(v);
+  hi[i] = h;
+  lo[i] = __double2float_rn(v - (double)h);
+}
 
 __device__ __forceinline__ bool dyn_stop(double phibar_prev, double phibar, double rate1,
                                          double nu, double sig_ell) {
@@ -51,6 +85,7 @@ __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
     c->pending = 1;
     c->init = 0;
     c->it = 0;
+    c->arnorm0 = alpha * c->beta1;
     if (alpha == 0.0) { c->done = 1; c->reason = R_EXACT; }
     return;
   }
@@ -82,6 +117,8 @@ __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
     reason = R_PS2;
   } else if (phibar <= c->eps * c->beta1) {
     reason = R_PS1;
+  } else if (c->inner > 0.0 && phibar * alpha * fabs(cc) <= c->inner * c->arnorm0) {
+    reason = R_INNER;
   } else if (dyn_stop(phibar_prev, phibar, c->rate1, c->nu, c->sig_ell)) {
     reason = R_DYNAMIC;
   } else if (c->tol > 0.0 && it >= c->next_check &&
@@ -93,13 +130,39 @@ __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
   if (reason != R_NONE) { c->done = 1; c->reason = reason; }
 }
 
-// ---- K1 -------------------------------------------------------------------------------
+// ---- per-element product helpers for the three modes ----------------------------------
 
-template <typename TA, typename TAcc>
+template <int MODE>
+struct Acc;
+template <>
+struct Acc<0> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double x, float, float) { v = fma(a, x, v); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct Acc<1> {
+  float v = 0.f;
+  __device__ __forceinline__ void add(float a, double, float h, float) { v = fmaf(a, h, v); }
+  __device__ __forceinline__ double get() const { return (double)v; }
+};
+template <>
+struct Acc<2> {
+  DF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float a, double, float h, float l) { df_fma(v, a, h, l); }
+  __device__ __forceinline__ double get() const { return df_val(v); }
+};
+
+// ---- K1: rows of A, two rows per warp -------------------------------------------------
+
+template <typename TA, int MODE, bool VEC>
 __global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
                                                const TA* __restrict__ A,
                                                const double* __restrict__ z,
-                                               double* __restrict__ u, LsqrCtl* ctl,
+                                               const float* __restrict__ zh,
+                                               const float* __restrict__ zl,
+                                               double* __restrict__ u, float* __restrict__ uh,
+                                               float* __restrict__ ul, LsqrCtl* ctl,
                                                double* __restrict__ red, int init) {
   __shared__ double sh[NT / 32];
   if (ctl->done) return;
@@ -110,22 +173,54 @@ __global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   double ss = 0.0;
-  for (int64_t i = warp; i < m; i += nwarps) {
-    const TA* a = A + i * ld;
-    TAcc acc = 0;
-    int64_t j = lane;
-    for (; j + 96 < n; j += 128) {
-      acc += (TAcc)a[j] * (TAcc)z[j];
-      acc += (TAcc)a[j + 32] * (TAcc)z[j + 32];
-      acc += (TAcc)a[j + 64] * (TAcc)z[j + 64];
-      acc += (TAcc)a[j + 96] * (TAcc)z[j + 96];
+  for (int64_t i0 = 2 * warp; i0 < m; i0 += 2 * nwarps) {
+    const bool two = i0 + 1 < m;
+    const TA* a0 = A + i0 * ld;
+    const TA* a1 = A + (two ? i0 + 1 : i0) * ld;
+    Acc<MODE> s0, s1;
+    int64_t jt = 0;
+    if constexpr (VEC && MODE != 0 && sizeof(TA) == 4) {
+      const int64_t n4 = n >> 2;
+      const float4* p0 = reinterpret_cast<const float4*>(a0);
+      const float4* p1 = reinterpret_cast<const float4*>(a1);
+      const float4* hv = reinterpret_cast<const float4*>(zh);
+      const float4* lv = reinterpret_cast<const float4*>(zl);
+      for (int64_t q = lane; q < n4; q += 32) {
+        const float4 x0 = __ldcs(p0 + q);
+        const float4 x1 = __ldcs(p1 + q);
+        const float4 h = hv[q];
+        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == 2) l = lv[q];
+        s0.add(x0.x, 0.0, h.x, l.x); s0.add(x0.y, 0.0, h.y, l.y);
+        s0.add(x0.z, 0.0, h.z, l.z); s0.add(x0.w, 0.0, h.w, l.w);
+        s1.add(x1.x, 0.0, h.x, l.x); s1.add(x1.y, 0.0, h.y, l.y);
+        s1.add(x1.z, 0.0, h.z, l.z); s1.add(x1.w, 0.0, h.w, l.w);
+      }
+      jt = n4 << 2;
     }
-    for (; j < n; j += 32) acc += (TAcc)a[j] * (TAcc)z[j];
-    const double s = warp_sum((double)acc);
+    for (int64_t j = jt + lane; j < n; j += 32) {
+      if constexpr (MODE == 0) {
+        s0.add((double)a0[j], z[j], 0.f, 0.f);
+        s1.add((double)a1[j], z[j], 0.f, 0.f);
+      } else {
+        const float l = MODE == 2 ? zl[j] : 0.f;
+        s0.add((float)a0[j], 0.0, zh[j], l);
+        s1.add((float)a1[j], 0.0, zh[j], l);
+      }
+    }
+    const double d0 = warp_sum(s0.get());
+    const double d1 = warp_sum(s1.get());
     if (lane == 0) {
-      const double val = ca * s + cu * u[i];
-      u[i] = val;
-      ss += val * val;
+      const double v0 = ca * d0 + cu * u[i0];
+      u[i0] = v0;
+      ss += v0 * v0;
+      if (uh) split(v0, uh, ul, i0);
+      if (two) {
+        const double v1 = ca * d1 + cu * u[i0 + 1];
+        u[i0 + 1] = v1;
+        ss += v1 * v1;
+        if (uh) split(v1, uh, ul, i0 + 1);
+      }
     }
   }
   for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
@@ -140,12 +235,15 @@ __global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
   if (threadIdx.x == 0) finalize_beta(ctl, tot, init);
 }
 
-template <typename TA, typename TAcc>
+template <typename TA, int MODE>
 __global__ void __launch_bounds__(NT) k1_csr(int64_t m, int64_t n, const int* __restrict__ rowptr,
                                              const int* __restrict__ colidx,
                                              const TA* __restrict__ vals,
                                              const double* __restrict__ z,
-                                             double* __restrict__ u, LsqrCtl* ctl,
+                                             const float* __restrict__ zh,
+                                             const float* __restrict__ zl,
+                                             double* __restrict__ u, float* __restrict__ uh,
+                                             float* __restrict__ ul, LsqrCtl* ctl,
                                              double* __restrict__ red, int init) {
   __shared__ double sh[NT / 32];
   if (ctl->done) return;
@@ -157,10 +255,15 @@ __global__ void __launch_bounds__(NT) k1_csr(int64_t m, int64_t n, const int* __
        i += (int64_t)gridDim.x * NT) {
     double val;
     if (i < m) {
-      TAcc acc = 0;
+      Acc<MODE> acc;
       const int e1 = rowptr[i + 1];
-      for (int e = rowptr[i]; e < e1; ++e) acc += (TAcc)vals[e] * (TAcc)z[colidx[e]];
-      val = ca * (double)acc + cu * u[i];
+      for (int e = rowptr[i]; e < e1; ++e) {
+        const int c = colidx[e];
+        if constexpr (MODE == 0) acc.add((double)vals[e], z[c], 0.f, 0.f);
+        else acc.add((float)vals[e], 0.0, zh[c], MODE == 2 ? zl[c] : 0.f);
+      }
+      val = ca * acc.get() + cu * u[i];
+      if (uh) split(val, uh, ul, i);
     } else {
       val = ca * delta * z[i - m] + cu * u[i];
     }
@@ -180,7 +283,7 @@ __global__ void __launch_bounds__(NT) k1_csr(int64_t m, int64_t n, const int* __
 // v and z are the same buffer when there is no preconditioner: no __restrict__ here.
 __device__ __forceinline__ double k2_tail(int64_t j, double gj, const LsqrCtl* c, int init,
                                           int fused, double* g, double* v, double* z, double* d,
-                                          double* x) {
+                                          double* x, float* zh, float* zl) {
   const int pend = c->pending;
   const double zs = c->zs;
   if (pend == 1) {
@@ -195,29 +298,37 @@ __device__ __forceinline__ double k2_tail(int64_t j, double gj, const LsqrCtl* c
   if (fused) {
     const double vn = init ? gj : gj - c->beta * (v[j] * zs);
     v[j] = vn;
+    if (zh) split(vn, zh, zl, j);
     return vn * vn;
   }
   g[j] = gj;
   return 0.0;
 }
 
-template <typename TA, typename TAcc>
+template <typename TA, int MODE>
 __global__ void __launch_bounds__(NT) k2_csr(int64_t m, int64_t n, const int* __restrict__ colptr,
                                              const int* __restrict__ rowidx,
                                              const TA* __restrict__ cvals,
-                                             const double* __restrict__ u, double* g, double* v,
-                                             double* z, double* d, double* x, LsqrCtl* ctl,
-                                             double* __restrict__ red, int init, int fused) {
+                                             const double* __restrict__ u,
+                                             const float* __restrict__ uh,
+                                             const float* __restrict__ ul, double* g, double* v,
+                                             double* z, double* d, double* x, float* zh, float* zl,
+                                             LsqrCtl* ctl, double* __restrict__ red, int init,
+                                             int fused) {
   __shared__ double sh[NT / 32];
   if (ctl->done) return;
   const double us = ctl->us, delta = ctl->delta;
   double ss = 0.0;
   for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
-    TAcc acc = 0;
+    Acc<MODE> acc;
     const int e1 = colptr[j + 1];
-    for (int e = colptr[j]; e < e1; ++e) acc += (TAcc)cvals[e] * (TAcc)u[rowidx[e]];
-    const double gj = us * ((double)acc + delta * u[m + j]);
-    ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x);
+    for (int e = colptr[j]; e < e1; ++e) {
+      const int r = rowidx[e];
+      if constexpr (MODE == 0) acc.add((double)cvals[e], u[r], 0.f, 0.f);
+      else acc.add((float)cvals[e], 0.0, uh[r], MODE == 2 ? ul[r] : 0.f);
+    }
+    const double gj = us * (acc.get() + delta * u[m + j]);
+    ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x, zh, zl);
   }
   if (!fused) return;
   const double b = block_sum(ss, sh);
@@ -227,29 +338,64 @@ __global__ void __launch_bounds__(NT) k2_csr(int64_t m, int64_t n, const int* __
   if (threadIdx.x == 0) finalize_alpha(ctl, tot, init);
 }
 
-// Dense A^T u: per (column block, row chunk) partial sums.
-template <typename TA, typename TAcc>
+// Dense A^T u: per (column block, row chunk) partial sums; four columns per thread in
+// the vector path.
+template <typename TA, int MODE, bool VEC>
 __global__ void __launch_bounds__(NT) k2a_dense(int64_t m, int64_t n, int64_t ld,
                                                 const TA* __restrict__ A,
                                                 const double* __restrict__ u,
+                                                const float* __restrict__ uh,
+                                                const float* __restrict__ ul,
                                                 double* __restrict__ part, int64_t rows_per,
                                                 const LsqrCtl* ctl) {
   if (ctl && ctl->done) return;
-  const int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x;
-  if (j >= n) return;
+  const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
   const int64_t r1 = r0 + rows_per < m ? r0 + rows_per : m;
-  TAcc acc = 0;
-  for (int64_t i = r0; i < r1; ++i) acc += (TAcc)A[i * ld + j] * (TAcc)u[i];
-  part[(int64_t)blockIdx.y * n + j] = (double)acc;
+  double* out = part + (int64_t)blockIdx.y * n;
+  if constexpr (VEC && MODE != 0 && sizeof(TA) == 4) {
+    const int64_t j = 4 * t;
+    if (j + 3 < n) {
+      Acc<MODE> a0, a1, a2, a3;
+      for (int64_t i = r0; i < r1; ++i) {
+        const float4 x = __ldcs(reinterpret_cast<const float4*>(A + i * ld + j));
+        const float h = uh[i];
+        const float l = MODE == 2 ? ul[i] : 0.f;
+        a0.add(x.x, 0.0, h, l);
+        a1.add(x.y, 0.0, h, l);
+        a2.add(x.z, 0.0, h, l);
+        a3.add(x.w, 0.0, h, l);
+      }
+      out[j] = a0.get();
+      out[j + 1] = a1.get();
+      out[j + 2] = a2.get();
+      out[j + 3] = a3.get();
+    } else {
+      for (int64_t jj = j; jj < n; ++jj) {
+        Acc<MODE> a;
+        for (int64_t i = r0; i < r1; ++i)
+          a.add((float)A[i * ld + jj], 0.0, uh[i], MODE == 2 ? ul[i] : 0.f);
+        out[jj] = a.get();
+      }
+    }
+  } else {
+    const int64_t j = t;
+    if (j >= n) return;
+    Acc<MODE> a;
+    for (int64_t i = r0; i < r1; ++i) {
+      if constexpr (MODE == 0) a.add((double)A[i * ld + j], u[i], 0.f, 0.f);
+      else a.add((float)A[i * ld + j], 0.0, uh[i], MODE == 2 ? ul[i] : 0.f);
+    }
+    out[j] = a.get();
+  }
 }
 
 __global__ void __launch_bounds__(NT) k2b_dense(int64_t m, int64_t n, int rchunks,
                                                 const double* __restrict__ part,
                                                 const double* __restrict__ u, double* g,
                                                 double* v, double* z, double* d, double* x,
-                                                LsqrCtl* ctl, double* __restrict__ red, int init,
-                                                int fused) {
+                                                float* zh, float* zl, LsqrCtl* ctl,
+                                                double* __restrict__ red, int init, int fused) {
   __shared__ double sh[NT / 32];
   if (ctl->done) return;
   const double us = ctl->us, delta = ctl->delta;
@@ -258,7 +404,7 @@ __global__ void __launch_bounds__(NT) k2b_dense(int64_t m, int64_t n, int rchunk
     double acc = 0.0;
     for (int c = 0; c < rchunks; ++c) acc += part[(int64_t)c * n + j];
     const double gj = us * (acc + delta * u[m + j]);
-    ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x);
+    ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x, zh, zl);
   }
   if (!fused) return;
   const double b = block_sum(ss, sh);
@@ -268,11 +414,10 @@ __global__ void __launch_bounds__(NT) k2b_dense(int64_t m, int64_t n, int rchunk
   if (threadIdx.x == 0) finalize_alpha(ctl, tot, init);
 }
 
-// ---- preconditioner passes ------------------------------------------------------------
+// ---- preconditioner passes (FP64 Vhat) -------------------------------------------------
 
-template <typename TV, typename TAcc>
 __global__ void __launch_bounds__(128) k3_partial(int64_t n, int ell, int64_t ldv,
-                                                  const TV* __restrict__ V,
+                                                  const double* __restrict__ V,
                                                   const double* __restrict__ w,
                                                   double* __restrict__ tpart, int64_t rows_per,
                                                   const LsqrCtl* ctl) {
@@ -281,9 +426,9 @@ __global__ void __launch_bounds__(128) k3_partial(int64_t n, int ell, int64_t ld
   if (k >= ell) return;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per;
   const int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
-  TAcc acc = 0;
-  for (int64_t i = r0; i < r1; ++i) acc += (TAcc)V[i * ldv + k] * (TAcc)w[i];
-  tpart[(int64_t)blockIdx.y * ell + k] = (double)acc;
+  double acc = 0.0;
+  for (int64_t i = r0; i < r1; ++i) acc = fma(V[i * ldv + k], w[i], acc);
+  tpart[(int64_t)blockIdx.y * ell + k] = acc;
 }
 
 __global__ void k3_reduce(int ell, int chunks, const double* __restrict__ tpart,
@@ -299,15 +444,14 @@ __global__ void k3_reduce(int ell, int chunks, const double* __restrict__ tpart,
 }
 
 // Expansion, one warp per row: out1 = w + V ct, out2 = w + V c2t.  In the LSQR phase
-// also subtracts beta v / beta z and reduces ||v'||^2.
-template <typename TV, typename TAcc>
+// also subtracts beta v / beta z, writes the FP32 split of z' and reduces ||v'||^2.
 __global__ void __launch_bounds__(NT) k4_expand(int64_t n, int ell, int64_t ldv,
-                                                const TV* __restrict__ V,
+                                                const double* __restrict__ V,
                                                 const double* __restrict__ ct,
                                                 const double* __restrict__ c2t,
                                                 const double* __restrict__ w, double* out1,
-                                                double* out2, LsqrCtl* ctl,
-                                                double* __restrict__ red, int init) {
+                                                double* out2, float* zh, float* zl,
+                                                LsqrCtl* ctl, double* __restrict__ red, int init) {
   __shared__ double sh[NT / 32];
   if (ctl && ctl->done) return;
   double beta = 0.0, zs = 0.0;
@@ -317,15 +461,15 @@ __global__ void __launch_bounds__(NT) k4_expand(int64_t n, int ell, int64_t ldv,
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   double ss = 0.0;
   for (int64_t i = warp; i < n; i += nwarps) {
-    const TV* vr = V + i * ldv;
-    TAcc s1 = 0, s2 = 0;
+    const double* vr = V + i * ldv;
+    double s1 = 0.0, s2 = 0.0;
     for (int k = lane; k < ell; k += 32) {
-      const TAcc vv = (TAcc)vr[k];
-      s1 += vv * (TAcc)ct[k];
-      if (out2) s2 += vv * (TAcc)c2t[k];
+      const double vv = vr[k];
+      s1 = fma(vv, ct[k], s1);
+      if (out2) s2 = fma(vv, c2t[k], s2);
     }
-    const double a1 = warp_sum((double)s1);
-    const double a2 = out2 ? warp_sum((double)s2) : 0.0;
+    const double a1 = warp_sum(s1);
+    const double a2 = out2 ? warp_sum(s2) : 0.0;
     if (lane == 0) {
       const double wi = w[i];
       double o1 = wi + a1;
@@ -335,6 +479,7 @@ __global__ void __launch_bounds__(NT) k4_expand(int64_t n, int ell, int64_t ldv,
         double o2 = wi + a2;
         if (ctl && !init) o2 -= beta * (out2[i] * zs);
         out2[i] = o2;
+        if (zh) split(o2, zh, zl, i);
       }
       ss += o1 * o1;
     }
@@ -354,43 +499,64 @@ __global__ void flush_x_kernel(int64_t n, double* x, const double* d, const Lsqr
   if (j < n) x[j] += ctl->xc * d[j];
 }
 
-template <typename TA, typename TAcc>
+__global__ void split_kernel(int64_t n, const double* v, float* hi, float* lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) split(v[i], hi, lo, i);
+}
+
+template <typename TA, int MODE>
 __global__ void __launch_bounds__(NT) mv_dense_rows(int64_t m, int64_t n, int64_t ld,
                                                     const TA* __restrict__ A,
-                                                    const double* __restrict__ x, double* y,
+                                                    const double* __restrict__ x,
+                                                    const float* __restrict__ xh,
+                                                    const float* __restrict__ xl, double* y,
                                                     double alpha, double beta) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   for (int64_t i = warp; i < m; i += nwarps) {
     const TA* a = A + i * ld;
-    TAcc acc = 0;
-    for (int64_t j = lane; j < n; j += 32) acc += (TAcc)a[j] * (TAcc)x[j];
-    const double s = warp_sum((double)acc);
+    Acc<MODE> acc;
+    for (int64_t j = lane; j < n; j += 32) {
+      if constexpr (MODE == 0) acc.add((double)a[j], x[j], 0.f, 0.f);
+      else acc.add((float)a[j], 0.0, xh[j], MODE == 2 ? xl[j] : 0.f);
+    }
+    const double s = warp_sum(acc.get());
     if (lane == 0) y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
   }
 }
 
-template <typename TA, typename TAcc>
+template <typename TA, int MODE>
 __global__ void mv_csr_rows(int64_t m, const int* __restrict__ rowptr,
                             const int* __restrict__ colidx, const TA* __restrict__ vals,
-                            const double* __restrict__ x, double* y, double alpha, double beta) {
+                            const double* __restrict__ x, const float* __restrict__ xh,
+                            const float* __restrict__ xl, double* y, double alpha, double beta) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  TAcc acc = 0;
-  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) acc += (TAcc)vals[e] * (TAcc)x[colidx[e]];
-  y[i] = beta == 0.0 ? alpha * (double)acc : alpha * (double)acc + beta * y[i];
+  Acc<MODE> acc;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int c = colidx[e];
+    if constexpr (MODE == 0) acc.add((double)vals[e], x[c], 0.f, 0.f);
+    else acc.add((float)vals[e], 0.0, xh[c], MODE == 2 ? xl[c] : 0.f);
+  }
+  const double s = acc.get();
+  y[i] = beta == 0.0 ? alpha * s : alpha * s + beta * y[i];
 }
 
-template <typename TA, typename TAcc>
+template <typename TA, int MODE>
 __global__ void mv_csc_cols(int64_t n, const int* __restrict__ colptr,
                             const int* __restrict__ rowidx, const TA* __restrict__ cvals,
-                            const double* __restrict__ x, double* y) {
+                            const double* __restrict__ x, const float* __restrict__ xh,
+                            const float* __restrict__ xl, double* y) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  TAcc acc = 0;
-  for (int e = colptr[j]; e < colptr[j + 1]; ++e) acc += (TAcc)cvals[e] * (TAcc)x[rowidx[e]];
-  y[j] = (double)acc;
+  Acc<MODE> acc;
+  for (int e = colptr[j]; e < colptr[j + 1]; ++e) {
+    const int r = rowidx[e];
+    if constexpr (MODE == 0) acc.add((double)cvals[e], x[r], 0.f, 0.f);
+    else acc.add((float)cvals[e], 0.0, xh[r], MODE == 2 ? xl[r] : 0.f);
+  }
+  y[j] = acc.get();
 }
 
 __global__ void colsum_kernel(int64_t n, int rchunks, const double* part, double* y) {
@@ -425,14 +591,77 @@ __global__ void norm2_kernel(int64_t n, const double* v, double* red, double* ou
 
 inline int sm_blocks() { return 152 * 8; }
 
+// Launch helpers dispatching (format, dtype, mode, vector) to template instances.
+template <int MODE>
+void launch_k1_mode(cudaStream_t st, const MatView& A, bool vec, int blocks, const double* z,
+                    const float* zh, const float* zl, double* u, float* uh, float* ul, LsqrCtl* c,
+                    double* red, int init) {
+  if (A.fmt == 0) {
+    if (A.dtype == 0) {
+      k1_dense<double, 0, false><<<blocks, NT, 0, st>>>(A.m, A.n, A.ld, (const double*)A.vals, z,
+                                                        zh, zl, u, uh, ul, c, red, init);
+    } else if (vec) {
+      k1_dense<float, MODE, true><<<blocks, NT, 0, st>>>(A.m, A.n, A.ld, (const float*)A.vals, z,
+                                                         zh, zl, u, uh, ul, c, red, init);
+    } else {
+      k1_dense<float, MODE, false><<<blocks, NT, 0, st>>>(A.m, A.n, A.ld, (const float*)A.vals, z,
+                                                          zh, zl, u, uh, ul, c, red, init);
+    }
+  } else {
+    if (A.dtype == 0)
+      k1_csr<double, 0><<<blocks, NT, 0, st>>>(A.m, A.n, A.rowptr, A.colidx,
+                                               (const double*)A.vals, z, zh, zl, u, uh, ul, c,
+                                               red, init);
+    else
+      k1_csr<float, MODE><<<blocks, NT, 0, st>>>(A.m, A.n, A.rowptr, A.colidx,
+                                                 (const float*)A.vals, z, zh, zl, u, uh, ul, c,
+                                                 red, init);
+  }
+}
+
+template <int MODE>
+void launch_k2_mode(cudaStream_t st, const MatView& A, bool vec, int blocks, int rchunks,
+                    double* part, const double* u, const float* uh, const float* ul, double* g,
+                    double* v, double* z, double* d, double* x, float* zh, float* zl, LsqrCtl* c,
+                    double* red, int init, int fused) {
+  if (A.fmt == 0) {
+    const int64_t rows_per = cdiv(A.m, rchunks);
+    if (A.dtype == 0) {
+      dim3 grid((unsigned)cdiv(A.n, NT), (unsigned)rchunks);
+      k2a_dense<double, 0, false><<<grid, NT, 0, st>>>(A.m, A.n, A.ld, (const double*)A.vals, u,
+                                                       uh, ul, part, rows_per, c);
+    } else if (vec && MODE != 0) {
+      dim3 grid((unsigned)cdiv(cdiv(A.n, 4), NT), (unsigned)rchunks);
+      k2a_dense<float, MODE, true><<<grid, NT, 0, st>>>(A.m, A.n, A.ld, (const float*)A.vals, u,
+                                                        uh, ul, part, rows_per, c);
+    } else {
+      dim3 grid((unsigned)cdiv(A.n, NT), (unsigned)rchunks);
+      k2a_dense<float, MODE, false><<<grid, NT, 0, st>>>(A.m, A.n, A.ld, (const float*)A.vals, u,
+                                                         uh, ul, part, rows_per, c);
+    }
+    APL_LAUNCH_CHECK();
+    k2b_dense<<<blocks, NT, 0, st>>>(A.m, A.n, rchunks, part, u, g, v, z, d, x, zh, zl, c, red,
+                                     init, fused);
+  } else {
+    if (A.dtype == 0)
+      k2_csr<double, 0><<<blocks, NT, 0, st>>>(A.m, A.n, A.colptr, A.rowidx,
+                                               (const double*)A.cvals, u, uh, ul, g, v, z, d, x,
+                                               zh, zl, c, red, init, fused);
+    else
+      k2_csr<float, MODE><<<blocks, NT, 0, st>>>(A.m, A.n, A.colptr, A.rowidx,
+                                                 (const float*)A.cvals, u, uh, ul, g, v, z, d, x,
+                                                 zh, zl, c, red, init, fused);
+  }
+}
+
 }  // namespace
 
 // ======================================================================================
 
-void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mixed, int graph_iters) {
+void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_iters) {
   st_ = st;
   A_ = A;
-  mixed_ = mixed;
+  mode_ = A.dtype == 1 ? mode : 0;  // FP64-stored A always uses FP64 products
   graph_iters_ = graph_iters;
   m_ = A.m;
   n_ = A.n;
@@ -447,9 +676,17 @@ void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mixed, int graph_i
   scal_.alloc(4, st);
   cnt_.alloc(1, st);
   cnt_.zero(st);
+  if (mode_ != 0) {
+    zh_.alloc(n_, st);
+    zl_.alloc(n_, st);
+    uh_.alloc(std::max(m_, n_), st);
+    ul_.alloc(std::max(m_, n_), st);
+  }
+  vec_ = A.fmt == 0 && A.dtype == 1 && (A.ld % 4 == 0) &&
+         ((reinterpret_cast<uintptr_t>(A.vals) & 15) == 0);
   if (A.fmt == 0) {
-    k1_blocks_ = (int)std::min<int64_t>(cdiv(m_ * 32, NT), sm_blocks());
-    const int64_t cb = cdiv(n_, NT);
+    k1_blocks_ = (int)std::min<int64_t>(cdiv(cdiv(m_, 2) * 32, NT), sm_blocks());
+    const int64_t cb = vec_ ? cdiv(cdiv(n_, 4), NT) : cdiv(n_, NT);
     k2_rchunks_ = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, cb), cdiv(m_, 32)));
     k2_blocks_ = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
     part_.alloc((size_t)k2_rchunks_ * n_, st);
@@ -462,71 +699,37 @@ void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mixed, int graph_i
 }
 
 void LsqrEngine::launch_k1(bool init, const double* z) {
-  LsqrCtl* c = ctl_.p;
-  // the residual that starts a phase is always formed with FP64 products (in the mixed
-  // form this makes every warm restart one step of FP64 iterative refinement)
-  const bool f32 = mixed_ && !init;
-  if (A_.fmt == 0) {
-    if (A_.dtype == 0)
-      k1_dense<double, double><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals, z,
-                                                           u_.p, c, red_.p, init);
-    else if (f32)
-      k1_dense<float, float><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, z,
-                                                         u_.p, c, red_.p, init);
-    else
-      k1_dense<float, double><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, z,
-                                                          u_.p, c, red_.p, init);
-  } else {
-    if (A_.dtype == 0)
-      k1_csr<double, double><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.rowptr, A_.colidx,
-                                                         (const double*)A_.vals, z, u_.p, c,
-                                                         red_.p, init);
-    else if (f32)
-      k1_csr<float, float><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.rowptr, A_.colidx,
-                                                       (const float*)A_.vals, z, u_.p, c, red_.p,
-                                                       init);
-    else
-      k1_csr<float, double><<<k1_blocks_, NT, 0, st_>>>(m_, n_, A_.rowptr, A_.colidx,
-                                                        (const float*)A_.vals, z, u_.p, c, red_.p,
-                                                        init);
-  }
+  // the residual that starts a phase is always formed with FP64 products; in the FP32
+  // modes it also writes the split of u' for the following A^T pass
+  float* uh = mode_ ? uh_.p : nullptr;
+  float* ul = mode_ ? ul_.p : nullptr;
+  const int md = init ? 0 : mode_;
+  if (md == 0)
+    launch_k1_mode<0>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
+                      init);
+  else if (md == 1)
+    launch_k1_mode<1>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
+                      init);
+  else
+    launch_k1_mode<2>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
+                      init);
   APL_LAUNCH_CHECK();
 }
 
 void LsqrEngine::launch_k2(bool init, bool fused) {
-  LsqrCtl* c = ctl_.p;
   // the stored z' lives in v_ when there is no preconditioner (z = v)
   double* zbuf = fused ? v_.p : z_.p;
-  if (A_.fmt == 0) {
-    dim3 grid((unsigned)cdiv(n_, NT), (unsigned)k2_rchunks_);
-    const int64_t rows_per = cdiv(m_, k2_rchunks_);
-    if (A_.dtype == 0)
-      k2a_dense<double, double><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals, u_.p,
-                                                      part_.p, rows_per, c);
-    else if (mixed_)
-      k2a_dense<float, float><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, u_.p,
-                                                    part_.p, rows_per, c);
-    else
-      k2a_dense<float, double><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, u_.p,
-                                                     part_.p, rows_per, c);
-    APL_LAUNCH_CHECK();
-    k2b_dense<<<k2_blocks_, NT, 0, st_>>>(m_, n_, k2_rchunks_, part_.p, u_.p, g_.p, v_.p, zbuf,
-                                          d_.p, x_, c, red_.p, init, fused);
-  } else {
-    if (A_.dtype == 0)
-      k2_csr<double, double><<<k2_blocks_, NT, 0, st_>>>(m_, n_, A_.colptr, A_.rowidx,
-                                                         (const double*)A_.cvals, u_.p, g_.p,
-                                                         v_.p, zbuf, d_.p, x_, c, red_.p, init,
-                                                         fused);
-    else if (mixed_)
-      k2_csr<float, float><<<k2_blocks_, NT, 0, st_>>>(m_, n_, A_.colptr, A_.rowidx,
-                                                       (const float*)A_.cvals, u_.p, g_.p, v_.p,
-                                                       zbuf, d_.p, x_, c, red_.p, init, fused);
-    else
-      k2_csr<float, double><<<k2_blocks_, NT, 0, st_>>>(m_, n_, A_.colptr, A_.rowidx,
-                                                        (const float*)A_.cvals, u_.p, g_.p, v_.p,
-                                                        zbuf, d_.p, x_, c, red_.p, init, fused);
-  }
+  float* zh = (mode_ && fused) ? zh_.p : nullptr;
+  float* zl = (mode_ && fused) ? zl_.p : nullptr;
+  if (mode_ == 0)
+    launch_k2_mode<0>(st_, A_, vec_, k2_blocks_, k2_rchunks_, part_.p, u_.p, uh_.p, ul_.p, g_.p,
+                      v_.p, zbuf, d_.p, x_, zh, zl, ctl_.p, red_.p, init, fused);
+  else if (mode_ == 1)
+    launch_k2_mode<1>(st_, A_, vec_, k2_blocks_, k2_rchunks_, part_.p, u_.p, uh_.p, ul_.p, g_.p,
+                      v_.p, zbuf, d_.p, x_, zh, zl, ctl_.p, red_.p, init, fused);
+  else
+    launch_k2_mode<2>(st_, A_, vec_, k2_blocks_, k2_rchunks_, part_.p, u_.p, uh_.p, ul_.p, g_.p,
+                      v_.p, zbuf, d_.p, x_, zh, zl, ctl_.p, red_.p, init, fused);
   APL_LAUNCH_CHECK();
 }
 
@@ -537,24 +740,17 @@ void LsqrEngine::launch_pre(const PrecondDev& P, const double* w, double* o1, do
   const int64_t rows_per = cdiv(n_, tchunks_);
   dim3 grid((unsigned)kb, (unsigned)tchunks_);
   const LsqrCtl* c = in_phase ? ctl_.p : nullptr;
-  if (P.fp32)
-    k3_partial<float, float><<<grid, 128, 0, st_>>>(n_, ell, P.ldv, P.V32, w, tpart_.p, rows_per,
-                                                    c);
-  else
-    k3_partial<double, double><<<grid, 128, 0, st_>>>(n_, ell, P.ldv, P.V64, w, tpart_.p,
-                                                      rows_per, c);
+  k3_partial<<<grid, 128, 0, st_>>>(n_, ell, P.ldv, P.V64, w, tpart_.p, rows_per, c);
   APL_LAUNCH_CHECK();
   k3_reduce<<<(unsigned)cdiv(ell, 128), 128, 0, st_>>>(ell, tchunks_, tpart_.p, P.coef, P.coef2,
                                                        ct_.p, o2 ? c2t_.p : nullptr, c);
   APL_LAUNCH_CHECK();
   const int blocks = (int)std::min<int64_t>(cdiv(n_ * 32, NT), sm_blocks());
   LsqrCtl* cw = in_phase ? ctl_.p : nullptr;
-  if (P.fp32)
-    k4_expand<float, float><<<blocks, NT, 0, st_>>>(n_, ell, P.ldv, P.V32, ct_.p, c2t_.p, w, o1,
-                                                    o2, cw, red_.p, init);
-  else
-    k4_expand<double, double><<<blocks, NT, 0, st_>>>(n_, ell, P.ldv, P.V64, ct_.p, c2t_.p, w, o1,
-                                                      o2, cw, red_.p, init);
+  float* zh = (in_phase && mode_) ? zh_.p : nullptr;
+  float* zl = (in_phase && mode_) ? zl_.p : nullptr;
+  k4_expand<<<blocks, NT, 0, st_>>>(n_, ell, P.ldv, P.V64, ct_.p, c2t_.p, w, o1, o2, zh, zl, cw,
+                                    red_.p, init);
   APL_LAUNCH_CHECK();
 }
 
@@ -577,8 +773,6 @@ void LsqrEngine::ensure_events(int n) {
   }
 }
 
-// Iteration i of a captured graph records events 4i..4i+3 around K1, K2 and the
-// preconditioner passes.
 void LsqrEngine::launch_iteration(const PrecondDev& P, bool init) {
   const bool pre = P.ell > 0;
   launch_k1(init, init ? x_ : (pre ? z_.p : v_.p));
@@ -627,6 +821,11 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     ct_.alloc(P.ell, st_);
     c2t_.alloc(P.ell, st_);
   }
+  // In the FP32-sum mode each phase is the inner solve of an FP64 iterative refinement:
+  // it stops once the estimate of ||Abar^T rbar|| fell by 1e-4 from its phase-start value
+  // (FP32 products cannot resolve much more), and the next phase restarts from an
+  // exactly formed residual.
+  const double eps = a.eps;
   // state
   APL_CUDA(cudaMemcpyAsync(u_.p, a.rhs_top, m_ * sizeof(double), cudaMemcpyDeviceToDevice, st_));
   if (a.rhs_bot)
@@ -640,7 +839,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   LsqrCtl h{};
   h.init = 1;
   h.delta = sqrt(a.mu);
-  h.eps = a.eps;
+  h.eps = eps;
   h.nu = a.nu;
   h.sig_ell = P.sig_ell;
   h.tol = a.tol;
@@ -650,6 +849,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   h.maxit = a.maxit;
   h.next_check = 0;
   h.use_p = pre ? 1 : 0;
+  h.inner = (mode_ == 1 && a.fixed_len < 0) ? 1e-4 : 0.0;
   APL_CUDA(cudaMemcpyAsync(ctl_.p, &h, sizeof(LsqrCtl), cudaMemcpyHostToDevice, st_));
   launch_iteration(P, true);
   APL_CUDA(cudaMemcpyAsync(&h, ctl_.p, sizeof(LsqrCtl), cudaMemcpyDeviceToHost, st_));
@@ -668,15 +868,15 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   {
     // algorithmic bytes of one launch of each hot-loop kernel
     const double va = A_.dtype == 0 ? 8.0 : 4.0;
+    const double sv = mode_ == 1 ? 4.0 : 8.0;  // operand vector bytes per element
     if (A_.fmt == 0) {
-      prof.bytes[0] = (double)m_ * n_ * va + 8.0 * n_ + 16.0 * (m_ + n_);
-      prof.bytes[1] = (double)m_ * n_ * va + 8.0 * (m_ + n_) + 48.0 * n_;
+      prof.bytes[0] = (double)m_ * n_ * va + sv * n_ + 16.0 * (m_ + n_) + (mode_ ? 8.0 * m_ : 0);
+      prof.bytes[1] = (double)m_ * n_ * va + sv * m_ + 8.0 * n_ + 48.0 * n_;
     } else {
-      prof.bytes[0] = (double)A_.nnz * (va + 4) + 4.0 * (m_ + 1) + 8.0 * n_ + 16.0 * (m_ + n_);
-      prof.bytes[1] = (double)A_.nnz * (va + 4) + 4.0 * (n_ + 1) + 8.0 * (m_ + n_) + 48.0 * n_;
+      prof.bytes[0] = (double)A_.nnz * (va + 4) + 4.0 * (m_ + 1) + sv * n_ + 16.0 * (m_ + n_);
+      prof.bytes[1] = (double)A_.nnz * (va + 4) + 4.0 * (n_ + 1) + sv * m_ + 8.0 * n_ + 48.0 * n_;
     }
-    const double vv = P.fp32 ? 4.0 : 8.0;
-    prof.bytes[2] = 2.0 * n_ * ell * vv + 56.0 * n_;
+    prof.bytes[2] = 2.0 * n_ * ell * 8.0 + 56.0 * n_;
   }
   kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 3 : 0);
   if (profile_) ensure_events(4 * std::max(G, 1));
@@ -711,6 +911,11 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   } guard{exec};
   const long long max_launch = a.maxit / std::max(G, 1) + 4;
   long long launches = 0;
+  // FP32-sum mode: an explicit FP64 check every `periodic` iterations ends the phase when
+  // the true residual stops falling (the recurrence can run ahead of it)
+  const int periodic = 10 * a.check_gap;
+  int next_periodic = periodic;
+  double last_periodic = INFINITY;
   while (true) {
     const int it0 = h.it;
     if (G > 0) APL_CUDA(cudaGraphLaunch(exec, st_));
@@ -722,6 +927,16 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     if (G > 0) add_launches((long long)kernels_per_iter_ * G);
     if (!h.done) {
       if (launches > max_launch) { res.reason = R_MAXIT; break; }
+      if (mode_ == 1 && a.tol > 0.0 && a.fixed_len < 0 && h.it >= next_periodic) {
+        if (h.pending == 2) { flush_x(); h.pending = 3; }
+        const double ne = ne_residual(a.rhs_top, a.rhs_bot, x_, sqrt(a.mu), a.norm_ref);
+        res.checks++;
+        res.ne_res = ne;
+        if (ne <= a.tol) { res.reason = R_TOL; break; }
+        if (ne > 0.5 * last_periodic) { res.reason = R_DRIFT; break; }
+        last_periodic = ne;
+        next_periodic = h.it + periodic;
+      }
       continue;
     }
     if (h.reason == R_CHECK) {
@@ -731,9 +946,9 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
       res.ne_res = ne;
       if (ne <= a.tol) { res.reason = R_TOL; break; }
       if ((long long)h.it >= a.maxit) { res.reason = R_MAXIT; break; }
-      // mixed form: the recurrence passed tol but the FP64 residual did not; end the phase
-      // so that the caller restarts from an exactly formed residual
-      if (mixed_) { res.reason = R_DRIFT; break; }
+      // FP32-sum mode: the recurrence passed tol but the FP64 residual did not; end the
+      // phase so that the caller restarts from an exactly formed residual
+      if (mode_ == 1) { res.reason = R_DRIFT; break; }
       const int zero = 0;
       const int nc = h.it + a.check_gap;
       APL_CUDA(cudaMemcpyAsync((char*)ctl_.p + offsetof(LsqrCtl, next_check), &nc, sizeof(int),
@@ -753,30 +968,43 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
 
 void LsqrEngine::matvec(int trans, const double* x, double* y, double alpha, double beta,
                         bool fp64) {
-  const bool f32acc = !fp64 && mixed_ && A_.dtype == 1;
+  const int md = fp64 ? 0 : mode_;
+  const int64_t len = trans ? m_ : n_;
+  if (md != 0) {
+    split_kernel<<<(unsigned)cdiv(len, NT), NT, 0, st_>>>(len, x, uh_.p, ul_.p);
+    APL_LAUNCH_CHECK();
+  }
+  const float* xh = uh_.p;
+  const float* xl = ul_.p;
   if (!trans) {
     if (A_.fmt == 0) {
       const int blocks = (int)std::min<int64_t>(cdiv(m_ * 32, NT), sm_blocks());
       if (A_.dtype == 0)
-        mv_dense_rows<double, double><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals,
-                                                              x, y, alpha, beta);
-      else if (f32acc)
-        mv_dense_rows<float, float><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
-                                                            y, alpha, beta);
+        mv_dense_rows<double, 0><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals, x,
+                                                         xh, xl, y, alpha, beta);
+      else if (md == 0)
+        mv_dense_rows<float, 0><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
+                                                        xh, xl, y, alpha, beta);
+      else if (md == 1)
+        mv_dense_rows<float, 1><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
+                                                        xh, xl, y, alpha, beta);
       else
-        mv_dense_rows<float, double><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals,
-                                                             x, y, alpha, beta);
+        mv_dense_rows<float, 2><<<blocks, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
+                                                        xh, xl, y, alpha, beta);
     } else {
       const unsigned g = (unsigned)cdiv(m_, NT);
       if (A_.dtype == 0)
-        mv_csr_rows<double, double><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx,
-                                                       (const double*)A_.vals, x, y, alpha, beta);
-      else if (f32acc)
-        mv_csr_rows<float, float><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx,
-                                                     (const float*)A_.vals, x, y, alpha, beta);
+        mv_csr_rows<double, 0><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx, (const double*)A_.vals,
+                                                  x, xh, xl, y, alpha, beta);
+      else if (md == 0)
+        mv_csr_rows<float, 0><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx, (const float*)A_.vals,
+                                                 x, xh, xl, y, alpha, beta);
+      else if (md == 1)
+        mv_csr_rows<float, 1><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx, (const float*)A_.vals,
+                                                 x, xh, xl, y, alpha, beta);
       else
-        mv_csr_rows<float, double><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx,
-                                                      (const float*)A_.vals, x, y, alpha, beta);
+        mv_csr_rows<float, 2><<<g, NT, 0, st_>>>(m_, A_.rowptr, A_.colidx, (const float*)A_.vals,
+                                                 x, xh, xl, y, alpha, beta);
     }
     APL_LAUNCH_CHECK();
     return;
@@ -784,30 +1012,36 @@ void LsqrEngine::matvec(int trans, const double* x, double* y, double alpha, dou
   // y = A^T x (alpha = 1, beta = 0 only)
   APL_REQUIRE(alpha == 1.0 && beta == 0.0, "matvec: transposed product takes alpha=1, beta=0");
   if (A_.fmt == 0) {
-    dim3 grid((unsigned)cdiv(n_, NT), (unsigned)k2_rchunks_);
     const int64_t rows_per = cdiv(m_, k2_rchunks_);
+    dim3 grid((unsigned)cdiv(n_, NT), (unsigned)k2_rchunks_);
     if (A_.dtype == 0)
-      k2a_dense<double, double><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals, x,
-                                                      part_.p, rows_per, nullptr);
-    else if (f32acc)
-      k2a_dense<float, float><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
-                                                    part_.p, rows_per, nullptr);
+      k2a_dense<double, 0, false><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const double*)A_.vals, x,
+                                                        xh, xl, part_.p, rows_per, nullptr);
+    else if (md == 0)
+      k2a_dense<float, 0, false><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x, xh,
+                                                       xl, part_.p, rows_per, nullptr);
+    else if (md == 1)
+      k2a_dense<float, 1, false><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x, xh,
+                                                       xl, part_.p, rows_per, nullptr);
     else
-      k2a_dense<float, double><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x,
-                                                     part_.p, rows_per, nullptr);
+      k2a_dense<float, 2, false><<<grid, NT, 0, st_>>>(m_, n_, A_.ld, (const float*)A_.vals, x, xh,
+                                                       xl, part_.p, rows_per, nullptr);
     APL_LAUNCH_CHECK();
     colsum_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, k2_rchunks_, part_.p, y);
   } else {
     const unsigned g = (unsigned)cdiv(n_, NT);
     if (A_.dtype == 0)
-      mv_csc_cols<double, double><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx,
-                                                     (const double*)A_.cvals, x, y);
-    else if (f32acc)
-      mv_csc_cols<float, float><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx,
-                                                   (const float*)A_.cvals, x, y);
+      mv_csc_cols<double, 0><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx, (const double*)A_.cvals,
+                                                x, xh, xl, y);
+    else if (md == 0)
+      mv_csc_cols<float, 0><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx, (const float*)A_.cvals, x,
+                                               xh, xl, y);
+    else if (md == 1)
+      mv_csc_cols<float, 1><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx, (const float*)A_.cvals, x,
+                                               xh, xl, y);
     else
-      mv_csc_cols<float, double><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx,
-                                                    (const float*)A_.cvals, x, y);
+      mv_csc_cols<float, 2><<<g, NT, 0, st_>>>(n_, A_.colptr, A_.rowidx, (const float*)A_.cvals, x,
+                                               xh, xl, y);
   }
   APL_LAUNCH_CHECK();
 }

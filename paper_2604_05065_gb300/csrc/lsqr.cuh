@@ -7,7 +7,7 @@
 namespace apl {
 
 enum StopReason { R_NONE = 0, R_EXACT = 1, R_REPLAY = 2, R_PS2 = 3, R_PS1 = 4, R_DYNAMIC = 5,
-                  R_TOL = 6, R_MAXIT = 7, R_CHECK = 8, R_DRIFT = 9 };
+                  R_TOL = 6, R_MAXIT = 7, R_CHECK = 8, R_DRIFT = 9, R_INNER = 10 };
 
 // Per-kernel device time of the hot loop, collected with CUDA events recorded inside the
 // captured iteration graphs when profiling is on.
@@ -30,18 +30,18 @@ struct LsqrCtl {
   int it, done, reason, init;
   int next_check, fixed_len, use_p, pad;
   double delta, eps, nu, sig_ell, tol, normP, norm_ref;
+  double inner;     // > 0: stop when ||Abar^T rbar|| estimate <= inner * its phase-start value
+  double arnorm0;   // alpha_1 beta_1 = ||Abar^T rbar_0||
   long long maxit;
   unsigned int counter[8];
 };
 
 // The preconditioner P^{-1} = I + Vhat diag(coef) Vhat^T (Eq. preconditioner2), with
-// Vhat stored row-major n x ell (ld ldv) in FP64 or FP32; coef2 gives P^{-2}.
+// Vhat stored row-major n x ell (ld ldv) in FP64; coef2 gives P^{-2}.
 struct PrecondDev {
   int ell = 0;
   int64_t ldv = 0;
-  int fp32 = 0;
   const double* V64 = nullptr;
-  const float* V32 = nullptr;
   const double* coef = nullptr;
   const double* coef2 = nullptr;
   double normP = 1.0;    // ||P||_2
@@ -67,7 +67,8 @@ struct PhaseResult {
 
 class LsqrEngine {
  public:
-  void setup(cudaStream_t st, const MatView& A, int mixed, int graph_iters);
+  // mode: 0 FP64 products, 1 FP32 products and sums, 2 compensated FP32 (see lsqr.cu)
+  void setup(cudaStream_t st, const MatView& A, int mode, int graph_iters);
   void set_profile(bool on) { profile_ = on; }
   KernelProfile prof;
   PhaseResult run_phase(const PrecondDev& P, const PhaseArgs& a);
@@ -91,11 +92,13 @@ class LsqrEngine {
 
   cudaStream_t st_ = nullptr;
   MatView A_;
-  int mixed_ = 0, graph_iters_ = 16;
+  int mode_ = 0, graph_iters_ = 16;
+  bool vec_ = false;  // dense rows 16-byte aligned: vector loads
   int64_t m_ = 0, n_ = 0;
   int k1_blocks_ = 0, k2_blocks_ = 0, k2_rchunks_ = 1, red_cap_ = 0;
   DBuf<LsqrCtl> ctl_;
   DBuf<double> u_, v_, z_, g_, d_, red_, part_, tpart_, ct_, c2t_, r_, q_;
+  DBuf<float> zh_, zl_, uh_, ul_;  // FP32 hi/lo splits of z' and u' (modes 1, 2)
   DBuf<double> scal_;
   DBuf<unsigned int> cnt_;
   double* x_ = nullptr;
