@@ -232,7 +232,29 @@ aplicur_status aplicur_reset_profile(aplicur_handle h);
 /* Kernels this process has launched through the library (every handle). */
 int64_t aplicur_launch_count(void);
 
-/* Message of the last failed call on h (never NULL). */
+/* y = A^T x for a dense row-major A (FP64 or FP32 values, FP64 products and sums)
+ * without allocating any device or host memory.  The paper has no counterpart; it
+ * is for callers that cannot allocate: code running inside a fixed memory budget
+ * or a pre-allocated arena (an inference server's pool, an embedding application
+ * that owns all device memory) and code paths where an allocation would
+ * synchronise or fail.
+ *  A   host struct: format APLICUR_DENSE_ROWMAJOR, dtype F64 or F32, values on the
+ *      device, m, n >= 1, ld >= n, n <= 524288.
+ *  x   device, m doubles; y device, n doubles (overwritten).
+ *  stream  cudaStream_t as void*.
+ * The only scratch, 4 MiB of row-chunk partial sums, is a static device array that
+ * every GPU loading the library keeps until the process exits.  All calls share it:
+ * calls that may overlap on the GPU (different streams, threads) race and must be
+ * serialised by the caller.  Each call overwrites the part it reads, so no state
+ * carries over.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Errors: EINVAL (null pointer, not dense, n above the limit; message through
+ * aplicur_last_error(NULL)), ECUDA.  The call does not synchronise. */
+aplicur_status aplicur_dense_atx_noalloc(const aplicur_matrix* A, const double* x, double* y,
+                                         void* stream);
+
+/* Message of the last failed call on h (never NULL); with h = NULL, the last
+ * failed aplicur_create or aplicur_dense_atx_noalloc of this thread. */
 const char* aplicur_last_error(aplicur_handle h);
 
 /* Static description of a status code (never NULL). */

@@ -77,6 +77,7 @@ SIGNATURES = {
     "aplicur_get_profile": (C.c_int, [_VP, C.POINTER(Profile)]),
     "aplicur_reset_profile": (C.c_int, [_VP]),
     "aplicur_launch_count": (C.c_int64, []),
+    "aplicur_dense_atx_noalloc": (C.c_int, [C.POINTER(Matrix), _VP, _VP, _VP]),
     "aplicur_last_error": (C.c_char_p, [_VP]),
     "aplicur_status_string": (C.c_char_p, [C.c_int]),
     "aplicur_destroy": (None, [_VP]),
@@ -331,6 +332,31 @@ class Solver:
         _check(self._lib, self._lib.aplicur_matvec(self._h, 1 if trans else 0, x.data_ptr(),
                                                    y.data_ptr()), self._h)
         return y
+
+
+def dense_atx_noalloc(A, x, y=None):
+    """y = A^T x for a dense CUDA tensor A through the allocation-free entry point (the
+    library allocates nothing; y, if not given, is allocated here by PyTorch)."""
+    torch = _torch()
+    lib = load()
+    if A.stride(1) != 1:
+        raise ValueError("A must be row-major")
+    mat = Matrix()
+    mat.format = 0
+    mat.dtype = 0 if A.dtype == torch.float64 else 1
+    mat.m, mat.n = int(A.shape[0]), int(A.shape[1])
+    mat.ld = A.stride(0)
+    mat.nnz = mat.m * mat.n
+    mat.values = A.data_ptr()
+    x = x.to(torch.float64).contiguous()
+    if y is None:
+        y = torch.empty(mat.n, dtype=torch.float64, device=A.device)
+    stream = torch.cuda.current_stream(A.device).cuda_stream
+    st = lib.aplicur_dense_atx_noalloc(C.byref(mat), x.data_ptr(), y.data_ptr(),
+                                       C.c_void_p(stream))
+    if st != 0:
+        raise AplicurError(st, lib.aplicur_last_error(None).decode())
+    return y
 
 
 def launch_count() -> int:

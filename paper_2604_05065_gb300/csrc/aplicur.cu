@@ -617,6 +617,14 @@ void aplicur_options_default(aplicur_options* o) {
 
 static thread_local std::string g_create_err;
 
+}  // extern "C"
+
+namespace apl {
+void set_noalloc_error(const char* msg) { g_create_err = msg; }
+}  // namespace apl
+
+extern "C" {
+
 aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, const double* b,
                               double mu, int32_t sketch_dim, const aplicur_options* opt,
                               void* stream) {

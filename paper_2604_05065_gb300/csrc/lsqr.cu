@@ -17,8 +17,10 @@
 //      unevaluated pair (Knuth's TwoSum), so the result is accurate to about 2^-44
 //      relative to sum |a_i z_i| while every instruction is an FP32 one.
 #include <cstddef>
+#include <mutex>
 #include <vector>
 
+#include "../../include/aplicur.h"
 #include "lsqr.cuh"
 
 namespace apl {
@@ -1082,3 +1084,98 @@ void LsqrEngine::apply_precond(const PrecondDev& P, const double* w, double* out
 }
 
 }  // namespace apl
+
+// ======================================================================================
+// Allocation-free dense A^T x (aplicur_dense_atx_noalloc).
+//
+// Its only scratch, the row-chunk partial sums of the transposed product, lives in this
+// file-scope device array; every GPU that loads the library holds it until the process
+// exits.  Host code cannot use the symbol as a device address, so the address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+// ======================================================================================
+
+namespace {
+constexpr int64_t kNoAllocDoubles = int64_t(1) << 19;  // 4 MiB
+constexpr int kMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Address of g_noalloc_scratch on the current device (looked up on first use).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+namespace apl {
+void set_noalloc_error(const char* msg);
+}
+
+extern "C" aplicur_status aplicur_dense_atx_noalloc(const aplicur_matrix* A, const double* x,
+                                                    double* y, void* stream) {
+  using namespace apl;
+  if (!A || !x || !y || !A->values) {
+    set_noalloc_error("aplicur_dense_atx_noalloc: null argument");
+    return APLICUR_EINVAL;
+  }
+  if (A->format != APLICUR_DENSE_ROWMAJOR || (A->dtype != APLICUR_F64 && A->dtype != APLICUR_F32) ||
+      A->m < 1 || A->n < 1 || A->ld < A->n) {
+    set_noalloc_error("aplicur_dense_atx_noalloc: need a dense row-major F64/F32 matrix, "
+                      "m, n >= 1, ld >= n");
+    return APLICUR_EINVAL;
+  }
+  if (A->n > kNoAllocDoubles) {
+    set_noalloc_error("aplicur_dense_atx_noalloc: n exceeds the 524288-column limit of the "
+                      "static scratch array");
+    return APLICUR_EINVAL;
+  }
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) {
+    set_noalloc_error(cudaGetErrorString(e));
+    return APLICUR_ECUDA;
+  }
+  const int64_t m = A->m, n = A->n;
+  // row chunks: as many as the scratch holds, at most 64, at least 32 rows each; every
+  // partial is written before it is read, so nothing needs clearing between calls
+  const int64_t rchunks = std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>(kNoAllocDoubles / n, 64), cdiv(m, 32)));
+  const int64_t rows_per = cdiv(m, rchunks);
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 grid((unsigned)cdiv(n, NT), (unsigned)rchunks);
+  if (A->dtype == APLICUR_F64)
+    k2a_dense<double, 0, false><<<grid, NT, 0, st>>>(m, n, A->ld, (const double*)A->values, x,
+                                                     nullptr, nullptr, scratch, rows_per, nullptr);
+  else
+    k2a_dense<float, 0, false><<<grid, NT, 0, st>>>(m, n, A->ld, (const float*)A->values, x,
+                                                    nullptr, nullptr, scratch, rows_per, nullptr);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    colsum_kernel<<<(unsigned)cdiv(n, NT), NT, 0, st>>>(n, (int)rchunks, scratch, y);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    set_noalloc_error(cudaGetErrorString(e));
+    return APLICUR_ECUDA;
+  }
+  note_launch();
+  note_launch();
+  return APLICUR_OK;
+}
+
