@@ -146,7 +146,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     opts = dict(precision=precision, profile=1, seed=1)
 
-    prof_tot = {"ms": [0.0] * 3, "launches": [0] * 3, "bytes": [0.0] * 3}
+    prof_tot = {"ms": [0.0] * 6, "launches": [0] * 6, "work": [0.0] * 6}
     sched = {}
 
     def one_solve(Adev, bdev, record=False):
@@ -155,10 +155,10 @@ def gpu_arm(args, rank, world, local_rank):
         st = s.stats()
         if record:
             pr = s.profile()
-            for k in range(3):
+            for k in range(6):
                 prof_tot["ms"][k] += pr["ms"][k]
                 prof_tot["launches"][k] += pr["launches"][k]
-                prof_tot["bytes"][k] += pr["bytes"][k]
+                prof_tot["work"][k] += pr["work"][k]
             sched.update(steps=st["nsteps"], phases=st["nphases"], iters=st["iters"],
                          ell=st["ell"], builds=sum(1 for q in s.steps() if q["rebuild"]),
                          ne_res=st["ne_res"], converged=st["converged"],
@@ -243,28 +243,53 @@ def gpu_arm(args, rank, world, local_rank):
                  "converged": bool(pst["converged"])}
         s.close()
 
-    # ---- roofline of the dominant hot-loop kernel
-    names = ["A z pass (k1)", "A^T u pass (k2)", "preconditioner passes (k3+k4)"]
-    k = max(range(3), key=lambda q: prof_tot["ms"][q])
-    peak, src = peaks()
-    roof = None
-    if prof_tot["launches"][k]:
-        avg_ms = prof_tot["ms"][k] / prof_tot["launches"][k]
-        bpl = prof_tot["bytes"][k] / prof_tot["launches"][k]
-        achieved = bpl / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic_for(k, bpl),
-                "kernel": names[k], "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
-                if src == "measured" else "fallback 6800 GB/s",
-                "avg_launch_ms": round(avg_ms, 5), "bytes_per_launch": int(bpl),
-                "launches_timed": prof_tot["launches"][k],
-                "all_kernels": {names[q]: {"ms_total": round(prof_tot["ms"][q], 3),
-                                           "launches": prof_tot["launches"][q],
-                                           "GBps": round(prof_tot["bytes"][q] /
-                                                         max(prof_tot["ms"][q], 1e-9) / 1e6, 1)}
-                                for q in range(3)}}
+    # ---- roofline of the dominant kernel family of the step (largest device time)
+    roof = roofline(prof_tot)
     return dict(value=value, ms=ms_max / args.steps, p=p, prec=prec, clocks=clk, e2e=e2e,
                 plain=plain, roof=roof, launches=launches, sched=sched, ne=st["ne_res"])
+
+
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64: 152 SMs x 2.07 GHz x 4 FLOP/clk/SM
+NAMES = ["A z pass (k1_dense)", "A^T u pass (k2a_dense + k2b_dense)",
+         "preconditioner passes (pre_qt, pre_vt, pre_v, pre_expand)", "FP64 GEMM (dgemm_kernel)",
+         "Jacobi sweeps (jacobi_round_kernel)", "LUPP selection (lupp_step_kernel)"]
+
+
+def roofline(prof):
+    k = max(range(6), key=lambda q: prof["ms"][q])
+    if not prof["launches"][k]:
+        return None
+    peak_bw, src = peaks()
+    fams = {}
+    for q in range(6):
+        if not prof["launches"][q]:
+            continue
+        rate = prof["work"][q] / max(prof["ms"][q], 1e-12) * 1e-3  # per second / 1e12... see unit
+        if q in (3, 4):
+            fams[NAMES[q]] = {"ms_total": round(prof["ms"][q], 2), "timed": prof["launches"][q],
+                              "TFLOPs": round(rate * 1e-6, 4),
+                              "frac": round(rate * 1e-6 / FP64_PEAK_TFLOPS, 4)}
+        else:
+            fams[NAMES[q]] = {"ms_total": round(prof["ms"][q], 2), "timed": prof["launches"][q],
+                              "GBps": round(rate * 1e-3, 1), "frac": round(rate * 1e-3 / peak_bw, 4)}
+    avg_ms = prof["ms"][k] / prof["launches"][k]
+    per = prof["work"][k] / prof["launches"][k]
+    if k in (3, 4):
+        achieved = per / (avg_ms * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
+               "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+               "traffic": traffic_for(k, per),
+               "peak_source": "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+               "flops_per_launch": int(per)}
+    else:
+        achieved = per / (avg_ms * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_bw, "unit": "GB/s",
+               "frac": round(achieved / peak_bw, 4), "traffic": traffic_for(k, per),
+               "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+               else "fallback 6800 GB/s", "bytes_per_launch": int(per)}
+    out.update(kernel=NAMES[k], avg_launch_ms=round(avg_ms, 5), launches_timed=prof["launches"][k],
+               families=fams)
+    return out
 
 
 def traffic_for(k, bpl):

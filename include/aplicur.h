@@ -107,16 +107,22 @@ typedef struct {
   /* Non-zero: record CUDA events around the hot-loop kernels inside every LSQR
    * iteration and accumulate their device times (aplicur_get_profile). */
   int32_t profile;
+  /* > 0: cap the CUR rank; reaching it ends rank growth like reaching min(m, n)
+   * (the last block is truncated to fit).  0: no cap. */
+  int32_t max_rank;
 } aplicur_options;
 
-/* Device time of the LSQR hot-loop kernels, accumulated over the solves since
- * creation or the last aplicur_reset_profile (requires options.profile).
- * Index 0: the A z pass, 1: the A^T u pass, 2: the preconditioner passes
- * (Vhat^T w and the expansion). */
+/* Device time by kernel family, accumulated over the solves since creation or the
+ * last aplicur_reset_profile (requires options.profile).  Families:
+ *  0 the A z pass, 1 the A^T u pass, 2 the preconditioner passes (LSQR hot loop;
+ *    timed by events inside the captured iteration graphs);
+ *  3 FP64 GEMMs (including those inside triangular solves and Cholesky),
+ *  4 Jacobi sweeps of the preconditioner SVD, 5 LUPP index selection.
+ * work[k] is algorithmic bytes for families 0, 1, 2, 5 and FP64 flops for 3, 4. */
 typedef struct {
-  double ms[3];              /* summed event-to-event device time */
-  int64_t launches[3];       /* timed launches */
-  double bytes[3];           /* summed algorithmic bytes of the timed launches */
+  double ms[6];              /* summed event-to-event device time */
+  int64_t launches[6];       /* timed regions (kernel launches, sweeps, selections) */
+  double work[6];            /* summed algorithmic bytes or flops */
   int64_t kernel_launches;   /* all kernels this process launched through the library */
 } aplicur_profile;
 

@@ -39,12 +39,18 @@ class Options(C.Structure):
                 ("sketch_signs", C.c_void_p), ("normest_w", C.c_void_p),
                 ("replay_nphases", C.c_int32), ("replay_phases", C.c_void_p),
                 ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("max_rank", C.c_int32)]
 
 
 class Profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 3), ("launches", C.c_int64 * 3), ("bytes", C.c_double * 3),
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("work", C.c_double * 6),
                 ("kernel_launches", C.c_int64)]
+
+
+# kernel families of aplicur_profile: (name, unit of work)
+PROFILE_FAMILIES = [("A z pass", "bytes"), ("A^T u pass", "bytes"),
+                    ("preconditioner passes", "bytes"), ("FP64 GEMM", "flops"),
+                    ("Jacobi sweeps", "flops"), ("LUPP selection", "bytes")]
 
 
 class Stats(C.Structure):
@@ -322,7 +328,7 @@ class Solver:
     def profile(self) -> dict:
         pr = Profile()
         _check(self._lib, self._lib.aplicur_get_profile(self._h, C.byref(pr)), self._h)
-        return {"ms": list(pr.ms), "launches": list(pr.launches), "bytes": list(pr.bytes),
+        return {"ms": list(pr.ms), "launches": list(pr.launches), "work": list(pr.work),
                 "kernel_launches": pr.kernel_launches}
 
     def matvec(self, x, trans: bool = False):

@@ -119,7 +119,7 @@ struct aplicur_ctx {
   // sketch
   DBuf<int> srows, tptr, ti;
   DBuf<signed char> ssign, tsgn;
-  DBuf<double> Y, E, W, T, scal;
+  DBuf<double> Y, E, Et, W, T, scal;
   // CUR state
   int ell = 0, cap = 0;
   std::vector<int> I, J;
@@ -129,7 +129,7 @@ struct aplicur_ctx {
   DBuf<int> info;
   LuppWork lw;
   // preconditioner
-  DBuf<double> Mb, VM, sigma, V64, coef, coef2;
+  DBuf<double> Mb, VM, sigma, coef, coef2;
   PrecondDev P;
   double sighat = 1.0;
   std::vector<double> sig_host;
@@ -143,6 +143,7 @@ struct aplicur_ctx {
   aplicur_stats stats{};
   std::string err;
   float setup_ms = 0;
+  ProfSink sink;
 };
 
 namespace {
@@ -171,7 +172,10 @@ void ctx_grow(aplicur_ctx* h, int need) {
                                cudaMemcpyDeviceToDevice, st));
     B.swap(nb);
   };
+  const double* oldQ = h->QR.p;
   regrow_cols(h->QR, h->n);
+  // the preconditioner reads the leading columns of Q_R in place
+  if (h->P.Q == oldQ) h->P.Q = h->QR.p;
   if (h->A.fmt == 0) {
     regrow_cols(h->Cbuf, h->m);
     DBuf<double> nb;
@@ -299,9 +303,12 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
   ctx_grow(h, (int)std::min<int64_t>(h->kmax, ell + std::max(kj, 1)));
   // ---- column selection: LUPP on E_row^T with the chosen columns zeroed
   zero_cols_cm(st, h->E.p, s, s, h->J_d.p, ell);
+  // E_row^T as an n x s column-major block: the elimination then reads columns
+  // contiguously across threads
+  dcopy2d(st, s, n, h->E.p, s, h->Et.p, n, true);
   std::vector<int> Jp, Ip;
   double mJ = INFINITY, mI = INFINITY;
-  const int nzJ = lupp_select(st, n, s, h->E.p, s, 1, kj, h->lw, Jp, &mJ);
+  const int nzJ = lupp_select(st, n, s, h->Et.p, 1, n, kj, h->lw, Jp, &mJ);
   int k = 0;
   if (nzJ > 0) {
     APL_CUDA(cudaMemcpyAsync(h->Jp_d.p, Jp.data(), nzJ * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -421,25 +428,24 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
   return k;
 }
 
-// CURPreconditioner Part 2: M = T_C U T_R^T, SVD, Vhat = Q_R V_M, coefficients.
+// CURPreconditioner Part 2: M = T_C U T_R^T, SVD of M, coefficients.  Vhat = Q_R V_M is
+// kept implicit (applied as two matrix-vector products per use).
 void build_preconditioner(aplicur_ctx* h) {
   cudaStream_t st = h->st;
   const int L = h->ell, cap = h->cap;
-  const int64_t n = h->n;
   h->Mb.alloc((size_t)L * L, st);
   h->VM.alloc((size_t)L * L, st);
   h->sigma.alloc(L, st);
-  h->work.alloc((size_t)L * L + L + 16, st);
+  h->work.alloc((size_t)L * L + 16, st);
   double* X = h->work.p;
   // X = A(I,J)^{-1} T_R^T
   dcopy2d(st, L, L, h->TR.p, cap, X, L, true);
   dtrsm(st, true, 'L', false, true, L, L, h->LU.p, cap, X, L);
   dtrsm(st, true, 'U', false, false, L, L, h->LU.p, cap, X, L);
-  dgemm(st, 0, 0, L, L, L, 1.0, h->TC.p, cap, X, L, 0.0, h->Mb.p, L);
-  jacobi_svd(st, L, h->Mb.p, L, h->VM.p, L, h->sigma.p, h->work.p, h->info.p);
-  // Vhat^T (L x n col-major) = V_M^T Q_R^T  ->  Vhat row-major n x L
-  h->V64.alloc((size_t)n * L, st);
-  dgemm(st, 1, 1, L, n, L, 1.0, h->VM.p, L, h->QR.p, n, 0.0, h->V64.p, L);
+  // M^T = X^T T_C^T; the Jacobi sweep on the columns of M^T gives the singular values
+  // and right singular vectors of M
+  dgemm(st, 1, 1, L, L, L, 1.0, X, L, h->TC.p, cap, 0.0, h->Mb.p, L);
+  jacobi_left(st, L, h->Mb.p, L, h->VM.p, L, h->sigma.p, h->info.p);
   h->sig_host.resize(L);
   APL_CUDA(cudaMemcpyAsync(h->sig_host.data(), h->sigma.p, L * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
@@ -460,12 +466,13 @@ void build_preconditioner(aplicur_ctx* h) {
   APL_CUDA(cudaMemcpyAsync(h->coef2.p, c2.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   PrecondDev P;
   P.ell = L;
-  P.ldv = L;
+  P.Q = h->QR.p;
+  P.ldq = h->n;
+  P.VM = h->VM.p;
   P.coef = h->coef.p;
   P.coef2 = h->coef2.p;
   P.normP = std::sqrt(h->sig_host[0] * h->sig_host[0] + d2) / h->sighat;
   P.sig_ell = sl;
-  P.V64 = h->V64.p;
   h->P = P;
   APL_CUDA(cudaStreamSynchronize(st));
 }
@@ -657,6 +664,8 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
     else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
     cudaStream_t st = h->st;
     h->m = A->m; h->n = A->n; h->kmax = std::min(h->m, h->n);
+    APL_REQUIRE(h->opt.max_rank >= 0, "max_rank must be >= 0");
+    if (h->opt.max_rank > 0) h->kmax = std::min<int64_t>(h->kmax, h->opt.max_rank);
     h->A.fmt = A->format; h->A.dtype = A->dtype; h->A.m = A->m; h->A.n = A->n; h->A.ld = A->ld;
     h->A.nnz = A->format == APLICUR_CSR ? A->nnz : A->m * A->n;
     h->A.vals = A->values; h->A.rowptr = A->rowptr; h->A.colidx = A->colidx;
@@ -690,6 +699,7 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
     const int64_t m = h->m, n = h->n;
     h->Y.alloc((size_t)h->s * n, st);
     h->E.alloc((size_t)h->s * n, st);
+    h->Et.alloc((size_t)h->s * n, st);
     h->T.alloc((size_t)h->s * h->r, st);
     h->scal.alloc(4, st);
     h->info.alloc(4, st);
@@ -740,7 +750,13 @@ aplicur_status aplicur_solve(aplicur_handle h, double tol, int64_t maxit, double
     APL_REQUIRE(tol >= 0.0 && maxit >= 0, "tol and maxit must be >= 0");
     load_replay(h);
     auto t0 = std::chrono::steady_clock::now();
+    struct SinkScope {
+      explicit SinkScope(aplicur_ctx* c) : h(c) { if (h->opt.profile) prof_set_sink(&h->sink); }
+      ~SinkScope() { prof_set_sink(nullptr); }
+      aplicur_ctx* h;
+    } scope(h);
     const int rc = do_solve(h, tol, maxit);
+    if (h->opt.profile) h->sink.harvest();
     APL_CUDA(cudaMemcpyAsync(x_out, h->x.p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     APL_CUDA(cudaStreamSynchronize(h->st));
     h->stats.time_solve_ms =
@@ -956,7 +972,12 @@ aplicur_status aplicur_get_profile(aplicur_handle h, aplicur_profile* out) {
   for (int k = 0; k < 3; ++k) {
     out->ms[k] = h->eng.prof.ms[k];
     out->launches[k] = h->eng.prof.launches[k];
-    out->bytes[k] = h->eng.prof.bytes_total[k];
+    out->work[k] = h->eng.prof.bytes_total[k];
+  }
+  for (int k = 3; k < PROF_NCAT; ++k) {
+    out->ms[k] = h->sink.ms[k];
+    out->launches[k] = h->sink.n[k];
+    out->work[k] = h->sink.work[k];
   }
   out->kernel_launches = launch_count();
   return APLICUR_OK;
@@ -970,6 +991,11 @@ aplicur_status aplicur_reset_profile(aplicur_handle h) {
     h->eng.prof.ms[k] = 0;
     h->eng.prof.launches[k] = 0;
     h->eng.prof.bytes_total[k] = 0;
+  }
+  for (int k = 0; k < PROF_NCAT; ++k) {
+    h->sink.ms[k] = 0;
+    h->sink.work[k] = 0;
+    h->sink.n[k] = 0;
   }
   return APLICUR_OK;
 }

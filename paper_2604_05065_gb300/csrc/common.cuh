@@ -40,6 +40,31 @@ struct CaptureScope {
   ~CaptureScope();
 };
 
+// Device-time accounting by kernel family, active while a solve with profiling runs on
+// this thread.  Categories: 0 A z pass, 1 A^T u pass, 2 preconditioner passes (bytes);
+// 3 FP64 GEMM, 4 Jacobi sweeps (FP64 flops); 5 LUPP selection (bytes).
+enum { PROF_NCAT = 6, PROF_GEMM = 3, PROF_JACOBI = 4, PROF_LUPP = 5 };
+struct ProfSink {
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> pool;
+  struct Rec { int cat; double work; int e0, e1; };
+  std::vector<Rec> recs;
+  double ms[PROF_NCAT] = {0};
+  double work[PROF_NCAT] = {0};
+  long long n[PROF_NCAT] = {0};
+  ~ProfSink();
+  int event();                  // record a fresh event on st, return its index
+  void harvest();               // synchronise and accumulate all pending records
+  void add(int cat, double ms_, double work_, long long cnt);
+};
+// The sink of the calling thread (NULL when profiling is off or a graph is captured).
+ProfSink* prof_sink();
+void prof_set_sink(ProfSink* s);
+// Open a timed region on stream st; returns a token for prof_end (or -1 when off).
+int prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st, int token, int cat, double work);
+void prof_set_work(int token_rec, double work);  // adjust the last record's work
+
 #define APL_LAUNCH_CHECK()            \
   do {                                \
     APL_CUDA(cudaGetLastError());     \

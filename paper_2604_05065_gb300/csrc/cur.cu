@@ -106,6 +106,10 @@ __device__ Cand block_cand(Cand c) {
   return r;
 }
 
+// One elimination step j.  A block owns 32 consecutive rows (lane = row) and its 8 warps
+// split the columns j-1.. K-1 (warp w takes columns j + w, j + w + 8, ...), so every
+// access X(i, c) is coalesced when rs = 1.  Step j applies the elimination of column
+// j-1 by the pivot row chosen at step j-1, then looks for the pivot of column j.
 __global__ void __launch_bounds__(256) lupp_step_kernel(
     int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int j,
     int* __restrict__ pos_of, int* __restrict__ row_at, int* __restrict__ piv,
@@ -113,26 +117,33 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
     unsigned int* counter, double* margin, int* iscal) {
   extern __shared__ double prow[];  // pivot row values for columns j-1 .. K-1
   if (iscal[1]) return;             // selection already stopped at a zero pivot
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
   const int p = j > 0 ? piv[j - 1] : -1;
   if (j > 0) {
     for (int64_t c = j - 1 + threadIdx.x; c < K; c += blockDim.x)
       prow[c - (j - 1)] = X[(int64_t)p * rs + c * cs];
   }
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = i < N && pos_of[i] >= j;  // not yet a pivot row
+  double* xi = X + i * rs;
+  double l = 0.0;
   __syncthreads();
+  if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] / prow[0];
+  __syncthreads();  // every warp has read X(i, j-1) before it is overwritten
   Cand mine{-1.0, INT_MAX, -1.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int pos = pos_of[i];
-    if (pos < j) continue;  // already a pivot row
-    double* xi = X + i * rs;
-    if (j > 0) {
-      const double l = xi[(j - 1) * cs] / prow[0];
-      xi[(j - 1) * cs] = l;
-      for (int64_t c = j; c < K; ++c) xi[c * cs] = xi[c * cs] - l * prow[c - (j - 1)];
-    }
-    if (j < K) {
-      Cand c{fabs(xi[(int64_t)j * cs]), pos, -1.0};
-      mine = cand_merge(mine, c);
+  if (live) {
+    if (j > 0 && wid == 0) xi[(int64_t)(j - 1) * cs] = l;
+    for (int64_t c = j + wid; c < K; c += nw) {
+      double v = xi[c * cs];
+      if (j > 0) {
+        v = v - l * prow[c - (j - 1)];
+        xi[c * cs] = v;
+      }
+      if (c == j) {
+        Cand cd{fabs(v), pos_of[i], -1.0};
+        mine = cd;
+      }
     }
   }
   Cand b = block_cand(mine);
@@ -386,7 +397,9 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
   *margin = INFINITY;
   if (k <= 0 || N <= 0) return 0;
   const int threads = 256;
-  const int blocks = (int)std::min<int64_t>(cdiv(N, threads), 2048);
+  const int64_t blocks64 = cdiv(N, 32);
+  APL_REQUIRE(blocks64 < (1LL << 31), "lupp_select: too many rows");
+  const int blocks = (int)blocks64;
   w.pos_of.alloc(N, st);
   w.row_at.alloc(N, st);
   w.piv.alloc(k, st);
@@ -400,12 +413,19 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
                                                           w.iscal.p, w.counter.p);
   APL_LAUNCH_CHECK();
   const size_t shm = (size_t)(K + 1) * sizeof(double);
+  const int tok = prof_begin(st);
   for (int j = 0; j < k; ++j) {
     lupp_step_kernel<<<blocks, threads, shm, st>>>(N, K, X, rs, cs, j, w.pos_of.p, w.row_at.p,
                                                    w.piv.p, w.pval.p, w.ppos.p, w.psec.p,
                                                    w.counter.p, w.scal.p, w.iscal.p);
   }
   APL_LAUNCH_CHECK();
+  {
+    // algorithmic bytes: step j reads and writes the N x (K - j) trailing block
+    double bytes = 0.0;
+    for (int j = 0; j < k; ++j) bytes += 16.0 * (double)N * (double)(K - j);
+    prof_end(st, tok, PROF_LUPP, bytes);
+  }
   int isc[2];
   APL_CUDA(cudaMemcpyAsync(isc, w.iscal.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaMemcpyAsync(margin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -21,18 +21,77 @@ long long launch_count() { return g_launches.load(); }
 CaptureScope::CaptureScope() { ++g_capture_depth; }
 CaptureScope::~CaptureScope() { --g_capture_depth; }
 
+namespace {
+thread_local ProfSink* g_sink = nullptr;
+}
+ProfSink* prof_sink() { return g_capture_depth == 0 ? g_sink : nullptr; }
+void prof_set_sink(ProfSink* s) { g_sink = s; }
+ProfSink::~ProfSink() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+int ProfSink::event() {
+  const int used = (int)(recs.size() * 2);
+  while ((int)pool.size() < used + 2) {
+    cudaEvent_t e;
+    APL_CUDA(cudaEventCreate(&e));
+    pool.push_back(e);
+  }
+  return used;
+}
+void ProfSink::add(int cat, double ms_, double work_, long long cnt) {
+  ms[cat] += ms_;
+  work[cat] += work_;
+  n[cat] += cnt;
+}
+void ProfSink::harvest() {
+  if (recs.empty()) return;
+  APL_CUDA(cudaStreamSynchronize(st));
+  for (const Rec& r : recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pool[r.e0], pool[r.e1]) == cudaSuccess) add(r.cat, t, r.work, 1);
+    else (void)cudaGetLastError();
+  }
+  recs.clear();
+}
+int prof_begin(cudaStream_t st) {
+  ProfSink* s = prof_sink();
+  if (!s) return -1;
+  if (s->recs.size() >= 4096) s->harvest();
+  const int e0 = s->event();
+  s->st = st;
+  APL_CUDA(cudaEventRecord(s->pool[e0], st));
+  s->recs.push_back(ProfSink::Rec{-1, 0.0, e0, e0 + 1});
+  return (int)s->recs.size() - 1;
+}
+void prof_end(cudaStream_t st, int token, int cat, double work) {
+  ProfSink* s = prof_sink();
+  if (!s || token < 0 || token >= (int)s->recs.size()) return;
+  ProfSink::Rec& r = s->recs[token];
+  r.cat = cat;
+  r.work = work;
+  APL_CUDA(cudaEventRecord(s->pool[r.e1], st));
+}
+void prof_set_work(int token, double work) {
+  ProfSink* s = prof_sink();
+  if (!s || token < 0 || token >= (int)s->recs.size()) return;
+  s->recs[token].work = work;
+}
+
 // ------------------------------------------------------------------------------------
 // GEMM: 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K step 16.
 // ------------------------------------------------------------------------------------
 namespace {
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
+// blockIdx.z selects a K range of length kchunk; with part != NULL the block writes its
+// unscaled partial product to part + z * M * N (leading dimension M) instead of C.
 __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int64_t M,
                                                     int64_t N, int64_t K, double alpha,
                                                     const double* __restrict__ A, int64_t lda,
                                                     const double* __restrict__ B, int64_t ldb,
                                                     double beta, double* __restrict__ C,
-                                                    int64_t ldc) {
+                                                    int64_t ldc, int64_t kchunk,
+                                                    double* __restrict__ part) {
   __shared__ double As[GBK][GBM + 1];
   __shared__ double Bs[GBK][GBN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -43,7 +102,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-  for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int lin = threadIdx.x + e * 256;  // 0..1023
@@ -51,13 +112,13 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
       if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
-      if (gm < M && gk < K) v = transA ? A[gk + gm * lda] : A[gm + gk * lda];
+      if (gm < M && gk < kend) v = transA ? A[gk + gm * lda] : A[gm + gk * lda];
       As[kk][mm] = v;
       int nn;
       if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
       const int64_t gn = n0 + nn, gk2 = k0 + kk;
       double w = 0.0;
-      if (gn < N && gk2 < K) w = transB ? B[gn + gk2 * ldb] : B[gk2 + gn * ldb];
+      if (gn < N && gk2 < kend) w = transB ? B[gn + gk2 * ldb] : B[gk2 + gn * ldb];
       Bs[kk][nn] = w;
     }
     __syncthreads();
@@ -83,11 +144,29 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
     for (int j = 0; j < 4; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double* c = C + gm + gn * ldc;
-      *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
+      if (part) {
+        part[(int64_t)blockIdx.z * M * N + gm + gn * M] = acc[i][j];
+      } else {
+        double* c = C + gm + gn * ldc;
+        *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
+      }
     }
   }
 }
+
+// C = alpha * sum_z part[z] + beta * C, summing the splits in a fixed order.
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const double* part,
+                                     double alpha, double beta, double* C, int64_t ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  double acc = 0.0;
+  for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * M * N + e];
+  const int64_t r = e % M, c = e / M;
+  double* out = C + r + c * ldc;
+  *out = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *out;
+}
+
+thread_local DBuf<double> g_splitk_ws;
 }  // namespace
 
 void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -104,9 +183,32 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   }
   dim3 grid((unsigned)cdiv(M, GBM), (unsigned)cdiv(N, GBN));
   APL_REQUIRE(grid.y <= 65535, "dgemm: N too large");
-  dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
-                                     ldc);
+  // split K when the output tiles alone cannot fill the GPU (tall inner dimension)
+  const int64_t tiles = (int64_t)grid.x * grid.y;
+  int64_t splits = 1;
+  if (tiles < 2 * 152 && K >= 4 * 256) {
+    splits = std::min<int64_t>(cdiv(4 * 152, tiles), K / 256);
+    splits = std::min<int64_t>(splits, 64);
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (int64_t)(1 << 24) / (M * N)));
+  }
+  const int tok = prof_begin(st);
+  if (splits > 1) {
+    const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
+    splits = cdiv(K, kchunk);
+    g_splitk_ws.alloc((size_t)splits * M * N, st);
+    grid.z = (unsigned)splits;
+    dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc,
+                                       kchunk, g_splitk_ws.p);
+    APL_LAUNCH_CHECK();
+    splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
+                                                                     g_splitk_ws.p, alpha, beta, C,
+                                                                     ldc);
+  } else {
+    dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
+                                       ldc, K, nullptr);
+  }
   APL_LAUNCH_CHECK();
+  prof_end(st, tok, PROF_GEMM, 2.0 * (double)M * (double)N * (double)K);
 }
 
 // ------------------------------------------------------------------------------------
@@ -116,38 +218,49 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
 namespace {
 constexpr int TNB = 64;
 
-// Solve T x = b for `nvec` vectors of length `len`.  T(r, c) = Tm[r * trs + c * tcs];
-// lower: forward substitution, else backward.  Vector v element i at
-// X[v * vstride + i * estride].
-__global__ void trsv_block_kernel(int64_t nvec, int len, double* __restrict__ X,
-                                  int64_t vstride, int64_t estride,
-                                  const double* __restrict__ Tm, int64_t trs, int64_t tcs,
-                                  int lower, int unit) {
+// Solve T x = b for `nvec` vectors of length `len` (<= 64), one warp per vector; lane q
+// holds x_q and x_{q+32}.  T(r, c) = Tm[r * trs + c * tcs]; lower: forward substitution,
+// else backward.  Vector v element i at X[v * vstride + i * estride].
+__global__ void __launch_bounds__(256) trsv_block_kernel(int64_t nvec, int len,
+                                                         double* __restrict__ X,
+                                                         int64_t vstride, int64_t estride,
+                                                         const double* __restrict__ Tm,
+                                                         int64_t trs, int64_t tcs, int lower,
+                                                         int unit) {
   __shared__ double Ts[TNB][TNB + 1];
   for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
     const int r = e % len, c = e / len;
     Ts[r][c] = Tm[r * trs + c * tcs];
   }
   __syncthreads();
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (v >= nvec) return;
   double* x = X + v * vstride;
-  double loc[TNB];
-  for (int i = 0; i < len; ++i) loc[i] = x[i * estride];
-  if (lower) {
-    for (int i = 0; i < len; ++i) {
-      double s = loc[i];
-      for (int c = 0; c < i; ++c) s -= Ts[i][c] * loc[c];
-      loc[i] = unit ? s : s / Ts[i][i];
+  double x0 = lane < len ? x[lane * estride] : 0.0;
+  double x1 = lane + 32 < len ? x[(lane + 32) * estride] : 0.0;
+  for (int t = 0; t < len; ++t) {
+    const int i = lower ? t : len - 1 - t;
+    // dot over the already solved entries (c < i for lower, c > i for upper)
+    double part = 0.0;
+    const int c0 = lane, c1 = lane + 32;
+    if (lower) {
+      if (c0 < i) part = fma(Ts[i][c0], x0, part);
+      if (c1 < i) part = fma(Ts[i][c1], x1, part);
+    } else {
+      if (c0 > i && c0 < len) part = fma(Ts[i][c0], x0, part);
+      if (c1 > i && c1 < len) part = fma(Ts[i][c1], x1, part);
     }
-  } else {
-    for (int i = len - 1; i >= 0; --i) {
-      double s = loc[i];
-      for (int c = i + 1; c < len; ++c) s -= Ts[i][c] * loc[c];
-      loc[i] = unit ? s : s / Ts[i][i];
+    part = warp_sum(part);
+    part = __shfl_sync(0xffffffffu, part, 0);
+    if (lane == (i & 31)) {
+      double& xi = (i < 32) ? x0 : x1;
+      const double s = xi - part;
+      xi = unit ? s : s / Ts[i][i];
     }
   }
-  for (int i = 0; i < len; ++i) x[i * estride] = loc[i];
+  if (lane < len) x[lane * estride] = x0;
+  if (lane + 32 < len) x[(lane + 32) * estride] = x1;
 }
 
 // Pointer/trans to the sub-block op(A)[r0:, c0:] for use as a GEMM operand.
@@ -168,12 +281,12 @@ void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t
     int64_t rs = trans ? lda : 1, cs = trans ? 1 : lda;
     if (left) {
       const int64_t nvec = N;
-      trsv_block_kernel<<<(unsigned)cdiv(nvec, 64), 64, 0, st>>>(
+      trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
           nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
     } else {
       // X T = B  <=>  T^T x^T = b^T : matrix element (r, c) of T^T = T(c, r)
       const int64_t nvec = M;
-      trsv_block_kernel<<<(unsigned)cdiv(nvec, 64), 64, 0, st>>>(
+      trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
           nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
     }
     APL_LAUNCH_CHECK();
@@ -218,55 +331,65 @@ void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t
 }
 
 // ------------------------------------------------------------------------------------
-// Cholesky (upper), one CTA, right-looking, in global memory.
+// Cholesky (upper), blocked: a shared-memory kernel factors each diagonal block of at
+// most 64, a triangular solve forms the block row and a GEMM updates the trailing part.
 // ------------------------------------------------------------------------------------
 namespace {
-__global__ void __launch_bounds__(1024) potrf_upper_kernel(int64_t n, double* A, int64_t lda,
-                                                           int* info) {
+constexpr int PNB = 64;
+
+__global__ void __launch_bounds__(256) potrf_small_kernel(int nb, double* A, int64_t lda,
+                                                          int* info, int64_t koff) {
+  __shared__ double S[PNB][PNB + 1];
   __shared__ int bad;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e % nb, c = e / nb;
+    S[r][c] = A[r + c * lda];
+  }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  for (int64_t k = 0; k < n; ++k) {
+  for (int k = 0; k < nb; ++k) {
     if (threadIdx.x == 0) {
-      const double d = A[k + k * lda];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = (int)k + 1;
-      } else {
-        A[k + k * lda] = sqrt(d);
-      }
+      const double d = S[k][k];
+      if (!(d > 0.0) || !isfinite(d)) bad = k + 1;
+      else S[k][k] = sqrt(d);
     }
     __syncthreads();
     if (bad) break;
-    const double dk = A[k + k * lda];
-    for (int64_t j = k + 1 + threadIdx.x; j < n; j += blockDim.x) A[k + j * lda] /= dk;
+    const double dk = S[k][k];
+    for (int j = k + 1 + threadIdx.x; j < nb; j += blockDim.x) S[k][j] /= dk;
     __syncthreads();
-    // trailing update of the upper triangle: A[i, j] -= A[k, i] A[k, j], k < i <= j
-    const int64_t t = n - k - 1;
-    const int64_t total = t * (t + 1) / 2;
-    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-      // map e -> (i, j) with i <= j over the t x t trailing block, column-major packed
-      int64_t j = (int64_t)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-      while ((j + 1) * (j + 2) / 2 <= e) ++j;
-      while (j * (j + 1) / 2 > e) --j;
-      const int64_t i = e - j * (j + 1) / 2;
-      const int64_t gi = k + 1 + i, gj = k + 1 + j;
-      A[gi + gj * lda] -= A[k + gi * lda] * A[k + gj * lda];
+    const int t = nb - k - 1;
+    for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+      const int i = k + 1 + e / t, j = k + 1 + e % t;
+      if (j >= i) S[i][j] -= S[k][i] * S[k][j];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *info = bad;
-  // zero the strictly lower part
-  for (int64_t e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int64_t r = e % n, c = e / n;
-    if (r > c) A[r + c * lda] = 0.0;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e % nb, c = e / nb;
+    A[r + c * lda] = r <= c ? S[r][c] : 0.0;
   }
+  if (threadIdx.x == 0 && bad && *info == 0) *info = (int)koff + bad;
 }
 }  // namespace
 
 void dpotrf_upper(cudaStream_t st, int64_t n, double* A, int64_t lda, int* info_dev) {
   if (n <= 0) return;
-  potrf_upper_kernel<<<1, 1024, 0, st>>>(n, A, lda, info_dev);
-  APL_LAUNCH_CHECK();
+  APL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
+  for (int64_t k0 = 0; k0 < n; k0 += PNB) {
+    const int64_t kb = std::min<int64_t>(PNB, n - k0);
+    double* Akk = A + k0 + k0 * lda;
+    potrf_small_kernel<<<1, 256, 0, st>>>((int)kb, Akk, lda, info_dev, k0);
+    APL_LAUNCH_CHECK();
+    const int64_t rest = n - k0 - kb;
+    if (rest > 0) {
+      double* Akr = A + k0 + (k0 + kb) * lda;
+      dtrsm(st, true, 'U', true, false, kb, rest, Akk, lda, Akr, lda);
+      dgemm(st, 1, 0, rest, rest, kb, -1.0, Akr, lda, Akr, lda, 1.0,
+            A + (k0 + kb) + (k0 + kb) * lda, lda);
+    }
+  }
+  dzero_lower(st, n, A, lda);
 }
 
 bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, double* R,
@@ -295,8 +418,12 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
 }
 
 // ------------------------------------------------------------------------------------
-// One-sided Jacobi SVD.  Round-robin ordering: in round r the N (even) columns form
-// N/2 disjoint pairs; one block rotates one pair of M and of V.
+// One-sided (Hestenes) Jacobi on the columns of B.  Round-robin ordering: in round r the
+// N (even) columns form N/2 disjoint pairs; one block rotates one pair.  No rotation
+// matrix is accumulated: at convergence the columns of B are mutually orthogonal, their
+// norms are the singular values of B and the normalised columns its left singular
+// vectors.  Applied to B = M^T this yields the singular values and the right singular
+// vectors of M.
 // ------------------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ int64_t rr_elem(int64_t pos, int64_t r, int64_t N) {
@@ -304,8 +431,7 @@ __device__ __forceinline__ int64_t rr_elem(int64_t pos, int64_t r, int64_t N) {
 }
 
 __global__ void __launch_bounds__(256) jacobi_round_kernel(int64_t l, int64_t N, int64_t r,
-                                                           double* __restrict__ M, int64_t ldm,
-                                                           double* __restrict__ V, int64_t ldv,
+                                                           double* __restrict__ B, int64_t ldb,
                                                            double tol, int* rotated) {
   __shared__ double sh[3][8];
   __shared__ double cs[2];
@@ -314,11 +440,11 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(int64_t l, int64_t N,
   int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
   if (p >= l || q >= l) return;
   if (p > q) { const int64_t t = p; p = q; q = t; }
-  double* mp = M + p * ldm;
-  double* mq = M + q * ldm;
+  double* bp = B + p * ldb;
+  double* bq = B + q * ldb;
   double a = 0.0, b = 0.0, g = 0.0;
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const double x = mp[i], y = mq[i];
+    const double x = bp[i], y = bq[i];
     a = fma(x, x, a);
     b = fma(y, y, b);
     g = fma(x, y, g);
@@ -347,16 +473,9 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(int64_t l, int64_t N,
   if (!doit) return;
   const double c = cs[0], s = cs[1];
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const double x = mp[i], y = mq[i];
-    mp[i] = c * x - s * y;
-    mq[i] = s * x + c * y;
-  }
-  double* vp = V + p * ldv;
-  double* vq = V + q * ldv;
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const double x = vp[i], y = vq[i];
-    vp[i] = c * x - s * y;
-    vq[i] = s * x + c * y;
+    const double x = bp[i], y = bq[i];
+    bp[i] = c * x - s * y;
+    bq[i] = s * x + c * y;
   }
 }
 
@@ -374,58 +493,60 @@ __global__ void col_norms_kernel(int64_t rows, int64_t cols, const double* M, in
   if (threadIdx.x == 0) out[c] = sqrt(s);
 }
 
-__global__ void eye_kernel(int64_t n, double* V, int64_t ldv) {
+// dst(:, q) = src(:, idx[q]) / sig[q]  (zero column when sig[q] == 0)
+__global__ void gather_normalise_kernel(int64_t rows, const double* src, int64_t lds,
+                                        const int* idx, const double* sig, int64_t k, double* dst,
+                                        int64_t ldd) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * n) return;
-  const int64_t r = e % n, c = e / n;
-  V[r + c * ldv] = (r == c) ? 1.0 : 0.0;
+  if (e >= rows * k) return;
+  const int64_t r = e % rows, q = e / rows;
+  const double sq = sig[q];
+  dst[r + q * ldd] = sq > 0.0 ? src[r + (int64_t)idx[q] * lds] / sq : 0.0;
 }
 }  // namespace
 
-int jacobi_svd(cudaStream_t st, int64_t l, double* M, int64_t ldm, double* V, int64_t ldv,
-               double* sigma, double* work, int* flag_dev) {
+int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
+                double* sigma, int* flag_dev) {
   if (l <= 0) return 0;
-  eye_kernel<<<(unsigned)cdiv(l * l, 256), 256, 0, st>>>(l, V, ldv);
-  APL_LAUNCH_CHECK();
   const int64_t N = (l % 2) ? l + 1 : l;
-  const double tol = 1e-15;
+  // relative orthogonality threshold: l * eps, the accuracy the rotations can reach
+  const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
   int sweeps = 0;
   if (l > 1) {
     for (; sweeps < 60;) {
       APL_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int), st));
-      for (int64_t r = 0; r < N - 1; ++r) {
-        jacobi_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, M, ldm, V, ldv, tol,
-                                                                 flag_dev);
-      }
+      const int tok = prof_begin(st);
+      for (int64_t r = 0; r < N - 1; ++r)
+        jacobi_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, B, ldb, tol, flag_dev);
       APL_LAUNCH_CHECK();
+      prof_end(st, tok, PROF_JACOBI, 0.0);
       ++sweeps;
       int rot = 0;
       APL_CUDA(cudaMemcpyAsync(&rot, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
       APL_CUDA(cudaStreamSynchronize(st));
+      // FP64 flops of the sweep: three dot products per pair, a 2-column rotation per hit
+      prof_set_work(tok, 6.0 * (double)l * ((double)(l * (l - 1)) / 2.0 + (double)rot));
       if (rot == 0) break;
     }
   }
-  col_norms_kernel<<<(unsigned)l, 256, 0, st>>>(l, l, M, ldm, sigma);
+  col_norms_kernel<<<(unsigned)l, 256, 0, st>>>(l, l, B, ldb, sigma);
   APL_LAUNCH_CHECK();
-  // sort descending (stable) and permute the columns of V
   std::vector<double> sg(l);
   APL_CUDA(cudaMemcpyAsync(sg.data(), sigma, l * sizeof(double), cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaStreamSynchronize(st));
   std::vector<int> perm(l);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sg[a] > sg[b]; });
-  bool ident = true;
-  for (int64_t i = 0; i < l; ++i) ident = ident && perm[i] == i;
-  if (!ident) {
-    std::vector<double> ss(l);
-    for (int64_t i = 0; i < l; ++i) ss[i] = sg[perm[i]];
-    int* perm_dev = reinterpret_cast<int*>(work + l * l);
-    APL_CUDA(cudaMemcpyAsync(perm_dev, perm.data(), l * sizeof(int), cudaMemcpyHostToDevice, st));
-    dgather_cols(st, l, V, ldv, perm_dev, l, work, l);
-    dcopy2d(st, l, l, work, l, V, ldv, false);
-    APL_CUDA(cudaMemcpyAsync(sigma, ss.data(), l * sizeof(double), cudaMemcpyHostToDevice, st));
-    APL_CUDA(cudaStreamSynchronize(st));
-  }
+  std::vector<double> ss(l);
+  for (int64_t i = 0; i < l; ++i) ss[i] = sg[perm[i]];
+  DBuf<int> perm_dev;
+  perm_dev.alloc(l, st);
+  APL_CUDA(cudaMemcpyAsync(perm_dev.p, perm.data(), l * sizeof(int), cudaMemcpyHostToDevice, st));
+  APL_CUDA(cudaMemcpyAsync(sigma, ss.data(), l * sizeof(double), cudaMemcpyHostToDevice, st));
+  gather_normalise_kernel<<<(unsigned)cdiv(l * l, 256), 256, 0, st>>>(l, B, ldb, perm_dev.p, sigma,
+                                                                     l, U, ldu);
+  APL_LAUNCH_CHECK();
+  APL_CUDA(cudaStreamSynchronize(st));
   return sweeps;
 }
 

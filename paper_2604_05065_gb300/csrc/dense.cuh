@@ -24,11 +24,12 @@ void dpotrf_upper(cudaStream_t st, int64_t n, double* A, int64_t lda, int* info_
 bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, double* R,
              int64_t ldr, double* work, int* info_dev);
 
-// One-sided Jacobi SVD of the square M (l x l, in place): on return the columns of M
-// are U Sigma and V (l x l) holds the right singular vectors; sigma gets the column
-// norms.  Columns are sorted by descending sigma.  Returns the sweep count.
-int jacobi_svd(cudaStream_t st, int64_t l, double* M, int64_t ldm, double* V, int64_t ldv,
-               double* sigma, double* work, int* flag_dev);
+// One-sided Jacobi on the columns of the square B (l x l, in place, destroyed).
+// sigma receives the singular values of B in descending order and U (l x l, ldu) the
+// matching left singular vectors (normalised columns).  With B = M^T these are the
+// singular values and right singular vectors of M.  Returns the sweep count.
+int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
+                double* sigma, int* flag_dev);
 
 // Elementwise helpers.
 void dcopy2d(cudaStream_t st, int64_t rows, int64_t cols, const double* src, int64_t lds,

@@ -416,75 +416,97 @@ __global__ void __launch_bounds__(NT) k2b_dense(int64_t m, int64_t n, int rchunk
   if (threadIdx.x == 0) finalize_alpha(ctl, tot, init);
 }
 
-// ---- preconditioner passes (FP64 Vhat) -------------------------------------------------
+// ---- preconditioner passes (FP64, Vhat = Q_R V_M implicit) -----------------------------
 
-__global__ void __launch_bounds__(128) k3_partial(int64_t n, int ell, int64_t ldv,
-                                                  const double* __restrict__ V,
-                                                  const double* __restrict__ w,
-                                                  double* __restrict__ tpart, int64_t rows_per,
-                                                  const LsqrCtl* ctl) {
+// q1 = Q^T w: one warp per column of Q.
+__global__ void __launch_bounds__(NT) pre_qt(int64_t n, int ell, int64_t ldq,
+                                             const double* __restrict__ Q,
+                                             const double* __restrict__ w,
+                                             double* __restrict__ q1, const LsqrCtl* ctl) {
   if (ctl && ctl->done) return;
-  const int k = blockIdx.x * 128 + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   if (k >= ell) return;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per;
-  const int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
-  double acc = 0.0;
-  for (int64_t i = r0; i < r1; ++i) acc = fma(V[i * ldv + k], w[i], acc);
-  tpart[(int64_t)blockIdx.y * ell + k] = acc;
+  const double* qk = Q + k * ldq;
+  double s = 0.0;
+  for (int64_t i = lane; i < n; i += 32) s = fma(qk[i], w[i], s);
+  s = warp_sum(s);
+  if (lane == 0) q1[k] = s;
 }
 
-__global__ void k3_reduce(int ell, int chunks, const double* __restrict__ tpart,
-                          const double* __restrict__ coef, const double* __restrict__ coef2,
-                          double* __restrict__ ct, double* __restrict__ c2t, const LsqrCtl* ctl) {
+// ct = coef (V_M^T q1), c2t = coef2 (V_M^T q1): one warp per column of V_M.
+__global__ void __launch_bounds__(NT) pre_vt(int ell, const double* __restrict__ VM,
+                                             const double* __restrict__ q1,
+                                             const double* __restrict__ coef,
+                                             const double* __restrict__ coef2,
+                                             double* __restrict__ ct, double* __restrict__ c2t,
+                                             const LsqrCtl* ctl) {
   if (ctl && ctl->done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   if (k >= ell) return;
-  double t = 0.0;
-  for (int c = 0; c < chunks; ++c) t += tpart[(int64_t)c * ell + k];
-  ct[k] = coef[k] * t;
-  if (c2t) c2t[k] = coef2[k] * t;
+  const double* vk = VM + k * (int64_t)ell;
+  double s = 0.0;
+  for (int i = lane; i < ell; i += 32) s = fma(vk[i], q1[i], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    ct[k] = coef[k] * s;
+    if (c2t) c2t[k] = coef2[k] * s;
+  }
 }
 
-// Expansion, one warp per row: out1 = w + V ct, out2 = w + V c2t.  In the LSQR phase
-// also subtracts beta v / beta z, writes the FP32 split of z' and reduces ||v'||^2.
-__global__ void __launch_bounds__(NT) k4_expand(int64_t n, int ell, int64_t ldv,
-                                                const double* __restrict__ V,
-                                                const double* __restrict__ ct,
-                                                const double* __restrict__ c2t,
-                                                const double* __restrict__ w, double* out1,
-                                                double* out2, float* zh, float* zl,
-                                                LsqrCtl* ctl, double* __restrict__ red, int init) {
+// q3 = V_M ct, q3b = V_M c2t: one thread per row of V_M.
+__global__ void __launch_bounds__(NT) pre_v(int ell, const double* __restrict__ VM,
+                                            const double* __restrict__ ct,
+                                            const double* __restrict__ c2t,
+                                            double* __restrict__ q3, double* __restrict__ q3b,
+                                            const LsqrCtl* ctl) {
+  if (ctl && ctl->done) return;
+  const int i = blockIdx.x * NT + threadIdx.x;
+  if (i >= ell) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int k = 0; k < ell; ++k) {
+    const double v = VM[i + (int64_t)k * ell];
+    s1 = fma(v, ct[k], s1);
+    if (q3b) s2 = fma(v, c2t[k], s2);
+  }
+  q3[i] = s1;
+  if (q3b) q3b[i] = s2;
+}
+
+// out1 = w + Q q3, out2 = w + Q q3b, one thread per row of Q.  In the LSQR phase also
+// subtracts beta v / beta z, writes the FP32 split of z' and reduces ||v'||^2.
+__global__ void __launch_bounds__(NT) pre_expand(int64_t n, int ell, int64_t ldq,
+                                                 const double* __restrict__ Q,
+                                                 const double* __restrict__ q3,
+                                                 const double* __restrict__ q3b,
+                                                 const double* __restrict__ w, double* out1,
+                                                 double* out2, float* zh, float* zl,
+                                                 LsqrCtl* ctl, double* __restrict__ red,
+                                                 int init) {
   __shared__ double sh[NT / 32];
   if (ctl && ctl->done) return;
   double beta = 0.0, zs = 0.0;
   if (ctl && !init) { beta = ctl->beta; zs = ctl->zs; }
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   double ss = 0.0;
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const double* vr = V + i * ldv;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
     double s1 = 0.0, s2 = 0.0;
-    for (int k = lane; k < ell; k += 32) {
-      const double vv = vr[k];
-      s1 = fma(vv, ct[k], s1);
-      if (out2) s2 = fma(vv, c2t[k], s2);
+    for (int k = 0; k < ell; ++k) {
+      const double q = Q[i + k * ldq];
+      s1 = fma(q, q3[k], s1);
+      if (out2) s2 = fma(q, q3b[k], s2);
     }
-    const double a1 = warp_sum(s1);
-    const double a2 = out2 ? warp_sum(s2) : 0.0;
-    if (lane == 0) {
-      const double wi = w[i];
-      double o1 = wi + a1;
-      if (ctl && !init) o1 -= beta * (out1[i] * zs);
-      out1[i] = o1;
-      if (out2) {
-        double o2 = wi + a2;
-        if (ctl && !init) o2 -= beta * (out2[i] * zs);
-        out2[i] = o2;
-        if (zh) split(o2, zh, zl, i);
-      }
-      ss += o1 * o1;
+    const double wi = w[i];
+    double o1 = wi + s1;
+    if (ctl && !init) o1 -= beta * (out1[i] * zs);
+    out1[i] = o1;
+    if (out2) {
+      double o2 = wi + s2;
+      if (ctl && !init) o2 -= beta * (out2[i] * zs);
+      out2[i] = o2;
+      if (zh) split(o2, zh, zl, i);
     }
+    ss += o1 * o1;
   }
   if (!ctl) return;
   const double b = block_sum(ss, sh);
@@ -738,21 +760,26 @@ void LsqrEngine::launch_k2(bool init, bool fused) {
 void LsqrEngine::launch_pre(const PrecondDev& P, const double* w, double* o1, double* o2,
                             bool in_phase, bool init) {
   const int ell = P.ell;
-  const int kb = (int)cdiv(ell, 128);
-  const int64_t rows_per = cdiv(n_, tchunks_);
-  dim3 grid((unsigned)kb, (unsigned)tchunks_);
+  q1_.alloc(ell, st_);
+  ct_.alloc(ell, st_);
+  c2t_.alloc(ell, st_);
+  q3_.alloc(ell, st_);
+  q3b_.alloc(ell, st_);
   const LsqrCtl* c = in_phase ? ctl_.p : nullptr;
-  k3_partial<<<grid, 128, 0, st_>>>(n_, ell, P.ldv, P.V64, w, tpart_.p, rows_per, c);
+  const unsigned wb = (unsigned)cdiv((int64_t)ell * 32, NT);
+  pre_qt<<<wb, NT, 0, st_>>>(n_, ell, P.ldq, P.Q, w, q1_.p, c);
   APL_LAUNCH_CHECK();
-  k3_reduce<<<(unsigned)cdiv(ell, 128), 128, 0, st_>>>(ell, tchunks_, tpart_.p, P.coef, P.coef2,
-                                                       ct_.p, o2 ? c2t_.p : nullptr, c);
+  pre_vt<<<wb, NT, 0, st_>>>(ell, P.VM, q1_.p, P.coef, P.coef2, ct_.p, o2 ? c2t_.p : nullptr, c);
   APL_LAUNCH_CHECK();
-  const int blocks = (int)std::min<int64_t>(cdiv(n_ * 32, NT), sm_blocks());
+  pre_v<<<(unsigned)cdiv(ell, NT), NT, 0, st_>>>(ell, P.VM, ct_.p, c2t_.p, q3_.p,
+                                                 o2 ? q3b_.p : nullptr, c);
+  APL_LAUNCH_CHECK();
+  const int blocks = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
   LsqrCtl* cw = in_phase ? ctl_.p : nullptr;
   float* zh = (in_phase && mode_) ? zh_.p : nullptr;
   float* zl = (in_phase && mode_) ? zl_.p : nullptr;
-  k4_expand<<<blocks, NT, 0, st_>>>(n_, ell, P.ldv, P.V64, ct_.p, c2t_.p, w, o1, o2, zh, zl, cw,
-                                    red_.p, init);
+  pre_expand<<<blocks, NT, 0, st_>>>(n_, ell, P.ldq, P.Q, q3_.p, q3b_.p, w, o1, o2, zh, zl, cw,
+                                     red_.p, init);
   APL_LAUNCH_CHECK();
 }
 
@@ -817,11 +844,11 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   x_ = a.x;
   const bool pre = P.ell > 0;
   if (pre) {
-    tchunks_ = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, cdiv(P.ell, 128)),
-                                                          cdiv(n_, 32)));
-    tpart_.alloc((size_t)tchunks_ * P.ell, st_);
+    q1_.alloc(P.ell, st_);
     ct_.alloc(P.ell, st_);
     c2t_.alloc(P.ell, st_);
+    q3_.alloc(P.ell, st_);
+    q3b_.alloc(P.ell, st_);
   }
   // In the FP32-sum mode each phase is the inner solve of an FP64 iterative refinement:
   // it stops once the estimate of ||Abar^T rbar|| fell by 1e-4 from its phase-start value
@@ -878,9 +905,9 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
       prof.bytes[0] = (double)A_.nnz * (va + 4) + 4.0 * (m_ + 1) + sv * n_ + 16.0 * (m_ + n_);
       prof.bytes[1] = (double)A_.nnz * (va + 4) + 4.0 * (n_ + 1) + sv * m_ + 8.0 * n_ + 48.0 * n_;
     }
-    prof.bytes[2] = 2.0 * n_ * ell * 8.0 + 56.0 * n_;
+    prof.bytes[2] = 2.0 * n_ * ell * 8.0 + 2.0 * ell * ell * 8.0 + 56.0 * n_;
   }
-  kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 3 : 0);
+  kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 4 : 0);
   if (profile_) ensure_events(4 * std::max(G, 1));
   auto iteration = [&](int i) {
     if (profile_) record(4 * i);
@@ -1075,11 +1102,6 @@ void LsqrEngine::apply_precond(const PrecondDev& P, const double* w, double* out
       APL_CUDA(cudaMemcpyAsync(out2, w, n_ * sizeof(double), cudaMemcpyDeviceToDevice, st_));
     return;
   }
-  tchunks_ = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, cdiv(P.ell, 128)),
-                                                        cdiv(n_, 32)));
-  tpart_.alloc((size_t)tchunks_ * P.ell, st_);
-  ct_.alloc(P.ell, st_);
-  c2t_.alloc(P.ell, st_);
   launch_pre(P, w, out, out2, false, false);
 }
 

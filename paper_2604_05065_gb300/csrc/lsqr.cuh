@@ -36,12 +36,14 @@ struct LsqrCtl {
   unsigned int counter[8];
 };
 
-// The preconditioner P^{-1} = I + Vhat diag(coef) Vhat^T (Eq. preconditioner2), with
-// Vhat stored row-major n x ell (ld ldv) in FP64; coef2 gives P^{-2}.
+// The preconditioner P^{-1} = I + Vhat diag(coef) Vhat^T (Eq. preconditioner2) with Vhat
+// kept implicit as Q_R V_M: Q (n x ell, column-major, ld ldq) and VM (ell x ell,
+// column-major).  coef2 gives P^{-2} = I + Vhat diag(coef2) Vhat^T.
 struct PrecondDev {
   int ell = 0;
-  int64_t ldv = 0;
-  const double* V64 = nullptr;
+  int64_t ldq = 0;
+  const double* Q = nullptr;
+  const double* VM = nullptr;
   const double* coef = nullptr;
   const double* coef2 = nullptr;
   double normP = 1.0;    // ||P||_2
@@ -97,12 +99,11 @@ class LsqrEngine {
   int64_t m_ = 0, n_ = 0;
   int k1_blocks_ = 0, k2_blocks_ = 0, k2_rchunks_ = 1, red_cap_ = 0;
   DBuf<LsqrCtl> ctl_;
-  DBuf<double> u_, v_, z_, g_, d_, red_, part_, tpart_, ct_, c2t_, r_, q_;
+  DBuf<double> u_, v_, z_, g_, d_, red_, part_, q1_, ct_, c2t_, q3_, q3b_, r_, q_;
   DBuf<float> zh_, zl_, uh_, ul_;  // FP32 hi/lo splits of z' and u' (modes 1, 2)
   DBuf<double> scal_;
   DBuf<unsigned int> cnt_;
   double* x_ = nullptr;
-  int tchunks_ = 1, tcap_ = 0;
   bool profile_ = false;
   std::vector<cudaEvent_t> ev_;
   int kernels_per_iter_ = 0;
