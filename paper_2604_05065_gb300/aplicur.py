@@ -331,6 +331,9 @@ class Solver:
         return {"ms": list(pr.ms), "launches": list(pr.launches), "work": list(pr.work),
                 "kernel_launches": pr.kernel_launches}
 
+    def reset_profile(self):
+        _check(self._lib, self._lib.aplicur_reset_profile(self._h), self._h)
+
     def matvec(self, x, trans: bool = False):
         torch = _torch()
         x = x.to(torch.float64).contiguous()

@@ -505,29 +505,182 @@ __global__ void gather_normalise_kernel(int64_t rows, const double* src, int64_t
 }
 }  // namespace
 
+namespace {
+// FP32 stage: one warp per pair; rotates the FP32 copy of B and accumulates the rotations
+// in W.  The angle is computed in FP64 from the FP32 sums (a few FP64 ops per pair).
+__global__ void __launch_bounds__(128) jacobi32_round_kernel(int64_t l, int64_t N, int64_t r,
+                                                             float* __restrict__ B,
+                                                             float* __restrict__ W, int64_t ld,
+                                                             double tol, int* rotated) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= N / 2) return;
+  int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
+  if (p >= l || q >= l) return;
+  if (p > q) { const int64_t t = p; p = q; q = t; }
+  float* bp = B + p * ld;
+  float* bq = B + q * ld;
+  float a = 0.f, b = 0.f, g = 0.f;
+  for (int64_t i = lane; i < l; i += 32) {
+    const float x = bp[i], y = bq[i];
+    a = fmaf(x, x, a);
+    b = fmaf(y, y, b);
+    g = fmaf(x, y, g);
+  }
+  a = __shfl_sync(0xffffffffu, warp_sumf(a), 0);
+  b = __shfl_sync(0xffffffffu, warp_sumf(b), 0);
+  g = __shfl_sync(0xffffffffu, warp_sumf(g), 0);
+  const double A_ = a, B_ = b, G_ = g;
+  if (!(A_ > 0.0 && B_ > 0.0 && fabs(G_) > tol * sqrt(A_) * sqrt(B_))) return;
+  const double zeta = (B_ - A_) / (2.0 * G_);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cd = 1.0 / sqrt(1.0 + t * t);
+  const float c = (float)cd, s = (float)(cd * t);
+  if (lane == 0) atomicAdd(rotated, 1);
+  float* wp = W + p * ld;
+  float* wq = W + q * ld;
+  for (int64_t i = lane; i < l; i += 32) {
+    const float x = bp[i], y = bq[i];
+    bp[i] = c * x - s * y;
+    bq[i] = s * x + c * y;
+    const float u = wp[i], v = wq[i];
+    wp[i] = c * u - s * v;
+    wq[i] = s * u + c * v;
+  }
+}
+
+// FP64 stage: one warp per pair, no rotation accumulation.
+__global__ void __launch_bounds__(128) jacobi64_round_kernel(int64_t l, int64_t N, int64_t r,
+                                                             double* __restrict__ B, int64_t ldb,
+                                                             double tol, int* rotated) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= N / 2) return;
+  int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
+  if (p >= l || q >= l) return;
+  if (p > q) { const int64_t t = p; p = q; q = t; }
+  double* bp = B + p * ldb;
+  double* bq = B + q * ldb;
+  double a = 0.0, b = 0.0, g = 0.0;
+  for (int64_t i = lane; i < l; i += 32) {
+    const double x = bp[i], y = bq[i];
+    a = fma(x, x, a);
+    b = fma(y, y, b);
+    g = fma(x, y, g);
+  }
+  a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
+  b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
+  g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
+  if (!(a > 0.0 && b > 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b))) return;
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  const double s = c * t;
+  if (lane == 0) atomicAdd(rotated, 1);
+  for (int64_t i = lane; i < l; i += 32) {
+    const double x = bp[i], y = bq[i];
+    bp[i] = c * x - s * y;
+    bq[i] = s * x + c * y;
+  }
+}
+
+__global__ void d2f_kernel(int64_t n, const double* s, float* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+__global__ void f2d_kernel(int64_t n, const float* s, double* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (double)s[i];
+}
+__global__ void eye32_kernel(int64_t n, float* W) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * n) W[e] = (e % n == e / n) ? 1.f : 0.f;
+}
+
+thread_local DBuf<float> g_jb32, g_jw32;
+thread_local DBuf<double> g_jw64, g_jtmp;
+
+// Run sweeps of `round` (a lambda launching round r) as one captured graph per sweep
+// until a sweep rotates nothing; returns the sweep count.
+template <typename F>
+int run_sweeps(cudaStream_t st, int64_t N, int max_sweeps, int* flag_dev, F&& round,
+               int prof_cat, double flops_per_sweep, double flops_per_rot) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  APL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  {
+    CaptureScope cs;
+    try {
+      for (int64_t r = 0; r < N - 1; ++r) round(r);
+    } catch (...) {
+      cudaStreamEndCapture(st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+  }
+  APL_CUDA(cudaStreamEndCapture(st, &graph));
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  APL_CUDA(e);
+  struct Guard {
+    cudaGraphExec_t e;
+    ~Guard() { cudaGraphExecDestroy(e); }
+  } guard{exec};
+  int sweeps = 0;
+  for (; sweeps < max_sweeps;) {
+    APL_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int), st));
+    const int tok = prof_cat >= 0 ? prof_begin(st) : -1;
+    APL_CUDA(cudaGraphLaunch(exec, st));
+    add_launches(N - 1);
+    if (tok >= 0) prof_end(st, tok, prof_cat, 0.0);
+    ++sweeps;
+    int rot = 0;
+    APL_CUDA(cudaMemcpyAsync(&rot, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    APL_CUDA(cudaStreamSynchronize(st));
+    if (tok >= 0) prof_set_work(tok, flops_per_sweep + flops_per_rot * rot);
+    if (rot == 0) break;
+  }
+  return sweeps;
+}
+}  // namespace
+
 int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
                 double* sigma, int* flag_dev) {
   if (l <= 0) return 0;
   const int64_t N = (l % 2) ? l + 1 : l;
-  // relative orthogonality threshold: l * eps, the accuracy the rotations can reach
-  const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
+  const unsigned blocks = (unsigned)cdiv(N / 2 * 32, 128);
   int sweeps = 0;
   if (l > 1) {
-    for (; sweeps < 60;) {
-      APL_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int), st));
-      const int tok = prof_begin(st);
-      for (int64_t r = 0; r < N - 1; ++r)
-        jacobi_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, B, ldb, tol, flag_dev);
+    // Stage 1 (FP32 pipes): sweeps on an FP32 copy that accumulate the rotation W until
+    // the columns are orthogonal to FP32 accuracy; then B <- B W in FP64.
+    const int64_t l2 = l * l;
+    g_jb32.alloc(l2, st);
+    g_jw32.alloc(l2, st);
+    g_jw64.alloc(l2, st);
+    g_jtmp.alloc(l2, st);
+    float* B32 = g_jb32.p;
+    float* W32 = g_jw32.p;
+    for (int64_t c = 0; c < l; ++c)
+      d2f_kernel<<<(unsigned)cdiv(l, 256), 256, 0, st>>>(l, B + c * ldb, B32 + c * l);
+    APL_LAUNCH_CHECK();
+    eye32_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32);
+    APL_LAUNCH_CHECK();
+    const double tol32 = std::max(1e-6, (double)l * 6e-8);
+    sweeps += run_sweeps(st, N, 40, flag_dev, [&](int64_t r) {
+      jacobi32_round_kernel<<<blocks, 128, 0, st>>>(l, N, r, B32, W32, l, tol32, flag_dev);
       APL_LAUNCH_CHECK();
-      prof_end(st, tok, PROF_JACOBI, 0.0);
-      ++sweeps;
-      int rot = 0;
-      APL_CUDA(cudaMemcpyAsync(&rot, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-      APL_CUDA(cudaStreamSynchronize(st));
-      // FP64 flops of the sweep: three dot products per pair, a 2-column rotation per hit
-      prof_set_work(tok, 6.0 * (double)l * ((double)(l * (l - 1)) / 2.0 + (double)rot));
-      if (rot == 0) break;
-    }
+    }, -1, 0.0, 0.0);
+    f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, g_jw64.p);
+    APL_LAUNCH_CHECK();
+    dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, g_jw64.p, l, 0.0, g_jtmp.p, l);
+    dcopy2d(st, l, l, g_jtmp.p, l, B, ldb, false);
+    // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
+    const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
+    const double pairs = (double)(l * (l - 1)) / 2.0;
+    sweeps += run_sweeps(st, N, 60, flag_dev, [&](int64_t r) {
+      jacobi64_round_kernel<<<blocks, 128, 0, st>>>(l, N, r, B, ldb, tol, flag_dev);
+      APL_LAUNCH_CHECK();
+    }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l);
   }
   col_norms_kernel<<<(unsigned)l, 256, 0, st>>>(l, l, B, ldb, sigma);
   APL_LAUNCH_CHECK();
