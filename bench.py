@@ -61,6 +61,18 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def aggregate(ms_local, steps, world, device=None):
+    """Max over ranks of the timed region (ms) and the whole-job throughput: every rank
+    solved `steps` replicas, so value = world * steps / max_ms."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1000.0)
+
+
 def make_workload(name):
     from paper_2604_05065_gb300 import workloads as wl
     gen, prec = WORKLOADS[name]
@@ -192,12 +204,7 @@ def gpu_arm(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     launches = pkg.launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.steps / (ms_max / 1000.0)
+    ms_max, value = aggregate(e0.elapsed_time(e1), args.steps, world, dev)
 
     # ---- end to end from pinned host buffers
     e2e = None
@@ -219,11 +226,8 @@ def gpu_arm(args, rank, world, local_rank):
             xh = one_solve(Ae, be)[0].to("cpu")
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
-        et = torch.tensor([ems], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / (float(et.item()) / 1000.0), "unit": "solves/s",
+        _, e2e_value = aggregate(f0.elapsed_time(f1), args.steps, world, dev)
+        e2e = {"value": e2e_value, "unit": "solves/s",
                "h2d_bytes_per_step": int(A_host.numel() * A_host.element_size() + b_host.numel() * 8),
                "d2h_bytes_per_step": int(p.n * 8)}
         del Ae, be
@@ -397,6 +401,17 @@ def oracle_sample(p, sched, iters_sample=6):
     return 1.0 / est, sample, t_sketch + t_step + t_build + iters_sample * t_iter
 
 
+def make_config(p, prec, world):
+    return {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu, "sketch_dim": p.sketch_dim,
+            "tol": TOL,
+            "precision": {"mixed": "fp32 products and sums, fp64 scalars/core/refinement",
+                          "df32": "fp32 storage, compensated fp32 products and sums (hi/lo "
+                                  "split), fp64 scalars/core/preconditioner"}.get(prec, "fp64"),
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2" if p.nnz * p.dtype.itemsize > 129e6
+            else "L2-resident inputs (no flush)"}
+
+
 def load_schedule(name):
     path = os.path.join(ROOT, "tests", "golden", f"schedule_{name}.json")
     try:
@@ -422,8 +437,7 @@ def reference_arm(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu,
-                       "sketch_dim": p.sketch_dim, "tol": TOL},
+            "config": make_config(p, prec, world),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -458,14 +472,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if r["prec"] in ("mixed", "df32") else "f64", "data": "synthetic",
-                "config": {"workload": p.name, "m": p.m, "n": p.n, "mu": p.mu,
-                           "sketch_dim": p.sketch_dim, "tol": TOL,
-                           "precision": {"mixed": "fp32 products and sums, fp64 scalars/core/refinement",
-                                         "df32": "fp32 storage, compensated fp32 products and sums (hi/lo split), fp64 scalars/core/preconditioner",
-                                         }.get(r["prec"], "fp64"),
-                           "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2" if p.nnz * p.dtype.itemsize > 129e6
-                           else "L2-resident inputs (no flush)"},
+                "config": make_config(p, r["prec"], world),
                 "time_to_tol_s": r["ms"] / 1000.0, "schedule": r["sched"],
                 "ne_res": r["ne"], "plain_lsqr": r["plain"], "clocks": r["clocks"],
                 "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roof"],

@@ -395,7 +395,7 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
       add2d_kernel<<<(unsigned)cdiv((int64_t)ell * k, 256), 256, 0, st>>>(ell, k, h->P2b.p, cap, P1, cap);
       APL_LAUNCH_CHECK();
     }
-    h->work.alloc((size_t)2 * k * k + 16, st);
+    h->work.alloc((size_t)3 * k * k + 16, st);
     if (!cholqr2(st, n, k, Cn, n, h->TR.p + ell + (int64_t)ell * cap, cap, h->work.p, h->info.p))
       throw Error(ST_EBREAKDOWN, "Cholesky QR of the new rows of R met a non-positive pivot");
     h->I.insert(h->I.end(), Ip.begin(), Ip.begin() + k);

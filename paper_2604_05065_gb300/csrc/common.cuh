@@ -113,6 +113,31 @@ struct DBuf {
   }
 };
 
+// Per-thread workspace reused across contexts and streams (thread_local in the dense
+// routines).  It holds no stream: the stream a buffer was last used on may belong to a
+// context that has been destroyed since, so growth and release use the synchronous
+// cudaMalloc / cudaFree (rare: the size only grows).  Never grown inside stream capture.
+template <typename T>
+struct Scratch {
+  T* p = nullptr;
+  size_t n = 0;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (p) cudaFree(p);
+  }
+  void ensure(size_t count) {
+    if (count <= n && p) return;
+    if (p) APL_CUDA(cudaFree(p));
+    p = nullptr;
+    n = 0;
+    if (count == 0) return;
+    APL_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    n = count;
+  }
+};
+
 // ---- device reductions (fixed order -> bitwise reproducible) -------------------------
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -166,7 +166,7 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const dou
   *out = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *out;
 }
 
-thread_local DBuf<double> g_splitk_ws;
+thread_local Scratch<double> g_splitk_ws;
 }  // namespace
 
 void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -195,7 +195,7 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   if (splits > 1) {
     const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
     splits = cdiv(K, kchunk);
-    g_splitk_ws.alloc((size_t)splits * M * N, st);
+    g_splitk_ws.ensure((size_t)splits * M * N);
     grid.z = (unsigned)splits;
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc,
                                        kchunk, g_splitk_ws.p);
@@ -392,11 +392,28 @@ void dpotrf_upper(cudaStream_t st, int64_t n, double* A, int64_t lda, int* info_
   dzero_lower(st, n, A, lda);
 }
 
+namespace {
+thread_local Scratch<double> g_qr_tmp;
+
+// E <- E T^{-1} for upper triangular T (k x k): T^{-1} by a left triangular solve on the
+// identity (contiguous columns), then one GEMM; E's rows are never walked with a stride.
+void right_upper_inverse_apply(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde,
+                               const double* T, int64_t ldt, double* Tinv) {
+  dset2d(st, k, k, 0.0, Tinv, k);
+  dset_diag(st, k, 1.0, Tinv, k);
+  dtrsm(st, true, 'U', false, false, k, k, T, ldt, Tinv, k);
+  g_qr_tmp.ensure((size_t)n * k);
+  dgemm(st, 0, 0, n, k, k, 1.0, E, lde, Tinv, k, 0.0, g_qr_tmp.p, n);
+  dcopy2d(st, n, k, g_qr_tmp.p, n, E, lde, false);
+}
+}  // namespace
+
 bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, double* R,
              int64_t ldr, double* work, int* info_dev) {
-  // work: 2 k x k blocks
+  // work: 3 k x k blocks
   double* G = work;
   double* R1 = work + k * k;
+  double* Ti = work + 2 * k * k;
   int info = 0;
   dgemm(st, 1, 0, k, k, n, 1.0, E, lde, E, lde, 0.0, G, k);
   dpotrf_upper(st, k, G, k, info_dev);
@@ -404,13 +421,13 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
   APL_CUDA(cudaStreamSynchronize(st));
   if (info) return false;
   dcopy2d(st, k, k, G, k, R1, k, false);
-  dtrsm(st, false, 'U', false, false, n, k, R1, k, E, lde);
+  right_upper_inverse_apply(st, n, k, E, lde, R1, k, Ti);
   dgemm(st, 1, 0, k, k, n, 1.0, E, lde, E, lde, 0.0, G, k);
   dpotrf_upper(st, k, G, k, info_dev);
   APL_CUDA(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaStreamSynchronize(st));
   if (info) return false;
-  dtrsm(st, false, 'U', false, false, n, k, G, k, E, lde);
+  right_upper_inverse_apply(st, n, k, E, lde, G, k, Ti);
   // R = R2 R1 (both upper; lower parts are zero)
   dgemm(st, 0, 0, k, k, k, 1.0, G, k, R1, k, 0.0, R, ldr);
   dzero_lower(st, k, R, ldr);
@@ -419,11 +436,16 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
 
 // ------------------------------------------------------------------------------------
 // One-sided (Hestenes) Jacobi on the columns of B.  Round-robin ordering: in round r the
-// N (even) columns form N/2 disjoint pairs; one block rotates one pair.  No rotation
-// matrix is accumulated: at convergence the columns of B are mutually orthogonal, their
-// norms are the singular values of B and the normalised columns its left singular
-// vectors.  Applied to B = M^T this yields the singular values and the right singular
-// vectors of M.
+// N (even) columns form N/2 disjoint pairs; one block rotates one pair.  At convergence
+// the columns of B are mutually orthogonal, their norms are the singular values of B and
+// the normalised columns its left singular vectors.  Applied to B = M^T this yields the
+// singular values and the right singular vectors of M.
+//
+// Two stages, because FP64 arithmetic is scarce on this part and FP32 is not: stage 1
+// sweeps an FP32 copy of B and accumulates the rotations in W (FP32); W is then made
+// orthogonal to FP64 accuracy (Newton-Schulz) and applied to B in FP64, which leaves the
+// singular values untouched to FP64 rounding.  Stage 2 sweeps B in FP64 from this nearly
+// orthogonal start down to the l * eps threshold; its result alone fixes the accuracy.
 // ------------------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ int64_t rr_elem(int64_t pos, int64_t r, int64_t N) {
@@ -506,40 +528,54 @@ __global__ void gather_normalise_kernel(int64_t rows, const double* src, int64_t
 }  // namespace
 
 namespace {
-// FP32 stage: one warp per pair; rotates the FP32 copy of B and accumulates the rotations
+// FP32 stage: one block per pair; rotates the FP32 copy of B and accumulates the rotations
 // in W.  The angle is computed in FP64 from the FP32 sums (a few FP64 ops per pair).
-__global__ void __launch_bounds__(128) jacobi32_round_kernel(int64_t l, int64_t N, int64_t r,
+__global__ void __launch_bounds__(256) jacobi32_round_kernel(int64_t l, int64_t N, int64_t r,
                                                              float* __restrict__ B,
                                                              float* __restrict__ W, int64_t ld,
                                                              double tol, int* rotated) {
-  const int lane = threadIdx.x & 31;
-  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (k >= N / 2) return;
+  __shared__ float sh[3][8];
+  __shared__ float cs[2];
+  __shared__ int doit;
+  const int64_t k = blockIdx.x;
   int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
   if (p >= l || q >= l) return;
   if (p > q) { const int64_t t = p; p = q; q = t; }
   float* bp = B + p * ld;
   float* bq = B + q * ld;
   float a = 0.f, b = 0.f, g = 0.f;
-  for (int64_t i = lane; i < l; i += 32) {
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     const float x = bp[i], y = bq[i];
     a = fmaf(x, x, a);
     b = fmaf(y, y, b);
     g = fmaf(x, y, g);
   }
-  a = __shfl_sync(0xffffffffu, warp_sumf(a), 0);
-  b = __shfl_sync(0xffffffffu, warp_sumf(b), 0);
-  g = __shfl_sync(0xffffffffu, warp_sumf(g), 0);
-  const double A_ = a, B_ = b, G_ = g;
-  if (!(A_ > 0.0 && B_ > 0.0 && fabs(G_) > tol * sqrt(A_) * sqrt(B_))) return;
-  const double zeta = (B_ - A_) / (2.0 * G_);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cd = 1.0 / sqrt(1.0 + t * t);
-  const float c = (float)cd, s = (float)(cd * t);
-  if (lane == 0) atomicAdd(rotated, 1);
+  a = warp_sumf(a);
+  b = warp_sumf(b);
+  g = warp_sumf(g);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = g; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A_ = 0, B_ = 0, G_ = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { A_ += sh[0][w]; B_ += sh[1][w]; G_ += sh[2][w]; }
+    doit = 0;
+    if (A_ > 0.0 && B_ > 0.0 && fabs(G_) > tol * sqrt(A_) * sqrt(B_)) {
+      const double zeta = (B_ - A_) / (2.0 * G_);
+      const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      const double c = 1.0 / sqrt(1.0 + t * t);
+      cs[0] = (float)c;
+      cs[1] = (float)(c * t);
+      doit = 1;
+      atomicAdd(rotated, 1);
+    }
+  }
+  __syncthreads();
+  if (!doit) return;
+  const float c = cs[0], s = cs[1];
   float* wp = W + p * ld;
   float* wq = W + q * ld;
-  for (int64_t i = lane; i < l; i += 32) {
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     const float x = bp[i], y = bq[i];
     bp[i] = c * x - s * y;
     bq[i] = s * x + c * y;
@@ -549,44 +585,12 @@ __global__ void __launch_bounds__(128) jacobi32_round_kernel(int64_t l, int64_t 
   }
 }
 
-// FP64 stage: one warp per pair, no rotation accumulation.
-__global__ void __launch_bounds__(128) jacobi64_round_kernel(int64_t l, int64_t N, int64_t r,
-                                                             double* __restrict__ B, int64_t ldb,
-                                                             double tol, int* rotated) {
-  const int lane = threadIdx.x & 31;
-  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (k >= N / 2) return;
-  int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
-  if (p >= l || q >= l) return;
-  if (p > q) { const int64_t t = p; p = q; q = t; }
-  double* bp = B + p * ldb;
-  double* bq = B + q * ldb;
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int64_t i = lane; i < l; i += 32) {
-    const double x = bp[i], y = bq[i];
-    a = fma(x, x, a);
-    b = fma(y, y, b);
-    g = fma(x, y, g);
-  }
-  a = __shfl_sync(0xffffffffu, warp_sum(a), 0);
-  b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
-  g = __shfl_sync(0xffffffffu, warp_sum(g), 0);
-  if (!(a > 0.0 && b > 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b))) return;
-  const double zeta = (b - a) / (2.0 * g);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t);
-  const double s = c * t;
-  if (lane == 0) atomicAdd(rotated, 1);
-  for (int64_t i = lane; i < l; i += 32) {
-    const double x = bp[i], y = bq[i];
-    bp[i] = c * x - s * y;
-    bq[i] = s * x + c * y;
-  }
-}
-
-__global__ void d2f_kernel(int64_t n, const double* s, float* d) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = (float)s[i];
+// d(:, c) = (float) s(:, c) for the l x l matrix s (leading dimension lds), d packed
+__global__ void d2f_kernel(int64_t l, const double* s, int64_t lds, float* d) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l * l) return;
+  const int64_t r = e % l, c = e / l;
+  d[e] = (float)s[r + c * lds];
 }
 __global__ void f2d_kernel(int64_t n, const float* s, double* d) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -597,8 +601,8 @@ __global__ void eye32_kernel(int64_t n, float* W) {
   if (e < n * n) W[e] = (e % n == e / n) ? 1.f : 0.f;
 }
 
-thread_local DBuf<float> g_jb32, g_jw32;
-thread_local DBuf<double> g_jw64, g_jtmp;
+thread_local Scratch<float> g_jb32, g_jw32;
+thread_local Scratch<double> g_jw64, g_jtmp, g_jw2;
 
 // Run sweeps of `round` (a lambda launching round r) as one captured graph per sweep
 // until a sweep rotates nothing; returns the sweep count.
@@ -648,37 +652,48 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
                 double* sigma, int* flag_dev) {
   if (l <= 0) return 0;
   const int64_t N = (l % 2) ? l + 1 : l;
-  const unsigned blocks = (unsigned)cdiv(N / 2 * 32, 128);
   int sweeps = 0;
   if (l > 1) {
-    // Stage 1 (FP32 pipes): sweeps on an FP32 copy that accumulate the rotation W until
-    // the columns are orthogonal to FP32 accuracy; then B <- B W in FP64.
+    // Stage 1 (FP32): sweeps on an FP32 copy that accumulate the rotation W until the
+    // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.
     const int64_t l2 = l * l;
-    g_jb32.alloc(l2, st);
-    g_jw32.alloc(l2, st);
-    g_jw64.alloc(l2, st);
-    g_jtmp.alloc(l2, st);
+    g_jb32.ensure(l2);
+    g_jw32.ensure(l2);
+    g_jw64.ensure(l2);
+    g_jtmp.ensure(l2);
+    g_jw2.ensure(l2);
     float* B32 = g_jb32.p;
     float* W32 = g_jw32.p;
-    for (int64_t c = 0; c < l; ++c)
-      d2f_kernel<<<(unsigned)cdiv(l, 256), 256, 0, st>>>(l, B + c * ldb, B32 + c * l);
+    d2f_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, B, ldb, B32);
     APL_LAUNCH_CHECK();
     eye32_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32);
     APL_LAUNCH_CHECK();
     const double tol32 = std::max(1e-6, (double)l * 6e-8);
     sweeps += run_sweeps(st, N, 40, flag_dev, [&](int64_t r) {
-      jacobi32_round_kernel<<<blocks, 128, 0, st>>>(l, N, r, B32, W32, l, tol32, flag_dev);
+      jacobi32_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, B32, W32, l, tol32,
+                                                               flag_dev);
       APL_LAUNCH_CHECK();
     }, -1, 0.0, 0.0);
     f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, g_jw64.p);
     APL_LAUNCH_CHECK();
-    dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, g_jw64.p, l, 0.0, g_jtmp.p, l);
+    // W is orthogonal only to FP32 accuracy; two Newton-Schulz steps
+    // W <- W (3 I - W^T W) / 2 make it orthogonal to FP64 accuracy, so B W keeps the
+    // singular values of B exactly (to rounding)
+    double* Wd = g_jw64.p;
+    double* G = g_jtmp.p;
+    for (int it = 0; it < 2; ++it) {
+      dgemm(st, 1, 0, l, l, l, -0.5, Wd, l, Wd, l, 0.0, G, l);
+      dadd_diag(st, l, 1.5, G, l);
+      dgemm(st, 0, 0, l, l, l, 1.0, Wd, l, G, l, 0.0, g_jw2.p, l);
+      dcopy2d(st, l, l, g_jw2.p, l, Wd, l, false);
+    }
+    dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, g_jtmp.p, l);
     dcopy2d(st, l, l, g_jtmp.p, l, B, ldb, false);
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
     const double pairs = (double)(l * (l - 1)) / 2.0;
     sweeps += run_sweeps(st, N, 60, flag_dev, [&](int64_t r) {
-      jacobi64_round_kernel<<<blocks, 128, 0, st>>>(l, N, r, B, ldb, tol, flag_dev);
+      jacobi_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, B, ldb, tol, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l);
   }
@@ -720,6 +735,10 @@ __global__ void set2d_kernel(int64_t rows, int64_t cols, double v, double* dst, 
   if (e >= rows * cols) return;
   dst[e % rows + (e / rows) * ldd] = v;
 }
+__global__ void set_diag_kernel(int64_t n, double v, double* A, int64_t lda) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + i * lda] = v;
+}
 __global__ void zero_lower_kernel(int64_t n, double* A, int64_t lda) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
@@ -745,6 +764,20 @@ void dcopy2d(cudaStream_t st, int64_t rows, int64_t cols, const double* src, int
 void dset2d(cudaStream_t st, int64_t rows, int64_t cols, double v, double* dst, int64_t ldd) {
   if (rows <= 0 || cols <= 0) return;
   set2d_kernel<<<(unsigned)cdiv(rows * cols, 256), 256, 0, st>>>(rows, cols, v, dst, ldd);
+  APL_LAUNCH_CHECK();
+}
+__global__ void add_diag_kernel(int64_t n, double v, double* A, int64_t lda) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + i * lda] += v;
+}
+void dadd_diag(cudaStream_t st, int64_t n, double v, double* A, int64_t lda) {
+  if (n <= 0) return;
+  add_diag_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, v, A, lda);
+  APL_LAUNCH_CHECK();
+}
+void dset_diag(cudaStream_t st, int64_t n, double v, double* A, int64_t lda) {
+  if (n <= 0) return;
+  set_diag_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, v, A, lda);
   APL_LAUNCH_CHECK();
 }
 void dzero_lower(cudaStream_t st, int64_t n, double* A, int64_t lda) {

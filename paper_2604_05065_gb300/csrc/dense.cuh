@@ -36,6 +36,8 @@ void dcopy2d(cudaStream_t st, int64_t rows, int64_t cols, const double* src, int
              double* dst, int64_t ldd, bool transpose);
 void dset2d(cudaStream_t st, int64_t rows, int64_t cols, double v, double* dst, int64_t ldd);
 void dzero_lower(cudaStream_t st, int64_t n, double* A, int64_t lda);
+void dset_diag(cudaStream_t st, int64_t n, double v, double* A, int64_t lda);
+void dadd_diag(cudaStream_t st, int64_t n, double v, double* A, int64_t lda);
 void dgather_cols(cudaStream_t st, int64_t rows, const double* src, int64_t lds,
                   const int* idx, int64_t k, double* dst, int64_t ldd);
 

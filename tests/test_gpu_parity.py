@@ -302,3 +302,29 @@ def test_deterministic_bitwise_rerun():
     x1 = s.solve(1e-10).cpu().numpy()
     x2 = s.solve(1e-10).cpu().numpy()
     assert np.array_equal(x1, x2)
+
+
+def test_autograd_function_gradients():
+    """torch.autograd.Function wrapper: loss = 0.5 ||x(A, b, mu) - x_target||^2 on a
+    scaled-down gradient workload (FP32 A, singular values exp(-i/200)); gradients with
+    respect to A, b and mu against the oracle's closed forms at the direct solution."""
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+    p = wl.config5(scale=50)  # 2000 x 40
+    A64 = p.dense.astype(np.float64)
+    xt = p.extra["x_target"]
+    fn = pkg.aplicur_solve_fn()
+    for mu in (1e-6, 1e-3, 1e-1):
+        A = torch.from_numpy(p.dense).cuda().requires_grad_(True)
+        b = torch.from_numpy(p.b).cuda().requires_grad_(True)
+        m = torch.tensor(mu, dtype=torch.float64, device="cuda", requires_grad=True)
+        x = fn.apply(A, b, m, p.sketch_dim, 1e-12, 100000, {"precision": pkg.PREC_DF32})
+        loss = 0.5 * ((x - torch.from_numpy(xt).cuda()) ** 2).sum()
+        loss.backward()
+        xd = O.ridge_direct(A64, p.b, mu)
+        _, gb, gmu, gA = O.ridge_gradients(A64, p.b, mu, xd, xd - xt)
+        assert rel(x.detach().cpu().numpy(), xd) <= 1e-8
+        assert rel(b.grad.cpu().numpy(), gb) <= 1e-7
+        assert float(m.grad) == pytest.approx(gmu, rel=1e-6)
+        assert rel(A.grad.double().cpu().numpy(), gA) <= 1e-6
