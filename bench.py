@@ -159,7 +159,8 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     opts = dict(precision=precision, profile=1, seed=1)
 
-    prof_tot = {"ms": [0.0] * 6, "launches": [0] * 6, "work": [0.0] * 6}
+    nfam = len(pkg.PROFILE_FAMILIES)
+    prof_tot = {"ms": [0.0] * nfam, "launches": [0] * nfam, "work": [0.0] * nfam}
     sched = {}
 
     def one_solve(Adev, bdev, record=False):
@@ -168,7 +169,7 @@ def gpu_arm(args, rank, world, local_rank):
         st = s.stats()
         if record:
             pr = s.profile()
-            for k in range(6):
+            for k in range(nfam):
                 prof_tot["ms"][k] += pr["ms"][k]
                 prof_tot["launches"][k] += pr["launches"][k]
                 prof_tot["work"][k] += pr["work"][k]
@@ -297,36 +298,41 @@ def spmv_measure(args, dev):
 
 
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64: 152 SMs x 2.07 GHz x 4 FLOP/clk/SM
+FP32_PEAK_TFLOPS = 80.5  # GB300 nominal FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz
 NAMES = ["A z pass (k1_dense)", "A^T u pass (k2a_dense + k2b_dense)",
          "preconditioner passes (pre_qt, pre_vt, pre_v, pre_expand)", "FP64 GEMM (dgemm_kernel)",
-         "Jacobi sweeps (jacobi_round_kernel)", "LUPP selection (lupp_step_kernel)"]
+         "FP64 Jacobi sweeps (jacobi_round_kernel)", "LUPP selection (lupp_step_kernel)",
+         "FP32 Jacobi sweeps (jacobi32_block_kernel)"]
+ALU = {3: (FP64_PEAK_TFLOPS, "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)"),
+       4: (FP64_PEAK_TFLOPS, "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)"),
+       6: (FP32_PEAK_TFLOPS, "nominal GB300 FP32 (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)")}
 
 
 def roofline(prof):
-    k = max(range(6), key=lambda q: prof["ms"][q])
+    nf = len(prof["ms"])
+    k = max(range(nf), key=lambda q: prof["ms"][q])
     if not prof["launches"][k]:
         return None
     peak_bw, src = peaks()
     fams = {}
-    for q in range(6):
+    for q in range(nf):
         if not prof["launches"][q]:
             continue
-        rate = prof["work"][q] / max(prof["ms"][q], 1e-12) * 1e-3  # per second / 1e12... see unit
-        if q in (3, 4):
+        rate = prof["work"][q] / max(prof["ms"][q], 1e-12) * 1e3  # work per second
+        if q in ALU:
             fams[NAMES[q]] = {"ms_total": round(prof["ms"][q], 2), "timed": prof["launches"][q],
-                              "TFLOPs": round(rate * 1e-6, 4),
-                              "frac": round(rate * 1e-6 / FP64_PEAK_TFLOPS, 4)}
+                              "TFLOPs": round(rate * 1e-12, 4),
+                              "frac": round(rate * 1e-12 / ALU[q][0], 4)}
         else:
             fams[NAMES[q]] = {"ms_total": round(prof["ms"][q], 2), "timed": prof["launches"][q],
-                              "GBps": round(rate * 1e-3, 1), "frac": round(rate * 1e-3 / peak_bw, 4)}
+                              "GBps": round(rate * 1e-9, 1), "frac": round(rate * 1e-9 / peak_bw, 4)}
     avg_ms = prof["ms"][k] / prof["launches"][k]
     per = prof["work"][k] / prof["launches"][k]
-    if k in (3, 4):
+    if k in ALU:
         achieved = per / (avg_ms * 1e-3) / 1e12
-        out = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
-               "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-               "traffic": traffic_for(k, per),
-               "peak_source": "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk)",
+        out = {"bound": "alu", "achieved": round(achieved, 4), "peak": ALU[k][0],
+               "unit": "TFLOP/s", "frac": round(achieved / ALU[k][0], 4),
+               "traffic": traffic_for(k, per), "peak_source": ALU[k][1],
                "flops_per_launch": int(per)}
     else:
         achieved = per / (avg_ms * 1e-3) / 1e9

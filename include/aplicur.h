@@ -117,12 +117,14 @@ typedef struct {
  *  0 the A z pass, 1 the A^T u pass, 2 the preconditioner passes (LSQR hot loop;
  *    timed by events inside the captured iteration graphs);
  *  3 FP64 GEMMs (including those inside triangular solves and Cholesky),
- *  4 Jacobi sweeps of the preconditioner SVD, 5 LUPP index selection.
- * work[k] is algorithmic bytes for families 0, 1, 2, 5 and FP64 flops for 3, 4. */
+ *  4 FP64 Jacobi sweeps of the preconditioner SVD, 5 LUPP index selection,
+ *  6 FP32 Jacobi sweeps (the first stage of the SVD).
+ * work[k] is algorithmic bytes for families 0, 1, 2, 5, FP64 flops for 3, 4 and FP32
+ * flops for 6. */
 typedef struct {
-  double ms[6];              /* summed event-to-event device time */
-  int64_t launches[6];       /* timed regions (kernel launches, sweeps, selections) */
-  double work[6];            /* summed algorithmic bytes or flops */
+  double ms[7];              /* summed event-to-event device time */
+  int64_t launches[7];       /* timed regions (kernel launches, sweeps, selections) */
+  double work[7];            /* summed algorithmic bytes or flops */
   int64_t kernel_launches;   /* all kernels this process launched through the library */
 } aplicur_profile;
 

@@ -5,4 +5,5 @@ The solver lives in the CUDA library libaplicur.so (C ABI in include/aplicur.h);
 `aplicur` is its Python binding and `workloads` holds seeded synthetic inputs.
 """
 from .aplicur import (AplicurError, Solver, aplicur_solve_fn, default_options, load,  # noqa
-                      solve, launch_count, PREC_FP64, PREC_MIXED, PREC_DF32)
+                      solve, launch_count, PREC_FP64, PREC_MIXED, PREC_DF32,
+                      PROFILE_FAMILIES)

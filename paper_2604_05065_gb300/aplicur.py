@@ -43,14 +43,15 @@ class Options(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("work", C.c_double * 6),
+    _fields_ = [("ms", C.c_double * 7), ("launches", C.c_int64 * 7), ("work", C.c_double * 7),
                 ("kernel_launches", C.c_int64)]
 
 
 # kernel families of aplicur_profile: (name, unit of work)
 PROFILE_FAMILIES = [("A z pass", "bytes"), ("A^T u pass", "bytes"),
                     ("preconditioner passes", "bytes"), ("FP64 GEMM", "flops"),
-                    ("Jacobi sweeps", "flops"), ("LUPP selection", "bytes")]
+                    ("FP64 Jacobi sweeps", "flops"), ("LUPP selection", "bytes"),
+                    ("FP32 Jacobi sweeps", "flops32")]
 
 
 class Stats(C.Structure):

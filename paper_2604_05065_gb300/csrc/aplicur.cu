@@ -967,6 +967,9 @@ aplicur_status aplicur_matvec(aplicur_handle h, int32_t trans, const double* x, 
   });
 }
 
+static_assert(sizeof(aplicur_profile::ms) / sizeof(double) == PROF_NCAT,
+              "aplicur_profile must hold one entry per kernel family");
+
 aplicur_status aplicur_get_profile(aplicur_handle h, aplicur_profile* out) {
   if (!h || !out) return APLICUR_EINVAL;
   for (int k = 0; k < 3; ++k) {

@@ -42,8 +42,9 @@ struct CaptureScope {
 
 // Device-time accounting by kernel family, active while a solve with profiling runs on
 // this thread.  Categories: 0 A z pass, 1 A^T u pass, 2 preconditioner passes (bytes);
-// 3 FP64 GEMM, 4 Jacobi sweeps (FP64 flops); 5 LUPP selection (bytes).
-enum { PROF_NCAT = 6, PROF_GEMM = 3, PROF_JACOBI = 4, PROF_LUPP = 5 };
+// 3 FP64 GEMM, 4 FP64 Jacobi sweeps (FP64 flops); 5 LUPP selection (bytes);
+// 6 FP32 Jacobi sweeps (FP32 flops).
+enum { PROF_NCAT = 7, PROF_GEMM = 3, PROF_JACOBI = 4, PROF_LUPP = 5, PROF_JACOBI32 = 6 };
 struct ProfSink {
   cudaStream_t st = nullptr;
   std::vector<cudaEvent_t> pool;

@@ -528,64 +528,130 @@ __global__ void gather_normalise_kernel(int64_t rows, const double* src, int64_t
 }  // namespace
 
 namespace {
-// FP32 stage: one block per pair; rotates the FP32 copy of B and accumulates the rotations
-// in W.  The angle is computed in FP64 from the FP32 sums (a few FP64 ops per pair).
-__global__ void __launch_bounds__(256) jacobi32_round_kernel(int64_t l, int64_t N, int64_t r,
-                                                             float* __restrict__ B,
-                                                             float* __restrict__ W, int64_t ld,
-                                                             double tol, int* rotated) {
-  __shared__ float sh[3][8];
-  __shared__ float cs[2];
-  __shared__ int doit;
-  const int64_t k = blockIdx.x;
-  int64_t p = rr_elem(k, r, N), q = rr_elem(N - 1 - k, r, N);
-  if (p >= l || q >= l) return;
-  if (p > q) { const int64_t t = p; p = q; q = t; }
-  float* bp = B + p * ld;
-  float* bq = B + q * ld;
+// FP32 stage, block-cyclic: the l columns form NB (even) blocks of JW columns; in block
+// round r the blocks form NB/2 disjoint pairs (round robin) and one CTA takes one pair.
+// The CTA holds its 2 JW columns in shared memory and rotates every (P-column, Q-column)
+// pair in JW inner rounds of JW disjoint pairs (one warp per pair); in block round 0 it
+// first rotates the pairs inside P and inside Q.  Over the NB - 1 block rounds of a sweep
+// every pair of columns meets once, as in a scalar cyclic sweep.  The rotations are
+// accumulated in a 2JW x 2JW matrix R and applied to the matching columns of W at the
+// end (W <- W R).  Angles are computed in FP32: this stage only has to bring the columns
+// close to orthogonal; the FP64 stage decides the accuracy.
+constexpr int JW = 8;
+constexpr int JW2 = 2 * JW;
+
+__device__ __forceinline__ void jac32_pair(float* __restrict__ cp, float* __restrict__ cq,
+                                           float* __restrict__ R, int p, int q, int64_t l,
+                                           float tol, int lane, int& rot) {
   float a = 0.f, b = 0.f, g = 0.f;
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const float x = bp[i], y = bq[i];
+  for (int64_t i = lane; i < l; i += 32) {
+    const float x = cp[i], y = cq[i];
     a = fmaf(x, x, a);
     b = fmaf(y, y, b);
     g = fmaf(x, y, g);
   }
-  a = warp_sumf(a);
-  b = warp_sumf(b);
-  g = warp_sumf(g);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = g; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+  }
+  if (!(a > 0.f && b > 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b))) return;
+  const float zeta = (b - a) / (2.f * g);
+  const float az = fabsf(zeta);
+  // tan of the rotation angle, the smaller root; 1 / (2 zeta) once zeta^2 would overflow
+  float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
+  t = zeta >= 0.f ? t : -t;
+  const float c = rsqrtf(1.f + t * t), sn = c * t;
+  for (int64_t i = lane; i < l; i += 32) {
+    const float x = cp[i], y = cq[i];
+    cp[i] = c * x - sn * y;
+    cq[i] = sn * x + c * y;
+  }
+  if (lane < JW2) {
+    const float u = R[lane * JW2 + p], v = R[lane * JW2 + q];
+    R[lane * JW2 + p] = c * u - sn * v;
+    R[lane * JW2 + q] = sn * u + c * v;
+  }
+  ++rot;
+}
+
+// grid NB/2, block 32 * JW threads, dynamic shared memory JW2 * l floats + R
+__global__ void __launch_bounds__(32 * JW) jacobi32_block_kernel(int64_t l, int64_t NB,
+                                                                 int64_t r, float* __restrict__ B,
+                                                                 float* __restrict__ W,
+                                                                 float tol, int* rotated) {
+  extern __shared__ float jsm[];
+  float* cols = jsm;                  // JW2 columns of length l
+  float* R = jsm + (size_t)JW2 * l;   // JW2 x JW2, row-major R[row * JW2 + col]
+  __shared__ int gcol[JW2];
+  __shared__ int cta_rot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = blockIdx.x;
+  const int64_t bp = rr_elem(k, r, NB), bq = rr_elem(NB - 1 - k, r, NB);
+  if (threadIdx.x < JW2) {
+    const int64_t blk = threadIdx.x < JW ? bp : bq;
+    const int64_t c = blk * JW + (threadIdx.x % JW);
+    gcol[threadIdx.x] = c < l ? (int)c : -1;
+  }
+  if (threadIdx.x == 0) cta_rot = 0;
+  for (int e = threadIdx.x; e < JW2 * JW2; e += blockDim.x)
+    R[e] = (e / JW2 == e % JW2) ? 1.f : 0.f;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double A_ = 0, B_ = 0, G_ = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { A_ += sh[0][w]; B_ += sh[1][w]; G_ += sh[2][w]; }
-    doit = 0;
-    if (A_ > 0.0 && B_ > 0.0 && fabs(G_) > tol * sqrt(A_) * sqrt(B_)) {
-      const double zeta = (B_ - A_) / (2.0 * G_);
-      const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      const double c = 1.0 / sqrt(1.0 + t * t);
-      cs[0] = (float)c;
-      cs[1] = (float)(c * t);
-      doit = 1;
-      atomicAdd(rotated, 1);
-    }
+  // one row index per thread and pass, all JW2 column loads in flight together
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
+    float v[JW2];
+#pragma unroll
+    for (int c = 0; c < JW2; ++c) v[c] = gcol[c] >= 0 ? B[(int64_t)gcol[c] * l + i] : 0.f;
+#pragma unroll
+    for (int c = 0; c < JW2; ++c) cols[(size_t)c * l + i] = v[c];
   }
   __syncthreads();
-  if (!doit) return;
-  const float c = cs[0], s = cs[1];
-  float* wp = W + p * ld;
-  float* wq = W + q * ld;
+  int rot = 0;
+  if (r == 0) {
+    // pairs inside each block: JW - 1 round-robin rounds of JW/2 pairs per block
+    for (int ir = 0; ir < JW - 1; ++ir) {
+      const int t = warp % (JW / 2), side = warp / (JW / 2);
+      int p = (int)rr_elem(t, ir, JW), q = (int)rr_elem(JW - 1 - t, ir, JW);
+      if (p > q) { const int z = p; p = q; q = z; }
+      p += side * JW;
+      q += side * JW;
+      if (gcol[p] >= 0 && gcol[q] >= 0)
+        jac32_pair(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q, l, tol, lane, rot);
+      __syncthreads();
+    }
+  }
+  for (int ir = 0; ir < JW; ++ir) {
+    const int p = warp, q = JW + (warp + ir) % JW;
+    if (gcol[p] >= 0 && gcol[q] >= 0)
+      jac32_pair(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q, l, tol, lane, rot);
+    __syncthreads();
+  }
+  if (lane == 0 && rot) atomicAdd(&cta_rot, rot);
+  __syncthreads();
+  if (cta_rot == 0) return;
+  if (threadIdx.x == 0) atomicAdd(rotated, cta_rot);
+  // write back the columns and W(:, cols) <- W(:, cols) R, one row per thread and pass
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    const float x = bp[i], y = bq[i];
-    bp[i] = c * x - s * y;
-    bq[i] = s * x + c * y;
-    const float u = wp[i], v = wq[i];
-    wp[i] = c * u - s * v;
-    wq[i] = s * u + c * v;
+#pragma unroll
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * l + i];
+    float w[JW2], o[JW2];
+#pragma unroll
+    for (int c = 0; c < JW2; ++c) {
+      w[c] = gcol[c] >= 0 ? W[(int64_t)gcol[c] * l + i] : 0.f;
+      o[c] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < JW2; ++c)
+#pragma unroll
+      for (int j = 0; j < JW2; ++j) o[j] = fmaf(w[c], R[c * JW2 + j], o[j]);
+#pragma unroll
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0) W[(int64_t)gcol[c] * l + i] = o[c];
   }
 }
 
-// d(:, c) = (float) s(:, c) for the l x l matrix s (leading dimension lds), d packed
 __global__ void d2f_kernel(int64_t l, const double* s, int64_t lds, float* d) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * l) return;
@@ -653,9 +719,11 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
   if (l <= 0) return 0;
   const int64_t N = (l % 2) ? l + 1 : l;
   int sweeps = 0;
-  if (l > 1) {
+  const size_t smem = ((size_t)JW2 * l + JW2 * JW2) * sizeof(float);
+  if (l > 1 && smem <= 227 * 1024) {
     // Stage 1 (FP32): sweeps on an FP32 copy that accumulate the rotation W until the
-    // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.
+    // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.  Skipped when the
+    // CTA's two column blocks do not fit in shared memory (l above about 3600).
     const int64_t l2 = l * l;
     g_jb32.ensure(l2);
     g_jw32.ensure(l2);
@@ -668,27 +736,37 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     APL_LAUNCH_CHECK();
     eye32_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32);
     APL_LAUNCH_CHECK();
-    const double tol32 = std::max(1e-6, (double)l * 6e-8);
-    sweeps += run_sweeps(st, N, 40, flag_dev, [&](int64_t r) {
-      jacobi32_round_kernel<<<(unsigned)(N / 2), 256, 0, st>>>(l, N, r, B32, W32, l, tol32,
-                                                               flag_dev);
+    // FP32 dot products summed lane-wise then by a 5-level tree: the relative error of
+    // g / sqrt(a b) stays below (l/32 + 5) u32; the threshold sits above twice that
+    const double tol32 = std::max(6e-6, 2.0 * ((double)l / 32.0 + 5.0) * 5.960464477539063e-8);
+    const int64_t nb = cdiv(l, (int64_t)JW);
+    const int64_t NB = nb + (nb % 2);
+    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double flops32 = 12.0 * (double)l * (double)l * (double)(l - 1) / 2.0;
+    sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
+      jacobi32_block_kernel<<<(unsigned)(NB / 2), 32 * JW, smem, st>>>(l, NB, r, B32, W32,
+                                                                      (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
-    }, -1, 0.0, 0.0);
+    }, PROF_JACOBI32, flops32, 0.0);
     f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, g_jw64.p);
     APL_LAUNCH_CHECK();
     // W is orthogonal only to FP32 accuracy; two Newton-Schulz steps
     // W <- W (3 I - W^T W) / 2 make it orthogonal to FP64 accuracy, so B W keeps the
     // singular values of B exactly (to rounding)
     double* Wd = g_jw64.p;
+    double* Wn = g_jw2.p;
     double* G = g_jtmp.p;
     for (int it = 0; it < 2; ++it) {
       dgemm(st, 1, 0, l, l, l, -0.5, Wd, l, Wd, l, 0.0, G, l);
       dadd_diag(st, l, 1.5, G, l);
-      dgemm(st, 0, 0, l, l, l, 1.0, Wd, l, G, l, 0.0, g_jw2.p, l);
-      dcopy2d(st, l, l, g_jw2.p, l, Wd, l, false);
+      dgemm(st, 0, 0, l, l, l, 1.0, Wd, l, G, l, 0.0, Wn, l);
+      std::swap(Wd, Wn);
     }
-    dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, g_jtmp.p, l);
-    dcopy2d(st, l, l, g_jtmp.p, l, B, ldb, false);
+    dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, G, l);
+    dcopy2d(st, l, l, G, l, B, ldb, false);
+  }
+  if (l > 1) {
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
     const double pairs = (double)(l * (l - 1)) / 2.0;
