@@ -261,6 +261,82 @@ int64_t aplicur_launch_count(void);
 aplicur_status aplicur_dense_atx_noalloc(const aplicur_matrix* A, const double* x, double* y,
                                          void* stream);
 
+/* ---- Batched solves ------------------------------------------------------------------
+ * nprob independent problems  min ||A_p x - b_{p,r}||^2 + mu ||x||^2,  r < nrhs, with
+ * FP32 matrices of uneven sizes.  APLICUR (Algorithm "APLICUR: detailed implementation")
+ * runs per problem: each problem gets its own sparse sign sketch (seed opt.seed + p), CUR
+ * rank steps and preconditioner builds, and its right-hand sides share them; each pair
+ * (p, r) runs its own LSQR recurrences (warm-started phases, Paige-Saunders and dynamic
+ * stopping tests of Section 5.3.2) and leaves the solve when its own normal-equation
+ * residual reaches tol, so a pair's result is that of a single-right-hand-side solve of
+ * (A_p, b_{p,r}).  The rank steps and builds of different problems run concurrently on
+ * their own streams; the LSQR iterations of all pairs run as grouped kernels (one launch
+ * per step of the iteration covers every problem, products with A are SpMM / tall-skinny
+ * GEMM over the nrhs block), captured in CUDA graphs.  Products use FP32 values and FP32
+ * sums; every phase starts from the normal-equation residual g = A^T (b - A x) - mu x
+ * formed with compensated FP32 products (about 2^-44 relative) and solves for the
+ * correction with right-hand side [0; g / sqrt(mu)], whose normal equations are those of
+ * the paper's warm start; the stopping tests use the paper's residual estimate.  Dense
+ * tile shapes are picked by timing candidates at creation. */
+typedef struct aplicur_batch_ctx* aplicur_batch_handle;
+
+typedef struct {
+  int32_t pairs;              /* nprob * nrhs */
+  int32_t converged;          /* pairs with normal-equation residual <= tol */
+  int64_t iters_max;          /* largest LSQR iteration count of a pair */
+  int64_t iters_sum;          /* LSQR iterations of all pairs */
+  double ne_max;              /* largest relative normal-equation residual */
+  double time_setup_ms;       /* creation: sketches, ||A^T b||, tuning (host clock) */
+  double time_rank_ms, time_build_ms, time_lsqr_ms, time_check_ms;  /* last solve */
+  int32_t rows_per_warp;      /* tuned dense A-pass tile */
+  int32_t cols_per_lane;      /* tuned dense A^T-pass tile */
+  int64_t launches_per_iter;  /* kernel launches of one grouped LSQR iteration */
+} aplicur_batch_stats;
+
+/* Create a batch.
+ *  A      host array of nprob matrices: format dense row-major (any ld >= n) or CSR, dtype
+ *         F32, values on the device, m_p >= n_p >= sketch_dim; borrowed until destroy.
+ *  b      host array of nprob device pointers, each m_p x nrhs FP64 column-major; borrowed.
+ *  nrhs   1..16.   mu > 0 (the refinement solves for corrections through the damping rows).
+ *  opt    as for aplicur_create (precision, replay and profile are ignored).
+ *  stream the stream of the grouped LSQR kernels (NULL: a private stream).
+ * Requires n_p * (nrhs rounded up to 4 or 16) * 4 bytes <= 200 KiB (n_p <= 3200 at 16
+ * right-hand sides).  Errors: EINVAL, ENOMEM, ECUDA; message via aplicur_batch_last_error. */
+aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
+                                    const aplicur_matrix* A, const double* const* b,
+                                    int32_t nrhs, double mu, int32_t sketch_dim,
+                                    const aplicur_options* opt, void* stream);
+
+/* Solve every pair to the relative normal-equation residual tol (as aplicur_solve), at
+ * most maxit LSQR iterations per pair.  After the rank steps, phases without the dynamic
+ * test continue until tol, the budget, 4 * max_extra_phases phases, or a phase that gains
+ * less than 10%.  x_out: host array of nprob device pointers, each
+ * n_p x nrhs FP64 column-major (overwritten).  ENOTCONV when a pair missed tol (x still
+ * written); EBREAKDOWN when a preconditioner build of some problem broke down. */
+aplicur_status aplicur_batch_solve(aplicur_batch_handle h, double tol, int64_t maxit,
+                                   double* const* x_out);
+
+/* The same batch by unpreconditioned LSQR with the same grouped kernels (P = I). */
+aplicur_status aplicur_batch_plain_lsqr(aplicur_batch_handle h, double tol, int64_t maxit,
+                                        double* const* x_out);
+
+/* Result of pair (p, r) of the last solve; any output may be NULL. */
+aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t r,
+                                      int64_t* iters, double* ne_res, int32_t* converged);
+
+/* CUR state of problem p after the last solve: rank, rank steps, phases, and the row
+ * and column indices in selection order (I, J: host, >= ell entries, or NULL). */
+aplicur_status aplicur_batch_get_problem(aplicur_batch_handle h, int32_t p, int32_t* ell,
+                                         int32_t* nsteps, int32_t* nphases, int32_t* I,
+                                         int32_t* J);
+
+aplicur_status aplicur_batch_get_stats(aplicur_batch_handle h, aplicur_batch_stats* st);
+
+/* Message of the last failed call on h (never NULL); NULL: last failed create. */
+const char* aplicur_batch_last_error(aplicur_batch_handle h);
+
+void aplicur_batch_destroy(aplicur_batch_handle h);
+
 /* Message of the last failed call on h (never NULL); with h = NULL, the last
  * failed aplicur_create or aplicur_dense_atx_noalloc of this thread. */
 const char* aplicur_last_error(aplicur_handle h);

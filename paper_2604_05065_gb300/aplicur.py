@@ -62,6 +62,15 @@ class Stats(C.Structure):
                 ("time_build_ms", C.c_double), ("time_lsqr_ms", C.c_double)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("pairs", C.c_int32), ("converged", C.c_int32), ("iters_max", C.c_int64),
+                ("iters_sum", C.c_int64), ("ne_max", C.c_double), ("time_setup_ms", C.c_double),
+                ("time_rank_ms", C.c_double), ("time_build_ms", C.c_double),
+                ("time_lsqr_ms", C.c_double), ("time_check_ms", C.c_double),
+                ("rows_per_warp", C.c_int32), ("cols_per_lane", C.c_int32),
+                ("launches_per_iter", C.c_int64)]
+
+
 # every entry point of include/aplicur.h: name -> (restype, argtypes)
 _VP, _D, _I32, _I64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
 _PI32 = C.POINTER(C.c_int32)
@@ -85,6 +94,15 @@ SIGNATURES = {
     "aplicur_reset_profile": (C.c_int, [_VP]),
     "aplicur_launch_count": (C.c_int64, []),
     "aplicur_dense_atx_noalloc": (C.c_int, [C.POINTER(Matrix), _VP, _VP, _VP]),
+    "aplicur_batch_create": (C.c_int, [C.POINTER(_VP), _I32, C.POINTER(Matrix), _VP, _I32, _D,
+                                       _I32, C.POINTER(Options), _VP]),
+    "aplicur_batch_solve": (C.c_int, [_VP, _D, _I64, _VP]),
+    "aplicur_batch_plain_lsqr": (C.c_int, [_VP, _D, _I64, _VP]),
+    "aplicur_batch_get_pair": (C.c_int, [_VP, _I32, _I32, C.POINTER(_I64), C.POINTER(_D), _PI32]),
+    "aplicur_batch_get_problem": (C.c_int, [_VP, _I32, _PI32, _PI32, _PI32, _VP, _VP]),
+    "aplicur_batch_get_stats": (C.c_int, [_VP, C.POINTER(BatchStats)]),
+    "aplicur_batch_last_error": (C.c_char_p, [_VP]),
+    "aplicur_batch_destroy": (None, [_VP]),
     "aplicur_last_error": (C.c_char_p, [_VP]),
     "aplicur_status_string": (C.c_char_p, [C.c_int]),
     "aplicur_destroy": (None, [_VP]),
@@ -136,6 +154,41 @@ def _torch():
     return torch
 
 
+def _marshal_matrix(torch, A):
+    """aplicur_matrix for a dense CUDA tensor (row-major rows, any row stride) or a
+    torch.sparse_csr_tensor; returns (struct, tensors to keep alive, value dtype)."""
+    mat = Matrix()
+    if A.layout == torch.sparse_csr:
+        rowptr = A.crow_indices().to(torch.int32).contiguous()
+        colidx = A.col_indices().to(torch.int32).contiguous()
+        vals = A.values().contiguous()
+        keep = [rowptr, colidx, vals]
+        mat.format = 1
+        mat.nnz = vals.numel()
+        mat.values = vals.data_ptr()
+        mat.rowptr = rowptr.data_ptr()
+        mat.colidx = colidx.data_ptr()
+        mat.ld = A.shape[1]
+        dt = vals.dtype
+    else:
+        if A.stride(1) != 1:
+            A = A.contiguous()
+        keep = [A]
+        mat.format = 0
+        mat.ld = A.stride(0)
+        mat.nnz = A.shape[0] * A.shape[1]
+        mat.values = A.data_ptr()
+        dt = A.dtype
+    if dt == torch.float64:
+        mat.dtype = 0
+    elif dt == torch.float32:
+        mat.dtype = 1
+    else:
+        raise TypeError("A must be float64 or float32")
+    mat.m, mat.n = int(A.shape[0]), int(A.shape[1])
+    return mat, keep, dt
+
+
 class Solver:
     """One APLICUR problem min ||A x - b||^2 + mu ||x||^2 on the GPU.
 
@@ -149,35 +202,7 @@ class Solver:
         lib = load()
         self._lib = lib
         self._h = None
-        mat = Matrix()
-        if A.layout == torch.sparse_csr:
-            rowptr = A.crow_indices().to(torch.int32).contiguous()
-            colidx = A.col_indices().to(torch.int32).contiguous()
-            vals = A.values().contiguous()
-            self._keep = [rowptr, colidx, vals]
-            mat.format = 1
-            mat.nnz = vals.numel()
-            mat.values = vals.data_ptr()
-            mat.rowptr = rowptr.data_ptr()
-            mat.colidx = colidx.data_ptr()
-            mat.ld = A.shape[1]
-            dt = vals.dtype
-        else:
-            if A.stride(1) != 1:
-                A = A.contiguous()
-            self._keep = [A]
-            mat.format = 0
-            mat.ld = A.stride(0)
-            mat.nnz = A.shape[0] * A.shape[1]
-            mat.values = A.data_ptr()
-            dt = A.dtype
-        if dt == torch.float64:
-            mat.dtype = 0
-        elif dt == torch.float32:
-            mat.dtype = 1
-        else:
-            raise TypeError("A must be float64 or float32")
-        mat.m, mat.n = int(A.shape[0]), int(A.shape[1])
+        mat, self._keep, dt = _marshal_matrix(torch, A)
         self.m, self.n = mat.m, mat.n
         self.dtype = dt
         self.device = b.device
@@ -424,3 +449,107 @@ def aplicur_solve_fn():
     """The torch.autograd.Function class (created lazily so that importing this module
     does not import torch)."""
     return _autograd_function()
+
+
+class BatchSolver:
+    """A batch of independent problems min ||A_p x - b_{p,r}||^2 + mu ||x||^2 solved by
+    the library's grouped multi-right-hand-side APLICUR (aplicur_batch_* entry points).
+
+    mats: list of FP32 CUDA matrices (dense, any row stride, or sparse CSR);
+    rhs: list of CUDA tensors of shape (m_p, R) or (m_p,) (converted to float64).
+    Problem p is seeded with options.seed + p."""
+
+    def __init__(self, mats, rhs, mu: float, sketch_dim: int, **opts):
+        torch = _torch()
+        lib = load()
+        self._lib = lib
+        self._h = None
+        if len(mats) != len(rhs) or not mats:
+            raise ValueError("need one right-hand-side block per matrix")
+        self._keep = []
+        arr = (Matrix * len(mats))()
+        self.shapes = []
+        R = None
+        bptr = (C.c_void_p * len(mats))()
+        for p, (A, b) in enumerate(zip(mats, rhs)):
+            mat, keep, _ = _marshal_matrix(torch, A)
+            self._keep += keep
+            arr[p] = mat
+            b2 = b.reshape(b.shape[0], -1).to(torch.float64)
+            if R is None:
+                R = b2.shape[1]
+            if b2.shape[1] != R or b2.shape[0] != mat.m:
+                raise ValueError("right-hand sides must be (m_p, R) with one R")
+            bt = b2.t().contiguous()  # column-major m x R
+            self._keep.append(bt)
+            bptr[p] = bt.data_ptr()
+            self.shapes.append((mat.m, mat.n))
+        self.R = R
+        self.device = rhs[0].device
+        o = default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        h = C.c_void_p()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = lib.aplicur_batch_create(C.byref(h), len(mats), arr, bptr, R, float(mu),
+                                      int(sketch_dim), C.byref(o), C.c_void_p(stream))
+        if st != 0:
+            raise AplicurError(st, lib.aplicur_batch_last_error(None).decode())
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.aplicur_batch_destroy(self._h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def _run(self, fn, tol, maxit):
+        torch = _torch()
+        xs = [torch.empty(self.R, n, dtype=torch.float64, device=self.device)
+              for (_, n) in self.shapes]
+        ptr = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        st = fn(self._h, float(tol), int(maxit), ptr)
+        if st != 0 and st != 4:
+            raise AplicurError(st, self._lib.aplicur_batch_last_error(self._h).decode())
+        self.last_status = st
+        return [x.t() for x in xs]
+
+    def solve(self, tol: float = 1e-8, maxit: int = 100000):
+        """List of (n_p, R) float64 solutions."""
+        return self._run(self._lib.aplicur_batch_solve, tol, maxit)
+
+    def plain_lsqr(self, tol: float = 1e-8, maxit: int = 100000):
+        return self._run(self._lib.aplicur_batch_plain_lsqr, tol, maxit)
+
+    def pair(self, p: int, r: int) -> dict:
+        it, ne, cv = C.c_int64(), C.c_double(), C.c_int32()
+        _check_b(self._lib, self._lib.aplicur_batch_get_pair(self._h, p, r, C.byref(it),
+                                                               C.byref(ne), C.byref(cv)), self._h)
+        return {"iters": it.value, "ne_res": ne.value, "converged": bool(cv.value)}
+
+    def problem(self, p: int) -> dict:
+        import numpy as np
+        ell, ns, nph = C.c_int32(), C.c_int32(), C.c_int32()
+        _check_b(self._lib, self._lib.aplicur_batch_get_problem(self._h, p, C.byref(ell), C.byref(ns),
+                                                                  C.byref(nph), None, None), self._h)
+        I = np.zeros(max(ell.value, 1), np.int32)
+        J = np.zeros(max(ell.value, 1), np.int32)
+        _check_b(self._lib, self._lib.aplicur_batch_get_problem(
+            self._h, p, None, None, None, I.ctypes.data, J.ctypes.data), self._h)
+        return {"ell": ell.value, "nsteps": ns.value, "nphases": nph.value,
+                "I": I[:ell.value].astype(np.int64), "J": J[:ell.value].astype(np.int64)}
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        _check_b(self._lib, self._lib.aplicur_batch_get_stats(self._h, C.byref(s)), self._h)
+        return {k: getattr(s, k) for k, _ in BatchStats._fields_}
+
+
+def _check_b(lib, st, h):
+    if st != 0:
+        raise AplicurError(st, lib.aplicur_batch_last_error(h).decode())
+    return st

@@ -2,13 +2,18 @@
 // The host keeps the state machine (rank steps, rebuild decisions, phases); every
 // operation with an m- or n-sized extent runs in the library's kernels.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <exception>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/aplicur.h"
+#include "batch.cuh"
 #include "dense.cuh"
 #include "lsqr.cuh"
 
@@ -144,6 +149,7 @@ struct aplicur_ctx {
   std::string err;
   float setup_ms = 0;
   ProfSink sink;
+  DenseWork dw;  // scratch of the dense routines, used on st only
 };
 
 namespace {
@@ -294,6 +300,7 @@ void reset_cur(aplicur_ctx* h) {
 // One rank step (Part 1 and Part 2 of the driver).  Returns the number of new indices;
 // *exhausted is set when LUPP met a zero pivot before the block was complete.
 int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) {
+  DenseWorkScope dws(&h->dw);
   cudaStream_t st = h->st;
   const int64_t m = h->m, n = h->n;
   const int s = h->s;
@@ -431,6 +438,7 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
 // CURPreconditioner Part 2: M = T_C U T_R^T, SVD of M, coefficients.  Vhat = Q_R V_M is
 // kept implicit (applied as two matrix-vector products per use).
 void build_preconditioner(aplicur_ctx* h) {
+  DenseWorkScope dws(&h->dw);
   cudaStream_t st = h->st;
   const int L = h->ell, cap = h->cap;
   h->Mb.alloc((size_t)L * L, st);
@@ -579,6 +587,103 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
   return finish(ne);
 }
 
+// Validation, sketch draws, the one-time sketch Y = S A and buffers of one problem; with
+// with_lsqr also the single-right-hand-side LSQR engine and ||A^T b||.  Throws Error.
+void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double mu,
+              int32_t sketch_dim, const aplicur_options* opt, void* stream, bool with_lsqr) {
+  APL_REQUIRE(A->format == APLICUR_DENSE_ROWMAJOR || A->format == APLICUR_CSR, "bad format");
+  APL_REQUIRE(A->dtype == APLICUR_F64 || A->dtype == APLICUR_F32, "bad dtype");
+  APL_REQUIRE(A->m >= 1 && A->n >= 1 && A->m >= A->n, "need m >= n >= 1");
+  APL_REQUIRE(A->m < (1LL << 31) && A->n < (1LL << 31), "dimensions exceed int32 indexing");
+  APL_REQUIRE(A->values != nullptr, "A values NULL");
+  APL_REQUIRE(mu >= 0.0 && std::isfinite(mu), "mu must be finite and >= 0");
+  APL_REQUIRE(sketch_dim >= 1 && sketch_dim <= A->n, "need 1 <= sketch_dim <= n");
+  if (A->format == APLICUR_DENSE_ROWMAJOR) APL_REQUIRE(A->ld >= A->n, "ld < n");
+  else APL_REQUIRE(A->rowptr && A->colidx && A->nnz >= 0 && A->nnz < (1LL << 31), "bad CSR");
+  if (opt) h->opt = *opt; else aplicur_options_default(&h->opt);
+  if (h->opt.replay_phases && h->opt.replay_nphases > 0)
+    h->rp_phases.assign(h->opt.replay_phases, h->opt.replay_phases + h->opt.replay_nphases);
+  else h->opt.replay_nphases = 0;
+  if (h->opt.replay_rebuild && h->opt.replay_nsteps > 0)
+    h->rp_rebuild.assign(h->opt.replay_rebuild, h->opt.replay_rebuild + h->opt.replay_nsteps);
+  else h->opt.replay_nsteps = 0;
+  APL_REQUIRE(h->opt.xi >= 1 && h->opt.normest_r >= 1 && h->opt.check_gap >= 1, "bad options");
+  APL_REQUIRE(h->opt.graph_iters >= 0 && h->opt.graph_iters <= 4096, "bad graph_iters");
+  APL_REQUIRE(h->opt.precision >= APLICUR_PREC_FP64 && h->opt.precision <= APLICUR_PREC_DF32,
+              "bad precision");
+  if (stream) h->st = (cudaStream_t)stream;
+  else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
+  cudaStream_t st = h->st;
+  h->m = A->m; h->n = A->n; h->kmax = std::min(h->m, h->n);
+  APL_REQUIRE(h->opt.max_rank >= 0, "max_rank must be >= 0");
+  if (h->opt.max_rank > 0) h->kmax = std::min<int64_t>(h->kmax, h->opt.max_rank);
+  h->A.fmt = A->format; h->A.dtype = A->dtype; h->A.m = A->m; h->A.n = A->n; h->A.ld = A->ld;
+  h->A.nnz = A->format == APLICUR_CSR ? A->nnz : A->m * A->n;
+  h->A.vals = A->values; h->A.rowptr = A->rowptr; h->A.colidx = A->colidx;
+  h->b = b;
+  h->mu = mu;
+  h->delta = std::sqrt(mu);
+  h->eps_cur = h->opt.eps_cur_factor * h->delta;
+  h->bsize = sketch_dim;
+  h->s = (11 * sketch_dim + 9) / 10;
+  h->xi = std::min(h->opt.xi, h->s);
+  h->r = h->opt.normest_r;
+  if (h->A.fmt == 1) build_csc(h);
+  // sketch and norm-estimate draws
+  std::vector<int> rows;
+  std::vector<int8_t> sg;
+  if (h->opt.sketch_rows && h->opt.sketch_signs) {
+    rows.assign(h->opt.sketch_rows, h->opt.sketch_rows + h->m * h->xi);
+    sg.assign(h->opt.sketch_signs, h->opt.sketch_signs + h->m * h->xi);
+  } else {
+    draw_sketch(h->opt.seed, h->s, h->m, h->xi, rows, sg);
+  }
+  upload_sketch(h, rows, sg);
+  std::vector<double> W;
+  if (h->opt.normest_w) W.assign(h->opt.normest_w, h->opt.normest_w + h->n * h->r);
+  else draw_gaussian(h->opt.seed, h->n, h->r, W);
+  h->W.alloc(W.size(), st);
+  APL_CUDA(cudaMemcpyAsync(h->W.p, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  h->opt.sketch_rows = nullptr; h->opt.sketch_signs = nullptr; h->opt.normest_w = nullptr;
+  h->opt.replay_phases = nullptr; h->opt.replay_rebuild = nullptr;
+  // buffers
+  const int64_t m = h->m, n = h->n;
+  h->Y.alloc((size_t)h->s * n, st);
+  h->E.alloc((size_t)h->s * n, st);
+  h->Et.alloc((size_t)h->s * n, st);
+  h->T.alloc((size_t)h->s * h->r, st);
+  h->scal.alloc(4, st);
+  h->info.alloc(4, st);
+  h->I_d.alloc(h->kmax, st); h->J_d.alloc(h->kmax, st);
+  h->Jp_d.alloc(h->bsize, st); h->Ip_d.alloc(h->bsize, st);
+  h->colpos.alloc(n, st); h->colpos_plus.alloc(n, st); h->rowpos.alloc(m, st);
+  h->Ecol.alloc((size_t)m * h->bsize, st);
+  if (h->A.fmt == 1) h->Cp.alloc((size_t)m * h->bsize, st);
+  if (with_lsqr) {
+    h->x.alloc(n, st); h->tmp_m.alloc(m, st); h->tmp_n.alloc(n, st); h->tmp_n2.alloc(n, st);
+    h->lam.alloc(n, st);
+  }
+  // the one-time sketch Y = S A
+  cudaEvent_t e0, e1;
+  APL_CUDA(cudaEventCreate(&e0));
+  APL_CUDA(cudaEventCreate(&e1));
+  APL_CUDA(cudaEventRecord(e0, st));
+  sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
+         1.0 / std::sqrt((double)h->xi), h->Y.p);
+  APL_CUDA(cudaEventRecord(e1, st));
+  APL_CUDA(cudaEventSynchronize(e1));
+  APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->stats.time_setup_ms = h->setup_ms;
+  if (!with_lsqr) return;
+  h->eng.setup(st, h->A, h->opt.precision, h->opt.graph_iters);
+  h->eng.set_profile(h->opt.profile != 0);
+  // ||A^T b|| in FP64
+  h->eng.matvec(1, b, h->tmp_n.p, 1.0, 0.0, true);
+  h->norm_Atb = h->eng.norm2(h->tmp_n.p, n);
+}
+
 aplicur_status fail(aplicur_ctx* h, const Error& e) {
   if (h) h->err = e.what();
   return (aplicur_status)e.code;
@@ -640,94 +745,7 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
   aplicur_ctx* h = new (std::nothrow) aplicur_ctx();
   if (!h) return APLICUR_ENOMEM;
   aplicur_status stt = guarded(h, [&]() -> int {
-    APL_REQUIRE(A->format == APLICUR_DENSE_ROWMAJOR || A->format == APLICUR_CSR, "bad format");
-    APL_REQUIRE(A->dtype == APLICUR_F64 || A->dtype == APLICUR_F32, "bad dtype");
-    APL_REQUIRE(A->m >= 1 && A->n >= 1 && A->m >= A->n, "need m >= n >= 1");
-    APL_REQUIRE(A->m < (1LL << 31) && A->n < (1LL << 31), "dimensions exceed int32 indexing");
-    APL_REQUIRE(A->values != nullptr, "A values NULL");
-    APL_REQUIRE(mu >= 0.0 && std::isfinite(mu), "mu must be finite and >= 0");
-    APL_REQUIRE(sketch_dim >= 1 && sketch_dim <= A->n, "need 1 <= sketch_dim <= n");
-    if (A->format == APLICUR_DENSE_ROWMAJOR) APL_REQUIRE(A->ld >= A->n, "ld < n");
-    else APL_REQUIRE(A->rowptr && A->colidx && A->nnz >= 0 && A->nnz < (1LL << 31), "bad CSR");
-    if (opt) h->opt = *opt; else aplicur_options_default(&h->opt);
-    if (h->opt.replay_phases && h->opt.replay_nphases > 0)
-      h->rp_phases.assign(h->opt.replay_phases, h->opt.replay_phases + h->opt.replay_nphases);
-    else h->opt.replay_nphases = 0;
-    if (h->opt.replay_rebuild && h->opt.replay_nsteps > 0)
-      h->rp_rebuild.assign(h->opt.replay_rebuild, h->opt.replay_rebuild + h->opt.replay_nsteps);
-    else h->opt.replay_nsteps = 0;
-    APL_REQUIRE(h->opt.xi >= 1 && h->opt.normest_r >= 1 && h->opt.check_gap >= 1, "bad options");
-    APL_REQUIRE(h->opt.graph_iters >= 0 && h->opt.graph_iters <= 4096, "bad graph_iters");
-    APL_REQUIRE(h->opt.precision >= APLICUR_PREC_FP64 && h->opt.precision <= APLICUR_PREC_DF32,
-                "bad precision");
-    if (stream) h->st = (cudaStream_t)stream;
-    else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
-    cudaStream_t st = h->st;
-    h->m = A->m; h->n = A->n; h->kmax = std::min(h->m, h->n);
-    APL_REQUIRE(h->opt.max_rank >= 0, "max_rank must be >= 0");
-    if (h->opt.max_rank > 0) h->kmax = std::min<int64_t>(h->kmax, h->opt.max_rank);
-    h->A.fmt = A->format; h->A.dtype = A->dtype; h->A.m = A->m; h->A.n = A->n; h->A.ld = A->ld;
-    h->A.nnz = A->format == APLICUR_CSR ? A->nnz : A->m * A->n;
-    h->A.vals = A->values; h->A.rowptr = A->rowptr; h->A.colidx = A->colidx;
-    h->b = b;
-    h->mu = mu;
-    h->delta = std::sqrt(mu);
-    h->eps_cur = h->opt.eps_cur_factor * h->delta;
-    h->bsize = sketch_dim;
-    h->s = (11 * sketch_dim + 9) / 10;
-    h->xi = std::min(h->opt.xi, h->s);
-    h->r = h->opt.normest_r;
-    if (h->A.fmt == 1) build_csc(h);
-    // sketch and norm-estimate draws
-    std::vector<int> rows;
-    std::vector<int8_t> sg;
-    if (h->opt.sketch_rows && h->opt.sketch_signs) {
-      rows.assign(h->opt.sketch_rows, h->opt.sketch_rows + h->m * h->xi);
-      sg.assign(h->opt.sketch_signs, h->opt.sketch_signs + h->m * h->xi);
-    } else {
-      draw_sketch(h->opt.seed, h->s, h->m, h->xi, rows, sg);
-    }
-    upload_sketch(h, rows, sg);
-    std::vector<double> W;
-    if (h->opt.normest_w) W.assign(h->opt.normest_w, h->opt.normest_w + h->n * h->r);
-    else draw_gaussian(h->opt.seed, h->n, h->r, W);
-    h->W.alloc(W.size(), st);
-    APL_CUDA(cudaMemcpyAsync(h->W.p, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    h->opt.sketch_rows = nullptr; h->opt.sketch_signs = nullptr; h->opt.normest_w = nullptr;
-    h->opt.replay_phases = nullptr; h->opt.replay_rebuild = nullptr;
-    // buffers
-    const int64_t m = h->m, n = h->n;
-    h->Y.alloc((size_t)h->s * n, st);
-    h->E.alloc((size_t)h->s * n, st);
-    h->Et.alloc((size_t)h->s * n, st);
-    h->T.alloc((size_t)h->s * h->r, st);
-    h->scal.alloc(4, st);
-    h->info.alloc(4, st);
-    h->I_d.alloc(h->kmax, st); h->J_d.alloc(h->kmax, st);
-    h->Jp_d.alloc(h->bsize, st); h->Ip_d.alloc(h->bsize, st);
-    h->colpos.alloc(n, st); h->colpos_plus.alloc(n, st); h->rowpos.alloc(m, st);
-    h->Ecol.alloc((size_t)m * h->bsize, st);
-    if (h->A.fmt == 1) h->Cp.alloc((size_t)m * h->bsize, st);
-    h->x.alloc(n, st); h->tmp_m.alloc(m, st); h->tmp_n.alloc(n, st); h->tmp_n2.alloc(n, st);
-    h->lam.alloc(n, st);
-    // the one-time sketch Y = S A
-    cudaEvent_t e0, e1;
-    APL_CUDA(cudaEventCreate(&e0));
-    APL_CUDA(cudaEventCreate(&e1));
-    APL_CUDA(cudaEventRecord(e0, st));
-    sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
-           1.0 / std::sqrt((double)h->xi), h->Y.p);
-    APL_CUDA(cudaEventRecord(e1, st));
-    APL_CUDA(cudaEventSynchronize(e1));
-    APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    h->eng.setup(st, h->A, h->opt.precision, h->opt.graph_iters);
-    h->eng.set_profile(h->opt.profile != 0);
-    // ||A^T b|| in FP64
-    h->eng.matvec(1, b, h->tmp_n.p, 1.0, 0.0, true);
-    h->norm_Atb = h->eng.norm2(h->tmp_n.p, n);
-    h->stats.time_setup_ms = h->setup_ms;
+    ctx_init(h, A, b, mu, sketch_dim, opt, stream, true);
     return ST_OK;
   });
   if (stt != APLICUR_OK) {
@@ -1031,6 +1049,372 @@ void aplicur_destroy(aplicur_handle h) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+}
+
+}  // extern "C"
+
+// ======================================================================================
+// Batched solves: per-problem CUR state machines (the driver of do_solve, in lock step
+// over the problems) around one grouped multi-right-hand-side LSQR engine.
+// ======================================================================================
+
+struct aplicur_batch_ctx {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int np = 0, R = 0;
+  double mu = 0;
+  std::vector<aplicur_ctx*> pc;
+  apl::BatchEngine eng;
+  std::vector<long long> iters;  // per pair p * R + r
+  std::vector<double> ne;
+  std::vector<char> conv;
+  aplicur_batch_stats stats{};
+  std::string err;
+  int nthreads = 1;
+  ~aplicur_batch_ctx() {
+    for (aplicur_ctx* c : pc) aplicur_destroy(c);
+  }
+};
+
+namespace {
+
+// Run f(i) for i < n on up to nthreads host threads (each bound to `device`); the first
+// exception is rethrown after all threads finished.
+template <typename F>
+void parallel_for(int n, int nthreads, int device, F&& f) {
+  std::atomic<int> next{0};
+  std::exception_ptr first;
+  std::mutex mtx;
+  auto work = [&]() {
+    cudaSetDevice(device);
+    while (true) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      try {
+        f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mtx);
+        if (!first) first = std::current_exception();
+      }
+    }
+  };
+  const int nt = std::max(1, std::min(nthreads, n));
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  if (first) std::rethrow_exception(first);
+}
+
+template <typename F>
+aplicur_status bguarded(aplicur_batch_ctx* h, F&& f) {
+  try {
+    return (aplicur_status)f();
+  } catch (const Error& e) {
+    h->err = e.what();
+    return (aplicur_status)e.code;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return APLICUR_ECUDA;
+  } catch (...) {
+    h->err = "unknown failure";
+    return APLICUR_ECUDA;
+  }
+}
+
+// Convergence bookkeeping shared by the preconditioned and plain batched solves.
+struct PairBook {
+  std::vector<char> stopped;   // no further phases (converged, stagnated, out of budget)
+  std::vector<double> prev;
+};
+
+void batch_phase(aplicur_batch_ctx* h, const std::vector<char>& mask, const std::vector<double>& nu,
+                 double tol, long long maxit, std::vector<long long>& it_out) {
+  const size_t npairs = (size_t)h->np * h->R;
+  std::vector<long long> budget(npairs, 0);
+  for (size_t e = 0; e < npairs; ++e) budget[e] = std::max(0LL, maxit - h->iters[e]);
+  std::vector<int> reasons;
+  h->eng.run_phase(mask, nu, h->pc.empty() ? 1e-10 : h->pc[0]->opt.eps_lsqr, tol, budget, it_out,
+                   reasons);
+  for (size_t e = 0; e < npairs; ++e) h->iters[e] += it_out[e];
+  std::vector<double> ne;
+  h->eng.ne_residual(mask, ne);
+  for (size_t e = 0; e < npairs; ++e) {
+    if (!mask[e]) continue;
+    h->ne[e] = ne[e];
+    h->conv[e] = ne[e] <= tol ? 1 : 0;
+  }
+}
+
+int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t0) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+  };
+  const int np = h->np, R = h->R;
+  const size_t npairs = (size_t)np * R;
+  h->iters.assign(npairs, 0);
+  h->ne.assign(npairs, INFINITY);
+  h->conv.assign(npairs, 0);
+  h->stats.time_rank_ms = h->stats.time_build_ms = h->stats.time_lsqr_ms = 0.0;
+  h->stats.time_check_ms = 0.0;
+  h->eng.zero_x();
+  for (int p = 0; p < np; ++p) {
+    h->eng.clear_precond(p);
+    for (int r = 0; r < R; ++r)
+      if (h->eng.norm_ref(p, r) == 0.0) { h->ne[(size_t)p * R + r] = 0.0; h->conv[(size_t)p * R + r] = 1; }
+  }
+  PairBook bk;
+  bk.stopped.assign(npairs, 0);
+  bk.prev.assign(npairs, INFINITY);
+  for (size_t e = 0; e < npairs; ++e) bk.stopped[e] = h->conv[e];
+  auto problem_done = [&](int p) {
+    for (int r = 0; r < R; ++r)
+      if (!bk.stopped[(size_t)p * R + r]) return false;
+    return true;
+  };
+  std::vector<long long> it;
+  const aplicur_options& o = h->pc[0]->opt;
+  if (!plain) {
+    std::vector<double> d_cur(np, INFINITY), rho(np, 0.0), margin(np, 0.0);
+    std::vector<char> last(np, 0), rank_done(np, 0), rebuild(np, 0);
+    std::vector<char> exhausted(np, 0);
+    parallel_for(np, h->nthreads, h->device, [&](int p) { reset_cur(h->pc[p]); });
+    while (true) {
+      std::vector<int> act;
+      for (int p = 0; p < np; ++p)
+        if (!rank_done[p] && !problem_done(p)) act.push_back(p);
+      if (act.empty()) break;
+      auto t0 = clk::now();
+      parallel_for((int)act.size(), h->nthreads, h->device, [&](int k) {
+        const int p = act[k];
+        aplicur_ctx* c = h->pc[p];
+        double rh = 0, mg = INFINITY;
+        bool ex = false;
+        rank_step(c, &rh, &ex, &mg);
+        const bool full = c->ell >= c->kmax;
+        const double rho_eff = ex ? 0.0 : rh;
+        last[p] = (rho_eff <= c->eps_cur || full || ex) ? 1 : 0;
+        const double gap = rho_eff - c->eps_cur;
+        rebuild[p] = (last[p] || (gap > 0.0 && d_cur[p] / gap >= c->opt.nu_prec)) ? 1 : 0;
+        rho[p] = rh;
+        exhausted[p] = ex ? 1 : 0;
+        c->steps.push_back(StepRec{c->ell, rh, rebuild[p], mg});
+      });
+      h->stats.time_rank_ms += ms_since(t0);
+      std::vector<int> reb;
+      for (int p : act)
+        if (rebuild[p] && h->pc[p]->ell > 0) reb.push_back(p);
+      t0 = clk::now();
+      parallel_for((int)reb.size(), h->nthreads, h->device,
+                   [&](int k) { build_preconditioner(h->pc[reb[k]]); });
+      for (int p : reb) h->eng.set_precond(p, h->pc[p]->P);
+      h->stats.time_build_ms += ms_since(t0);
+      std::vector<char> mask(npairs, 0);
+      std::vector<double> nu(np, INFINITY);
+      bool any = false;
+      for (int p : reb) {
+        nu[p] = last[p] ? INFINITY : h->pc[p]->opt.nu_lsqr;
+        for (int r = 0; r < R; ++r) {
+          const size_t e = (size_t)p * R + r;
+          if (!bk.stopped[e] && h->iters[e] < maxit) { mask[e] = 1; any = true; }
+        }
+      }
+      if (any) {
+        t0 = clk::now();
+        batch_phase(h, mask, nu, tol, maxit, it);
+        h->stats.time_lsqr_ms += ms_since(t0);
+        for (int p : reb) {
+          long long mx = 0;
+          for (int r = 0; r < R; ++r) mx = std::max(mx, it[(size_t)p * R + r]);
+          double nmax = 0;
+          for (int r = 0; r < R; ++r) nmax = std::max(nmax, h->ne[(size_t)p * R + r]);
+          h->pc[p]->phases.push_back(PhaseRec{h->pc[p]->ell, mx, 0, nmax});
+        }
+        for (size_t e = 0; e < npairs; ++e) {
+          if (!mask[e]) continue;
+          bk.prev[e] = h->ne[e];
+          if (h->conv[e] || h->iters[e] >= maxit) bk.stopped[e] = 1;
+        }
+      }
+      for (int p : reb) d_cur[p] = (exhausted[p] ? 0.0 : rho[p]) - h->pc[p]->eps_cur;
+      for (int p : act)
+        if (last[p]) rank_done[p] = 1;
+    }
+  }
+  // final phases without the dynamic test (the last phase of the driver continued, or
+  // the plain solve): until tol, the iteration budget, or a phase that halves the
+  // residual no more
+  // FP32 recurrences end each phase after a smaller true gain than the FP64 driver's
+  // (the estimate runs ahead of the residual), so the batch allows 4x the phases
+  for (int rep = 0; rep <= 4 * o.max_extra_phases; ++rep) {
+    std::vector<char> mask(npairs, 0);
+    bool any = false;
+    for (size_t e = 0; e < npairs; ++e)
+      if (!bk.stopped[e] && h->iters[e] < maxit) { mask[e] = 1; any = true; }
+    if (!any) break;
+    std::vector<double> nu(np, INFINITY);
+    auto t0 = clk::now();
+    batch_phase(h, mask, nu, tol, maxit, it);
+    h->stats.time_lsqr_ms += ms_since(t0);
+    for (size_t e = 0; e < npairs; ++e) {
+      if (!mask[e]) continue;
+      // a refinement phase that no longer gains 10% ends the pair's solve
+      const bool stag = !plain || rep > 0 ? (it[e] == 0 || h->ne[e] > 0.9 * bk.prev[e]) : false;
+      if (h->conv[e] || h->iters[e] >= maxit || stag) bk.stopped[e] = 1;
+      bk.prev[e] = h->ne[e];
+    }
+  }
+  int nconv = 0;
+  long long imax = 0, isum = 0;
+  double nmax = 0;
+  for (size_t e = 0; e < npairs; ++e) {
+    nconv += h->conv[e];
+    imax = std::max(imax, h->iters[e]);
+    isum += h->iters[e];
+    nmax = std::max(nmax, h->ne[e]);
+  }
+  h->stats.pairs = (int32_t)npairs;
+  h->stats.converged = nconv;
+  h->stats.iters_max = imax;
+  h->stats.iters_sum = isum;
+  h->stats.ne_max = nmax;
+  h->stats.rows_per_warp = h->eng.tuned_rw();
+  h->stats.cols_per_lane = h->eng.tuned_cw();
+  h->stats.launches_per_iter = h->eng.launches_per_iter();
+  return nconv == (int)npairs ? ST_OK : ST_ENOTCONV;
+}
+
+}  // namespace
+
+static thread_local std::string g_batch_err;
+
+extern "C" {
+
+aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
+                                    const aplicur_matrix* A, const double* const* b,
+                                    int32_t nrhs, double mu, int32_t sketch_dim,
+                                    const aplicur_options* opt, void* stream) {
+  if (!out || !A || !b || nprob < 1) { g_batch_err = "null argument or nprob < 1"; return APLICUR_EINVAL; }
+  *out = nullptr;
+  aplicur_batch_ctx* h = new (std::nothrow) aplicur_batch_ctx();
+  if (!h) return APLICUR_ENOMEM;
+  aplicur_status stt = bguarded(h, [&]() -> int {
+    auto t0 = std::chrono::steady_clock::now();
+    APL_REQUIRE(nrhs >= 1 && nrhs <= BATCH_MAX_RHS, "nrhs must be 1..16");
+    APL_REQUIRE(mu > 0.0 && std::isfinite(mu), "batched solves need mu > 0");
+    for (int p = 0; p < nprob; ++p) {
+      APL_REQUIRE(A[p].dtype == APLICUR_F32, "batched solves take FP32 matrices");
+      APL_REQUIRE(b[p] != nullptr, "b[p] NULL");
+    }
+    APL_CUDA(cudaGetDevice(&h->device));
+    if (stream) h->st = (cudaStream_t)stream;
+    else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
+    h->np = nprob;
+    h->R = nrhs;
+    h->mu = mu;
+    h->nthreads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    aplicur_options o;
+    if (opt) o = *opt; else aplicur_options_default(&o);
+    o.replay_nphases = 0; o.replay_phases = nullptr;
+    o.replay_nsteps = 0; o.replay_rebuild = nullptr;
+    o.sketch_rows = nullptr; o.sketch_signs = nullptr; o.normest_w = nullptr;
+    o.profile = 0;
+    h->pc.assign(nprob, nullptr);
+    for (int p = 0; p < nprob; ++p) {
+      h->pc[p] = new (std::nothrow) aplicur_ctx();
+      APL_REQUIRE(h->pc[p] != nullptr, "out of host memory");
+    }
+    parallel_for(nprob, h->nthreads, h->device, [&](int p) {
+      aplicur_options op = o;
+      op.seed = o.seed + (uint64_t)p;
+      ctx_init(h->pc[p], &A[p], nullptr, mu, sketch_dim, &op, nullptr, false);
+    });
+    std::vector<BatchSrc> src(nprob);
+    for (int p = 0; p < nprob; ++p) src[p] = BatchSrc{h->pc[p]->A, b[p]};
+    h->eng.setup(h->st, src, nrhs, mu);
+    h->eng.autotune();
+    h->stats.time_setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->stats.rows_per_warp = h->eng.tuned_rw();
+    h->stats.cols_per_lane = h->eng.tuned_cw();
+    return ST_OK;
+  });
+  if (stt != APLICUR_OK) {
+    g_batch_err = h->err;
+    aplicur_batch_destroy(h);
+    return stt;
+  }
+  *out = h;
+  return APLICUR_OK;
+}
+
+static aplicur_status batch_run(aplicur_batch_handle h, double tol, int64_t maxit,
+                                double* const* x_out, bool plain) {
+  if (!h || !x_out) return APLICUR_EINVAL;
+  return bguarded(h, [&]() -> int {
+    APL_REQUIRE(tol >= 0.0 && maxit >= 0, "need tol >= 0 and maxit >= 0");
+    for (int p = 0; p < h->np; ++p) APL_REQUIRE(x_out[p] != nullptr, "x_out[p] NULL");
+    const int st = batch_solve(h, tol, maxit, plain);
+    for (int p = 0; p < h->np; ++p) h->eng.get_x(p, x_out[p]);
+    APL_CUDA(cudaStreamSynchronize(h->st));
+    return st;
+  });
+}
+
+aplicur_status aplicur_batch_solve(aplicur_batch_handle h, double tol, int64_t maxit,
+                                   double* const* x_out) {
+  return batch_run(h, tol, maxit, x_out, false);
+}
+
+aplicur_status aplicur_batch_plain_lsqr(aplicur_batch_handle h, double tol, int64_t maxit,
+                                        double* const* x_out) {
+  return batch_run(h, tol, maxit, x_out, true);
+}
+
+aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t r,
+                                      int64_t* iters, double* ne_res, int32_t* converged) {
+  if (!h || p < 0 || p >= h->np || r < 0 || r >= h->R) return APLICUR_EINVAL;
+  if (h->iters.empty()) { h->err = "no solve yet"; return APLICUR_EINVAL; }
+  const size_t e = (size_t)p * h->R + r;
+  if (iters) *iters = h->iters[e];
+  if (ne_res) *ne_res = h->ne[e];
+  if (converged) *converged = h->conv[e];
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_batch_get_problem(aplicur_batch_handle h, int32_t p, int32_t* ell,
+                                         int32_t* nsteps, int32_t* nphases, int32_t* I,
+                                         int32_t* J) {
+  if (!h || p < 0 || p >= h->np) return APLICUR_EINVAL;
+  const aplicur_ctx* c = h->pc[p];
+  if (ell) *ell = c->ell;
+  if (nsteps) *nsteps = (int32_t)c->steps.size();
+  if (nphases) *nphases = (int32_t)c->phases.size();
+  if (I) std::copy(c->I.begin(), c->I.end(), I);
+  if (J) std::copy(c->J.begin(), c->J.end(), J);
+  return APLICUR_OK;
+}
+
+aplicur_status aplicur_batch_get_stats(aplicur_batch_handle h, aplicur_batch_stats* st) {
+  if (!h || !st) return APLICUR_EINVAL;
+  *st = h->stats;
+  return APLICUR_OK;
+}
+
+const char* aplicur_batch_last_error(aplicur_batch_handle h) {
+  if (!h) return g_batch_err.c_str();
+  return h->err.c_str();
+}
+
+void aplicur_batch_destroy(aplicur_batch_handle h) {
+  if (!h) return;
+  cudaStream_t st = h->st;
+  const bool own = h->own_stream;
+  if (st) cudaStreamSynchronize(st);
+  delete h;
+  if (own && st) cudaStreamDestroy(st);
 }
 
 }  // extern "C"

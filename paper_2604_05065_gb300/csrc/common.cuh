@@ -114,29 +114,20 @@ struct DBuf {
   }
 };
 
-// Per-thread workspace reused across contexts and streams (thread_local in the dense
-// routines).  It holds no stream: the stream a buffer was last used on may belong to a
-// context that has been destroyed since, so growth and release use the synchronous
-// cudaMalloc / cudaFree (rare: the size only grows).  Never grown inside stream capture.
-template <typename T>
-struct Scratch {
-  T* p = nullptr;
-  size_t n = 0;
-  Scratch() = default;
-  Scratch(const Scratch&) = delete;
-  Scratch& operator=(const Scratch&) = delete;
-  ~Scratch() {
-    if (p) cudaFree(p);
-  }
-  void ensure(size_t count) {
-    if (count <= n && p) return;
-    if (p) APL_CUDA(cudaFree(p));
-    p = nullptr;
-    n = 0;
-    if (count == 0) return;
-    APL_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
-    n = count;
-  }
+// Scratch buffers of the dense routines (split-K partial sums, Cholesky QR temporary,
+// Jacobi copies).  They belong to the calling context, whose stream carries every use,
+// so growing one is stream-ordered (cudaFreeAsync/cudaMallocAsync on that stream) and
+// contexts driven from different threads never share or free each other's buffers.
+// The context installs its workspace for the duration of a call with DenseWorkScope.
+struct DenseWork {
+  DBuf<double> splitk, qrtmp, jw64, jtmp, jw2;
+  DBuf<float> jb32, jw32;
+};
+DenseWork& dense_work();  // the workspace installed on the calling thread (throws if none)
+struct DenseWorkScope {
+  DenseWork* prev;
+  explicit DenseWorkScope(DenseWork* w);
+  ~DenseWorkScope();
 };
 
 // ---- device reductions (fixed order -> bitwise reproducible) -------------------------

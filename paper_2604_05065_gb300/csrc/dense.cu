@@ -23,8 +23,15 @@ CaptureScope::~CaptureScope() { --g_capture_depth; }
 
 namespace {
 thread_local ProfSink* g_sink = nullptr;
+thread_local DenseWork* g_work = nullptr;
 }
 ProfSink* prof_sink() { return g_capture_depth == 0 ? g_sink : nullptr; }
+DenseWork& dense_work() {
+  APL_REQUIRE(g_work != nullptr, "internal: dense routine called without a workspace");
+  return *g_work;
+}
+DenseWorkScope::DenseWorkScope(DenseWork* w) : prev(g_work) { g_work = w; }
+DenseWorkScope::~DenseWorkScope() { g_work = prev; }
 void prof_set_sink(ProfSink* s) { g_sink = s; }
 ProfSink::~ProfSink() {
   for (cudaEvent_t e : pool) cudaEventDestroy(e);
@@ -166,7 +173,6 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const dou
   *out = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *out;
 }
 
-thread_local Scratch<double> g_splitk_ws;
 }  // namespace
 
 void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
@@ -195,13 +201,13 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   if (splits > 1) {
     const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
     splits = cdiv(K, kchunk);
-    g_splitk_ws.ensure((size_t)splits * M * N);
+    dense_work().splitk.alloc((size_t)splits * M * N, st);
     grid.z = (unsigned)splits;
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc,
-                                       kchunk, g_splitk_ws.p);
+                                       kchunk, dense_work().splitk.p);
     APL_LAUNCH_CHECK();
     splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
-                                                                     g_splitk_ws.p, alpha, beta, C,
+                                                                     dense_work().splitk.p, alpha, beta, C,
                                                                      ldc);
   } else {
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
@@ -393,7 +399,6 @@ void dpotrf_upper(cudaStream_t st, int64_t n, double* A, int64_t lda, int* info_
 }
 
 namespace {
-thread_local Scratch<double> g_qr_tmp;
 
 // E <- E T^{-1} for upper triangular T (k x k): T^{-1} by a left triangular solve on the
 // identity (contiguous columns), then one GEMM; E's rows are never walked with a stride.
@@ -402,9 +407,10 @@ void right_upper_inverse_apply(cudaStream_t st, int64_t n, int64_t k, double* E,
   dset2d(st, k, k, 0.0, Tinv, k);
   dset_diag(st, k, 1.0, Tinv, k);
   dtrsm(st, true, 'U', false, false, k, k, T, ldt, Tinv, k);
-  g_qr_tmp.ensure((size_t)n * k);
-  dgemm(st, 0, 0, n, k, k, 1.0, E, lde, Tinv, k, 0.0, g_qr_tmp.p, n);
-  dcopy2d(st, n, k, g_qr_tmp.p, n, E, lde, false);
+  DBuf<double>& tmp = dense_work().qrtmp;
+  tmp.alloc((size_t)n * k, st);
+  dgemm(st, 0, 0, n, k, k, 1.0, E, lde, Tinv, k, 0.0, tmp.p, n);
+  dcopy2d(st, n, k, tmp.p, n, E, lde, false);
 }
 }  // namespace
 
@@ -539,6 +545,7 @@ namespace {
 // close to orthogonal; the FP64 stage decides the accuracy.
 constexpr int JW = 8;
 constexpr int JW2 = 2 * JW;
+constexpr int kJac32SmemCap = 220 * 1024;  // dynamic shared memory cap of the FP32 stage
 
 __device__ __forceinline__ void jac32_pair(float* __restrict__ cp, float* __restrict__ cq,
                                            float* __restrict__ R, int p, int q, int64_t l,
@@ -667,8 +674,6 @@ __global__ void eye32_kernel(int64_t n, float* W) {
   if (e < n * n) W[e] = (e % n == e / n) ? 1.f : 0.f;
 }
 
-thread_local Scratch<float> g_jb32, g_jw32;
-thread_local Scratch<double> g_jw64, g_jtmp, g_jw2;
 
 // Run sweeps of `round` (a lambda launching round r) as one captured graph per sweep
 // until a sweep rotates nothing; returns the sweep count.
@@ -720,18 +725,19 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
   const int64_t N = (l % 2) ? l + 1 : l;
   int sweeps = 0;
   const size_t smem = ((size_t)JW2 * l + JW2 * JW2) * sizeof(float);
-  if (l > 1 && smem <= 227 * 1024) {
+  if (l > 1 && smem <= (size_t)kJac32SmemCap) {
     // Stage 1 (FP32): sweeps on an FP32 copy that accumulate the rotation W until the
     // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.  Skipped when the
     // CTA's two column blocks do not fit in shared memory (l above about 3600).
     const int64_t l2 = l * l;
-    g_jb32.ensure(l2);
-    g_jw32.ensure(l2);
-    g_jw64.ensure(l2);
-    g_jtmp.ensure(l2);
-    g_jw2.ensure(l2);
-    float* B32 = g_jb32.p;
-    float* W32 = g_jw32.p;
+    DenseWork& wk = dense_work();
+    wk.jb32.alloc(l2, st);
+    wk.jw32.alloc(l2, st);
+    wk.jw64.alloc(l2, st);
+    wk.jtmp.alloc(l2, st);
+    wk.jw2.alloc(l2, st);
+    float* B32 = wk.jb32.p;
+    float* W32 = wk.jw32.p;
     d2f_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, B, ldb, B32);
     APL_LAUNCH_CHECK();
     eye32_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32);
@@ -741,22 +747,24 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     const double tol32 = std::max(6e-6, 2.0 * ((double)l / 32.0 + 5.0) * 5.960464477539063e-8);
     const int64_t nb = cdiv(l, (int64_t)JW);
     const int64_t NB = nb + (nb % 2);
+    // one value for every call: threads that build preconditioners concurrently must not
+    // lower the cap under each other's launches
     APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     const double flops32 = 12.0 * (double)l * (double)l * (double)(l - 1) / 2.0;
     sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
       jacobi32_block_kernel<<<(unsigned)(NB / 2), 32 * JW, smem, st>>>(l, NB, r, B32, W32,
                                                                       (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI32, flops32, 0.0);
-    f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, g_jw64.p);
+    f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, wk.jw64.p);
     APL_LAUNCH_CHECK();
     // W is orthogonal only to FP32 accuracy; two Newton-Schulz steps
     // W <- W (3 I - W^T W) / 2 make it orthogonal to FP64 accuracy, so B W keeps the
     // singular values of B exactly (to rounding)
-    double* Wd = g_jw64.p;
-    double* Wn = g_jw2.p;
-    double* G = g_jtmp.p;
+    double* Wd = wk.jw64.p;
+    double* Wn = wk.jw2.p;
+    double* G = wk.jtmp.p;
     for (int it = 0; it < 2; ++it) {
       dgemm(st, 1, 0, l, l, l, -0.5, Wd, l, Wd, l, 0.0, G, l);
       dadd_diag(st, l, 1.5, G, l);

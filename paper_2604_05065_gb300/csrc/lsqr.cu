@@ -22,32 +22,13 @@
 
 #include "../../include/aplicur.h"
 #include "lsqr.cuh"
+#include "df32.cuh"
 
 namespace apl {
 
 namespace {
 
 constexpr int NT = 256;
-
-// ---- compensated FP32 accumulation ----------------------------------------------------
-
-struct DF {
-  float s, c;
-};
-
-// s + c += a * (h + l): exact product a*h = p + e by FMA, TwoSum of s and p.  Explicit
-// round-to-nearest intrinsics keep the compiler from contracting the error terms.
-__device__ __forceinline__ void df_fma(DF& acc, float a, float h, float l) {
-  const float p = __fmul_rn(a, h);
-  const float e = __fmaf_rn(a, h, -p);
-  const float t = __fadd_rn(acc.s, p);
-  const float bv = __fsub_rn(t, acc.s);
-  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-  acc.s = t;
-  acc.c = __fmaf_rn(a, l, __fadd_rn(acc.c, __fadd_rn(err, e)));
-}
-
-__device__ __forceinline__ double df_val(const DF& a) { return (double)a.s + (double)a.c; }
 
 __device__ __forceinline__ void split(double v, float* hi, float* lo, int64_t i) {
   const float h = __double2float_rn(v);

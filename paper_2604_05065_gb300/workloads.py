@@ -200,3 +200,37 @@ def small_sparse(m, n, seed, nnz_per_col=3, mu=1e-4, sketch_dim=4, dtype=np.floa
 def by_name(name: str, scale: int = 1) -> Problem:
     return {"config1": config1, "config2": config2, "config3": config3,
             "config5": config5}[name](scale)
+
+
+def batched(nprob=512, m_range=(2000, 50000), n_range=(100, 2000), density=1e-3, nrhs=16,
+            mu=1e-5, sketch_dim=50, decay_orders=6.0, index=4, seed=None) -> list:
+    """Batch of independent problems of uneven sizes: m ~ U[m_range], n ~ U[n_range]
+    (m >= n); the first half dense, A = U diag(s) V^T with U, V from QR of Gaussians and
+    s_i = 10^(-decay_orders i/(n-1)); the second half CSR with each entry nonzero with
+    probability `density` and N(0,1) values; FP32 storage; nrhs right-hand sides ~ N(0,1)
+    per problem (b has shape m x nrhs).  Host numpy generation (tests and small batches)."""
+    rng = _rng(index) if seed is None else np.random.Generator(np.random.PCG64(seed))
+    out = []
+    half = nprob // 2
+    for p in range(nprob):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        m = int(rng.integers(max(m_range[0], n), m_range[1] + 1))
+        b = rng.standard_normal((m, nrhs))
+        if p < half:
+            U = _orth(rng, m, n)
+            V = _orth(rng, n, n)
+            sv = 10.0 ** (-decay_orders * np.arange(n) / max(n - 1, 1))
+            A = np.ascontiguousarray(((U * sv) @ V.T).astype(np.float32))
+            out.append(Problem(f"batch_dense_{p}_{m}x{n}", m, n, "dense", np.dtype(np.float32), mu,
+                               sketch_dim, b, dense=A, extra={"sigma": sv}))
+        else:
+            mask = rng.random((m, n)) < density
+            rows, cols = np.nonzero(mask)
+            vals = rng.standard_normal(rows.size).astype(np.float32)
+            indptr = np.zeros(m + 1, np.int64)
+            np.add.at(indptr, rows + 1, 1)
+            indptr = np.cumsum(indptr)
+            out.append(Problem(f"batch_csr_{p}_{m}x{n}", m, n, "csr", np.dtype(np.float32), mu,
+                               sketch_dim, b, indptr=indptr, indices=cols.astype(np.int64),
+                               data=vals))
+    return out
