@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--maxit", type=int, default=200000)
     ap.add_argument("--no-spmv", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-nprob", type=int, default=64,
+                    help="problems of the batched workload (512 is the full configuration; a "
+                         "full solve takes minutes, so the default line carries 64)")
     return ap.parse_args()
 
 
@@ -252,7 +256,9 @@ def gpu_arm(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel family of the step (largest device time)
     roof = roofline(prof_tot)
     spmv = None if args.no_spmv else spmv_measure(args, dev)
+    batched = None if (args.no_batched or world > 1) else batched_measure(args, dev)
     return dict(value=value, ms=ms_max / args.steps, p=p, prec=prec, clocks=clk, e2e=e2e,
+                batched=batched,
                 plain=plain, roof=roof, launches=launches, sched=sched, ne=st["ne_res"],
                 spmv=spmv)
 
@@ -308,6 +314,65 @@ ALU = {3: (FP64_PEAK_TFLOPS, "nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 FLOP/cl
        6: (FP32_PEAK_TFLOPS, "nominal GB300 FP32 (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)")}
 
 
+def batched_measure(args, dev):
+    """The batched workload (uneven dense and CSR FP32 problems, 16 right-hand sides each,
+    mu 1e-5, sketch dimension 50): one warm-up and one timed APLICUR batch solve to the
+    time-to-tol target, then the same batch by plain LSQR with the same grouped kernels.
+    Throughput counts solved (problem, right-hand side) pairs per second."""
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+    from paper_2604_05065_gb300 import workloads as wl
+
+    nprob, R = args.batched_nprob, 16
+    t0 = time.perf_counter()
+    mats, rhs, sizes = wl.batched_device(dev, nprob=nprob, nrhs=R)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    abytes = sum(4 * m * n for (m, n, f) in sizes if f == "dense")
+    abytes += sum(8 * a.values().numel() for a, (m, n, f) in zip(mats, sizes) if f == "csr")
+    t0 = time.perf_counter()
+    s = pkg.BatchSolver(mats, rhs, 1e-5, 50, seed=1)
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"batched_{nprob}x{R}", "problems": nprob, "nrhs": R,
+           "note": ("the full 512-problem configuration" if nprob == 512 else
+                    f"{nprob} problems drawn by the 512-problem recipe (--batched-nprob 512 "
+                    "runs the full configuration)"),
+           "pairs": nprob * R, "a_bytes": int(abytes), "generate_s": round(gen_s, 2),
+           "create_s": round(create_s, 2)}
+
+    def timed(fn, warm=True):
+        if warm:
+            fn(TOL, args.maxit)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(TOL, args.maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0
+
+    secs = timed(s.solve)
+    st = s.stats()
+    out.update(solve_s=round(secs, 3), solves_per_s=round(nprob * R / secs, 2),
+               converged=st["converged"], ne_max=st["ne_max"], iters_max=st["iters_max"],
+               iters_sum=st["iters_sum"], ms_rank=round(st["time_rank_ms"], 1),
+               ms_build=round(st["time_build_ms"], 1), ms_lsqr=round(st["time_lsqr_ms"], 1),
+               tuned={"rows_per_warp": st["rows_per_warp"], "cols_per_lane": st["cols_per_lane"]},
+               launches_per_iter=st["launches_per_iter"])
+    if not args.no_plain:
+        psecs = timed(s.plain_lsqr, warm=False)  # kernels already warm from the solves
+        pst = s.stats()
+        out["plain_lsqr"] = {"solve_s": round(psecs, 3), "solves_per_s": round(nprob * R / psecs, 2),
+                             "converged": pst["converged"], "ne_max": pst["ne_max"],
+                             "iters_max": pst["iters_max"]}
+        out["speedup_vs_plain"] = round(psecs / secs, 3)
+    s.close()
+    return out
+
+
 def roofline(prof):
     nf = len(prof["ms"])
     k = max(range(nf), key=lambda q: prof["ms"][q])
@@ -346,22 +411,22 @@ def roofline(prof):
 
 
 def traffic_for(k, bpl):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this launch size,
-    or None when no capture of the current kernel source exists."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per launch from the committed ncu summary table (profiles/ncu_traffic.md),
+    scaled to this launch size, or None when no capture of the current kernel source exists."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     try:
-        with open(path) as f:
-            d = json.load(f)
-        ent = d.get(str(k))
-        if not ent:
-            return None
-        import hashlib
-        src = open(os.path.join(ROOT, ent["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != ent["sha256"]:
-            return None
-        return int(ent["dram_bytes_per_algorithmic_byte"] * bpl)
-    except Exception:
+        for line in open(path):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) < 4 or cells[0] != str(k):
+                continue
+            src = open(os.path.join(ROOT, cells[1]), "rb").read()
+            if hashlib.sha256(src).hexdigest() != cells[2]:
+                return None
+            return int(float(cells[3]) * bpl)
+    except (OSError, ValueError):
         return None
+    return None
 
 
 # ----------------------------------------------------------------------------- CPU arm --
@@ -482,7 +547,7 @@ def main():
                 "time_to_tol_s": r["ms"] / 1000.0, "schedule": r["sched"],
                 "ne_res": r["ne"], "plain_lsqr": r["plain"], "clocks": r["clocks"],
                 "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roof"],
-                "spmv": r["spmv"],
+                "spmv": r["spmv"], "batched": r["batched"],
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:

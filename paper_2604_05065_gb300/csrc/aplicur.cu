@@ -1314,7 +1314,9 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     h->np = nprob;
     h->R = nrhs;
     h->mu = mu;
-    h->nthreads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    // worker threads mostly wait on their problem's stream, so more threads than cores
+    // keep more problems' small kernels in flight
+    h->nthreads = (int)std::max(4u, std::min(32u, 2 * std::thread::hardware_concurrency()));
     aplicur_options o;
     if (opt) o = *opt; else aplicur_options_default(&o);
     o.replay_nphases = 0; o.replay_phases = nullptr;

@@ -234,3 +234,46 @@ def batched(nprob=512, m_range=(2000, 50000), n_range=(100, 2000), density=1e-3,
                                sketch_dim, b, indptr=indptr, indices=cols.astype(np.int64),
                                data=vals))
     return out
+
+
+def batched_device(device, nprob=512, m_range=(2000, 50000), n_range=(100, 2000), density=1e-3,
+                   nrhs=16, mu=1e-5, decay_orders=6.0, index=4):
+    """The batched workload generated on the GPU (torch, seeded): same recipe as
+    ``batched`` (sizes from the same host generator, U and V from QR of Gaussians drawn on
+    the device, FP32 storage).  Dense rows are padded to a multiple of 4 floats (16-byte
+    rows; A is a view with row stride ld).  Returns (mats, rhs, sizes) with device tensors
+    (CSR matrices as torch.sparse_csr_tensor, right-hand sides m x nrhs float64)."""
+    import torch
+
+    rng = _rng(index)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(BASE_SEED + index)
+    mats, rhs, sizes = [], [], []
+    half = nprob // 2
+    for p in range(nprob):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        m = int(rng.integers(max(m_range[0], n), m_range[1] + 1))
+        b = torch.randn(m, nrhs, generator=gen, device=device, dtype=torch.float64)
+        if p < half:
+            U, _ = torch.linalg.qr(torch.randn(m, n, generator=gen, device=device))
+            V, _ = torch.linalg.qr(torch.randn(n, n, generator=gen, device=device))
+            sv = 10.0 ** (-decay_orders * torch.arange(n, device=device, dtype=torch.float32)
+                          / max(n - 1, 1))
+            ld = (n + 3) // 4 * 4
+            buf = torch.zeros(m, ld, device=device, dtype=torch.float32)
+            buf[:, :n] = (U * sv) @ V.T
+            del U, V
+            mats.append(buf[:, :n])
+        else:
+            mask = torch.rand(m, n, generator=gen, device=device) < density
+            idx = mask.nonzero()
+            vals = torch.randn(idx.shape[0], generator=gen, device=device, dtype=torch.float32)
+            counts = torch.bincount(idx[:, 0], minlength=m)
+            crow = torch.zeros(m + 1, dtype=torch.int64, device=device)
+            crow[1:] = torch.cumsum(counts, 0)
+            mats.append(torch.sparse_csr_tensor(crow, idx[:, 1].contiguous(), vals, size=(m, n)))
+            del mask
+        rhs.append(b)
+        sizes.append((m, n, "dense" if p < half else "csr"))
+    return mats, rhs, sizes
+
