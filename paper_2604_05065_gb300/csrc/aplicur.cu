@@ -1135,8 +1135,10 @@ void batch_phase(aplicur_batch_ctx* h, const std::vector<char>& mask, const std:
   std::vector<long long> budget(npairs, 0);
   for (size_t e = 0; e < npairs; ++e) budget[e] = std::max(0LL, maxit - h->iters[e]);
   std::vector<int> reasons;
-  h->eng.run_phase(mask, nu, h->pc.empty() ? 1e-10 : h->pc[0]->opt.eps_lsqr, tol, budget, it_out,
-                   reasons);
+  // the Paige-Saunders tests must not end a phase before the refinement can reach tol:
+  // with FP32 recurrences a phase stopped at eps_lsqr ~ tol leaves the pair just short
+  const double eps = std::min(h->pc[0]->opt.eps_lsqr, 0.01 * tol);
+  h->eng.run_phase(mask, nu, eps, tol, budget, it_out, reasons);
   for (size_t e = 0; e < npairs; ++e) h->iters[e] += it_out[e];
   std::vector<double> ne;
   h->eng.ne_residual(mask, ne);

@@ -399,20 +399,32 @@ __global__ void __launch_bounds__(NT) k2b_dense(int64_t m, int64_t n, int rchunk
 
 // ---- preconditioner passes (FP64, Vhat = Q_R V_M implicit) -----------------------------
 
-// q1 = Q^T w: one warp per column of Q.
+// Partial q1 = Q^T w: block (k, c) sums column k of Q over the row chunk c (QT_CHUNK
+// rows), so ell x chunks blocks share the pass; pre_qsum adds the chunks in order.
+constexpr int QT_CHUNK = 2048;
 __global__ void __launch_bounds__(NT) pre_qt(int64_t n, int ell, int64_t ldq,
                                              const double* __restrict__ Q,
                                              const double* __restrict__ w,
-                                             double* __restrict__ q1, const LsqrCtl* ctl) {
+                                             double* __restrict__ qpart, const LsqrCtl* ctl) {
+  __shared__ double sh[NT / 32];
   if (ctl && ctl->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t k = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-  if (k >= ell) return;
+  const int64_t k = blockIdx.x, c = blockIdx.y;
   const double* qk = Q + k * ldq;
+  const int64_t i1 = min(n, (c + 1) * (int64_t)QT_CHUNK);
   double s = 0.0;
-  for (int64_t i = lane; i < n; i += 32) s = fma(qk[i], w[i], s);
-  s = warp_sum(s);
-  if (lane == 0) q1[k] = s;
+  for (int64_t i = c * QT_CHUNK + threadIdx.x; i < i1; i += NT) s = fma(qk[i], w[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) qpart[k * gridDim.y + c] = s;
+}
+
+__global__ void pre_qsum(int ell, int nch, const double* __restrict__ qpart,
+                         double* __restrict__ q1, const LsqrCtl* ctl) {
+  if (ctl && ctl->done) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ell) return;
+  double s = 0.0;
+  for (int c = 0; c < nch; ++c) s += qpart[(int64_t)k * nch + c];
+  q1[k] = s;
 }
 
 // ct = coef (V_M^T q1), c2t = coef2 (V_M^T q1): one warp per column of V_M.
@@ -436,27 +448,40 @@ __global__ void __launch_bounds__(NT) pre_vt(int ell, const double* __restrict__
   }
 }
 
-// q3 = V_M ct, q3b = V_M c2t: one thread per row of V_M.
+// q3 = V_M ct, q3b = V_M c2t: a block takes 32 rows (lanes, coalesced column reads of the
+// column-major V_M) and its 8 warps split the k range; the partial sums meet in shared
+// memory in warp order.
 __global__ void __launch_bounds__(NT) pre_v(int ell, const double* __restrict__ VM,
                                             const double* __restrict__ ct,
                                             const double* __restrict__ c2t,
                                             double* __restrict__ q3, double* __restrict__ q3b,
                                             const LsqrCtl* ctl) {
+  __shared__ double r1[NT / 32][32], r2[NT / 32][32];
   if (ctl && ctl->done) return;
-  const int i = blockIdx.x * NT + threadIdx.x;
-  if (i >= ell) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   double s1 = 0.0, s2 = 0.0;
-  for (int k = 0; k < ell; ++k) {
-    const double v = VM[i + (int64_t)k * ell];
-    s1 = fma(v, ct[k], s1);
-    if (q3b) s2 = fma(v, c2t[k], s2);
+  if (i < ell) {
+    for (int k = warp; k < ell; k += NT / 32) {
+      const double v = VM[i + (int64_t)k * ell];
+      s1 = fma(v, ct[k], s1);
+      if (q3b) s2 = fma(v, c2t[k], s2);
+    }
   }
-  q3[i] = s1;
-  if (q3b) q3b[i] = s2;
+  r1[warp][lane] = s1;
+  r2[warp][lane] = s2;
+  __syncthreads();
+  if (warp != 0 || i >= ell) return;
+  double t1 = 0.0, t2 = 0.0;
+  for (int w = 0; w < NT / 32; ++w) { t1 += r1[w][lane]; t2 += r2[w][lane]; }
+  q3[i] = t1;
+  if (q3b) q3b[i] = t2;
 }
 
-// out1 = w + Q q3, out2 = w + Q q3b, one thread per row of Q.  In the LSQR phase also
-// subtracts beta v / beta z, writes the FP32 split of z' and reduces ||v'||^2.
+// out1 = w + Q q3, out2 = w + Q q3b.  A block takes 32 rows per pass (lanes: coalesced
+// reads of the column-major Q) and its 8 warps split the k range; warp 0 combines the
+// partial sums in warp order and writes the row.  In the LSQR phase also subtracts beta v /
+// beta z, writes the FP32 split of z' and reduces ||v'||^2.
 __global__ void __launch_bounds__(NT) pre_expand(int64_t n, int ell, int64_t ldq,
                                                  const double* __restrict__ Q,
                                                  const double* __restrict__ q3,
@@ -466,28 +491,41 @@ __global__ void __launch_bounds__(NT) pre_expand(int64_t n, int ell, int64_t ldq
                                                  LsqrCtl* ctl, double* __restrict__ red,
                                                  int init) {
   __shared__ double sh[NT / 32];
+  __shared__ double r1[NT / 32][32], r2[NT / 32][32];
   if (ctl && ctl->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double beta = 0.0, zs = 0.0;
   if (ctl && !init) { beta = ctl->beta; zs = ctl->zs; }
   double ss = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+  for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < n; r0 += (int64_t)gridDim.x * 32) {
+    const int64_t i = r0 + lane;
     double s1 = 0.0, s2 = 0.0;
-    for (int k = 0; k < ell; ++k) {
-      const double q = Q[i + k * ldq];
-      s1 = fma(q, q3[k], s1);
-      if (out2) s2 = fma(q, q3b[k], s2);
+    if (i < n) {
+      for (int k = warp; k < ell; k += NT / 32) {
+        const double q = Q[i + k * ldq];
+        s1 = fma(q, q3[k], s1);
+        if (out2) s2 = fma(q, q3b[k], s2);
+      }
     }
-    const double wi = w[i];
-    double o1 = wi + s1;
-    if (ctl && !init) o1 -= beta * (out1[i] * zs);
-    out1[i] = o1;
-    if (out2) {
-      double o2 = wi + s2;
-      if (ctl && !init) o2 -= beta * (out2[i] * zs);
-      out2[i] = o2;
-      if (zh) split(o2, zh, zl, i);
+    r1[warp][lane] = s1;
+    r2[warp][lane] = s2;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+      double t1 = 0.0, t2 = 0.0;
+      for (int v = 0; v < NT / 32; ++v) { t1 += r1[v][lane]; t2 += r2[v][lane]; }
+      const double wi = w[i];
+      double o1 = wi + t1;
+      if (ctl && !init) o1 -= beta * (out1[i] * zs);
+      out1[i] = o1;
+      if (out2) {
+        double o2 = wi + t2;
+        if (ctl && !init) o2 -= beta * (out2[i] * zs);
+        out2[i] = o2;
+        if (zh) split(o2, zh, zl, i);
+      }
+      ss += o1 * o1;
     }
-    ss += o1 * o1;
+    __syncthreads();
   }
   if (!ctl) return;
   const double b = block_sum(ss, sh);
@@ -748,14 +786,18 @@ void LsqrEngine::launch_pre(const PrecondDev& P, const double* w, double* o1, do
   q3b_.alloc(ell, st_);
   const LsqrCtl* c = in_phase ? ctl_.p : nullptr;
   const unsigned wb = (unsigned)cdiv((int64_t)ell * 32, NT);
-  pre_qt<<<wb, NT, 0, st_>>>(n_, ell, P.ldq, P.Q, w, q1_.p, c);
+  const int nch = (int)cdiv(n_, (int64_t)QT_CHUNK);
+  qpart_.alloc((size_t)ell * nch, st_);
+  pre_qt<<<dim3((unsigned)ell, (unsigned)nch), NT, 0, st_>>>(n_, ell, P.ldq, P.Q, w, qpart_.p, c);
+  APL_LAUNCH_CHECK();
+  pre_qsum<<<(unsigned)cdiv(ell, NT), NT, 0, st_>>>(ell, nch, qpart_.p, q1_.p, c);
   APL_LAUNCH_CHECK();
   pre_vt<<<wb, NT, 0, st_>>>(ell, P.VM, q1_.p, P.coef, P.coef2, ct_.p, o2 ? c2t_.p : nullptr, c);
   APL_LAUNCH_CHECK();
-  pre_v<<<(unsigned)cdiv(ell, NT), NT, 0, st_>>>(ell, P.VM, ct_.p, c2t_.p, q3_.p,
+  pre_v<<<(unsigned)cdiv(ell, 32), NT, 0, st_>>>(ell, P.VM, ct_.p, c2t_.p, q3_.p,
                                                  o2 ? q3b_.p : nullptr, c);
   APL_LAUNCH_CHECK();
-  const int blocks = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
+  const int blocks = (int)std::min<int64_t>(cdiv(n_, 32), sm_blocks());
   LsqrCtl* cw = in_phase ? ctl_.p : nullptr;
   float* zh = (in_phase && mode_) ? zh_.p : nullptr;
   float* zl = (in_phase && mode_) ? zl_.p : nullptr;
@@ -888,7 +930,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     }
     prof.bytes[2] = 2.0 * n_ * ell * 8.0 + 2.0 * ell * ell * 8.0 + 56.0 * n_;
   }
-  kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 4 : 0);
+  kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 5 : 0);
   if (profile_) ensure_events(4 * std::max(G, 1));
   auto iteration = [&](int i) {
     if (profile_) record(4 * i);

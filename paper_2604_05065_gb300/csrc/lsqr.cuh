@@ -99,7 +99,7 @@ class LsqrEngine {
   int64_t m_ = 0, n_ = 0;
   int k1_blocks_ = 0, k2_blocks_ = 0, k2_rchunks_ = 1, red_cap_ = 0;
   DBuf<LsqrCtl> ctl_;
-  DBuf<double> u_, v_, z_, g_, d_, red_, part_, q1_, ct_, c2t_, q3_, q3b_, r_, q_;
+  DBuf<double> u_, v_, z_, g_, d_, red_, part_, q1_, ct_, c2t_, q3_, q3b_, r_, q_, qpart_;
   DBuf<float> zh_, zl_, uh_, ul_;  // FP32 hi/lo splits of z' and u' (modes 1, 2)
   DBuf<double> scal_;
   DBuf<unsigned int> cnt_;
