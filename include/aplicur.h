@@ -110,6 +110,12 @@ typedef struct {
   /* > 0: cap the CUR rank; reaching it ends rank growth like reaching min(m, n)
    * (the last block is truncated to fit).  0: no cap. */
   int32_t max_rank;
+  /* Non-zero: the dense products of the rank steps and preconditioner builds (GEMMs of
+   * augmentQR, E_col, E_row, Cholesky and triangular-solve updates, the Jacobi rotation
+   * transfer) run on the FP64 units.  0 (default): compensated FP32 (hi + lo operands,
+   * exact hi products, TwoSum accumulation; about 2^-46 relative), several times faster
+   * on GB300, whose FP64 rate is 1/64 of its FP32 rate. */
+  int32_t fp64_dense;
 } aplicur_options;
 
 /* Device time by kernel family, accumulated over the solves since creation or the

@@ -627,6 +627,7 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   h->bsize = sketch_dim;
   h->s = (11 * sketch_dim + 9) / 10;
   h->xi = std::min(h->opt.xi, h->s);
+  h->dw.fp64_gemm = h->opt.fp64_dense != 0;
   h->r = h->opt.normest_r;
   if (h->A.fmt == 1) build_csc(h);
   // sketch and norm-estimate draws

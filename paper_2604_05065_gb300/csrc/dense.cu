@@ -86,6 +86,8 @@ void prof_set_work(int token, double work) {
 
 // ------------------------------------------------------------------------------------
 // GEMM: 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K step 16.
+// Two arithmetic forms: FP64 (dgemm_kernel) and compensated FP32 (df32gemm_kernel, the
+// default; the context's DenseWork selects).
 // ------------------------------------------------------------------------------------
 namespace {
 constexpr int GBM = 64, GBN = 64, GBK = 16;
@@ -161,6 +163,98 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
   }
 }
 
+// The same tiling with compensated FP32 arithmetic: every FP64 operand is split into
+// FP32 hi + lo when its tile is staged (hi + lo keeps 48 of its 53 bits), a product is
+// formed exactly in its hi * hi part (an FMA gives the rounding error) plus the two cross
+// terms, and the running sum is an unevaluated FP32 pair updated by Knuth's TwoSum.  The
+// result is accurate to about 2^-46 relative to sum |a_i b_i| with only FP32 instructions,
+// which GB300 issues at 64 times its FP64 rate.
+__global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, int64_t M,
+                                                       int64_t N, int64_t K, double alpha,
+                                                       const double* __restrict__ A,
+                                                       int64_t lda,
+                                                       const double* __restrict__ B,
+                                                       int64_t ldb, double beta,
+                                                       double* __restrict__ C, int64_t ldc,
+                                                       int64_t kchunk,
+                                                       double* __restrict__ part) {
+  __shared__ float Ah[GBK][GBM + 1], Al[GBK][GBM + 1];
+  __shared__ float Bh[GBK][GBN + 1], Bl[GBK][GBN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
+
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = threadIdx.x + e * 256;
+      int mm, kk;
+      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < M && gk < kend) v = transA ? A[gk + gm * lda] : A[gm + gk * lda];
+      const float vh = __double2float_rn(v);
+      Ah[kk][mm] = vh;
+      Al[kk][mm] = __double2float_rn(v - (double)vh);
+      int nn;
+      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
+      const int64_t gn = n0 + nn, gk2 = k0 + kk;
+      double w = 0.0;
+      if (gn < N && gk2 < kend) w = transB ? B[gn + gk2 * ldb] : B[gk2 + gn * ldb];
+      const float wh = __double2float_rn(w);
+      Bh[kk][nn] = wh;
+      Bl[kk][nn] = __double2float_rn(w - (double)wh);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GBK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { ah[i] = Ah[kk][ty + 16 * i]; al[i] = Al[kk][ty + 16 * i]; }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { bh[j] = Bh[kk][tx + 16 * j]; bl[j] = Bl[kk][tx + 16 * j]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float p = __fmul_rn(ah[i], bh[j]);
+          float x = __fmaf_rn(ah[i], bh[j], -p);
+          x = __fmaf_rn(ah[i], bl[j], x);
+          x = __fmaf_rn(al[i], bh[j], x);
+          const float t = __fadd_rn(s[i][j], p);
+          const float bv = __fsub_rn(t, s[i][j]);
+          const float err = __fadd_rn(__fsub_rn(s[i][j], __fsub_rn(t, bv)), __fsub_rn(p, bv));
+          s[i][j] = t;
+          c[i][j] = __fadd_rn(c[i][j], __fadd_rn(err, x));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      const double acc = (double)s[i][j] + (double)c[i][j];
+      if (part) {
+        part[(int64_t)blockIdx.z * M * N + gm + gn * M] = acc;
+      } else {
+        double* cp = C + gm + gn * ldc;
+        *cp = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *cp;
+      }
+    }
+  }
+}
+
 // C = alpha * sum_z part[z] + beta * C, summing the splits in a fixed order.
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const double* part,
                                      double alpha, double beta, double* C, int64_t ldc) {
@@ -197,21 +291,29 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
     splits = std::min<int64_t>(splits, 64);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, (int64_t)(1 << 24) / (M * N)));
   }
+  const bool fp64 = dense_work().fp64_gemm;
   const int tok = prof_begin(st);
   if (splits > 1) {
     const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
     splits = cdiv(K, kchunk);
     dense_work().splitk.alloc((size_t)splits * M * N, st);
     grid.z = (unsigned)splits;
-    dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc,
-                                       kchunk, dense_work().splitk.p);
+    if (fp64)
+      dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
+                                         ldc, kchunk, dense_work().splitk.p);
+    else
+      df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
+                                            ldc, kchunk, dense_work().splitk.p);
     APL_LAUNCH_CHECK();
     splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
                                                                      dense_work().splitk.p, alpha, beta, C,
                                                                      ldc);
-  } else {
+  } else if (fp64) {
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
                                        ldc, K, nullptr);
+  } else {
+    df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta,
+                                          C, ldc, K, nullptr);
   }
   APL_LAUNCH_CHECK();
   prof_end(st, tok, PROF_GEMM, 2.0 * (double)M * (double)N * (double)K);
@@ -659,6 +761,145 @@ __global__ void __launch_bounds__(32 * JW) jacobi32_block_kernel(int64_t l, int6
   }
 }
 
+// Stage 2 in compensated FP32, block-cyclic like stage 1: the CTA's 16 columns live in
+// shared memory as FP32 hi/lo pairs (48 of the 53 bits of B); the three dot products of a
+// pair are summed as unevaluated FP32 pairs (TwoSum) and the angle is formed in FP64 from
+// them, so c^2 + s^2 = 1 to FP64 accuracy; the rotation is applied in compensated FP32.
+// Singular values depend on the off-diagonal only to second order, so the threshold
+// (set above the dot-product noise, about 1e-12) leaves them accurate to rounding; the
+// vectors carry first-order errors at the threshold.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+// (h, l) <- c * x with c = ch + cl and x = xh + xl
+__device__ __forceinline__ void df_scale(float ch, float cl, float xh, float xl, float& h,
+                                         float& l) {
+  h = __fmul_rn(ch, xh);
+  const float e = __fmaf_rn(ch, xh, -h);
+  l = __fmaf_rn(ch, xl, __fmaf_rn(cl, xh, e));
+}
+// acc += x * y (pairs)
+__device__ __forceinline__ void df_dot_add(float& s, float& c, float xh, float xl, float yh,
+                                           float yl) {
+  const float p = __fmul_rn(xh, yh);
+  const float e = __fmaf_rn(xh, yh, -p);
+  const float cross = __fmaf_rn(xh, yl, __fmul_rn(xl, yh));
+  float t, err;
+  df_two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, cross)));
+}
+
+__device__ __forceinline__ double warp_allsum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void jacdf_pair(float2* __restrict__ cp, float2* __restrict__ cq,
+                                           int64_t l, double tol, int lane, int& rot) {
+  float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, gs = 0.f, gc = 0.f;
+  for (int64_t i = lane; i < l; i += 32) {
+    const float2 x = cp[i], y = cq[i];
+    df_dot_add(as, ac, x.x, x.y, x.x, x.y);
+    df_dot_add(bs, bc, y.x, y.y, y.x, y.y);
+    df_dot_add(gs, gc, x.x, x.y, y.x, y.y);
+  }
+  // lane sums to FP64, then a butterfly (identical on every lane)
+  const double a = warp_allsum_d((double)as + (double)ac);
+  const double b = warp_allsum_d((double)bs + (double)bc);
+  const double g = warp_allsum_d((double)gs + (double)gc);
+  if (!(a > 0.0 && b > 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b))) return;
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cd = 1.0 / sqrt(1.0 + t * t), sd = cd * t;
+  const float ch = __double2float_rn(cd), cl = __double2float_rn(cd - (double)ch);
+  const float sh = __double2float_rn(sd), sl = __double2float_rn(sd - (double)sh);
+  for (int64_t i = lane; i < l; i += 32) {
+    const float2 x = cp[i], y = cq[i];
+    float cxh, cxl, syh, syl, sxh, sxl, cyh, cyl;
+    df_scale(ch, cl, x.x, x.y, cxh, cxl);
+    df_scale(sh, sl, y.x, y.y, syh, syl);
+    df_scale(sh, sl, x.x, x.y, sxh, sxl);
+    df_scale(ch, cl, y.x, y.y, cyh, cyl);
+    float r, er;
+    df_two_sum(cxh, -syh, r, er);  // x' = c x - s y
+    float lo = __fadd_rn(er, __fsub_rn(cxl, syl));
+    float h2, l2;
+    df_two_sum(r, lo, h2, l2);
+    cp[i] = make_float2(h2, l2);
+    df_two_sum(sxh, cyh, r, er);   // y' = s x + c y
+    lo = __fadd_rn(er, __fadd_rn(sxl, cyl));
+    df_two_sum(r, lo, h2, l2);
+    cq[i] = make_float2(h2, l2);
+  }
+  ++rot;
+}
+
+// grid NB/2, block 32 * JW threads, dynamic shared memory JW2 * l float2
+__global__ void __launch_bounds__(32 * JW) jacobi_df_block_kernel(int64_t l, int64_t NB,
+                                                                  int64_t r, double* __restrict__ B,
+                                                                  int64_t ldb, double tol,
+                                                                  int* rotated) {
+  extern __shared__ float2 dsm[];
+  __shared__ int gcol[JW2];
+  __shared__ int cta_rot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = blockIdx.x;
+  const int64_t bp = rr_elem(k, r, NB), bq = rr_elem(NB - 1 - k, r, NB);
+  if (threadIdx.x < JW2) {
+    const int64_t blk = threadIdx.x < JW ? bp : bq;
+    const int64_t c = blk * JW + (threadIdx.x % JW);
+    gcol[threadIdx.x] = c < l ? (int)c : -1;
+  }
+  if (threadIdx.x == 0) cta_rot = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
+    double v[JW2];
+#pragma unroll
+    for (int c = 0; c < JW2; ++c) v[c] = gcol[c] >= 0 ? B[(int64_t)gcol[c] * ldb + i] : 0.0;
+#pragma unroll
+    for (int c = 0; c < JW2; ++c) {
+      const float h = __double2float_rn(v[c]);
+      dsm[(size_t)c * l + i] = make_float2(h, __double2float_rn(v[c] - (double)h));
+    }
+  }
+  __syncthreads();
+  int rot = 0;
+  if (r == 0) {
+    for (int ir = 0; ir < JW - 1; ++ir) {
+      const int t = warp % (JW / 2), side = warp / (JW / 2);
+      int p = (int)rr_elem(t, ir, JW), q = (int)rr_elem(JW - 1 - t, ir, JW);
+      if (p > q) { const int z = p; p = q; q = z; }
+      p += side * JW;
+      q += side * JW;
+      if (gcol[p] >= 0 && gcol[q] >= 0)
+        jacdf_pair(dsm + (size_t)p * l, dsm + (size_t)q * l, l, tol, lane, rot);
+      __syncthreads();
+    }
+  }
+  for (int ir = 0; ir < JW; ++ir) {
+    const int p = warp, q = JW + (warp + ir) % JW;
+    if (gcol[p] >= 0 && gcol[q] >= 0)
+      jacdf_pair(dsm + (size_t)p * l, dsm + (size_t)q * l, l, tol, lane, rot);
+    __syncthreads();
+  }
+  if (lane == 0 && rot) atomicAdd(&cta_rot, rot);
+  __syncthreads();
+  if (cta_rot == 0) return;
+  if (threadIdx.x == 0) atomicAdd(rotated, cta_rot);
+  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0) {
+        const float2 v = dsm[(size_t)c * l + i];
+        B[(int64_t)gcol[c] * ldb + i] = (double)v.x + (double)v.y;
+      }
+  }
+}
+
 __global__ void d2f_kernel(int64_t l, const double* s, int64_t lds, float* d) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * l) return;
@@ -774,7 +1015,22 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, G, l);
     dcopy2d(st, l, l, G, l, B, ldb, false);
   }
-  if (l > 1) {
+  const size_t smem_df = (size_t)JW2 * l * sizeof(float2);
+  if (l > 1 && !dense_work().fp64_gemm && smem_df <= (size_t)kJac32SmemCap) {
+    // Stage 2 in compensated FP32 (block-cyclic): threshold above the noise of the
+    // compensated dot products, about (l/32 + 5) 2^-46 relative
+    const double tol = std::max(1e-13, 4.0 * ((double)l / 32.0 + 5.0) * 1.4210854715202004e-14);
+    const int64_t nb = cdiv(l, (int64_t)JW);
+    const int64_t NB = nb + (nb % 2);
+    APL_CUDA(cudaFuncSetAttribute(jacobi_df_block_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
+    const double pairs = (double)(l * (l - 1)) / 2.0;
+    sweeps += run_sweeps(st, NB, 60, flag_dev, [&](int64_t r) {
+      jacobi_df_block_kernel<<<(unsigned)(NB / 2), 32 * JW, smem_df, st>>>(l, NB, r, B, ldb, tol,
+                                                                          flag_dev);
+      APL_LAUNCH_CHECK();
+    }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l);
+  } else if (l > 1) {
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
     const double pairs = (double)(l * (l - 1)) / 2.0;
