@@ -2,6 +2,7 @@
 // steps: tiled GEMM, blocked triangular solves, single-CTA Cholesky, Cholesky QR2 and a
 // parallel one-sided (Hestenes) Jacobi SVD.
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 #include <numeric>
 
@@ -649,44 +650,67 @@ constexpr int JW = 8;
 constexpr int JW2 = 2 * JW;
 constexpr int kJac32SmemCap = 220 * 1024;  // dynamic shared memory cap of the FP32 stage
 
-__device__ __forceinline__ void jac32_pair(float* __restrict__ cp, float* __restrict__ cq,
-                                           float* __restrict__ R, int p, int q, int64_t l,
-                                           float tol, int lane, int& rot) {
-  float a = 0.f, b = 0.f, g = 0.f;
-  for (int64_t i = lane; i < l; i += 32) {
-    const float x = cp[i], y = cq[i];
-    a = fmaf(x, x, a);
-    b = fmaf(y, y, b);
-    g = fmaf(x, y, g);
-  }
+__device__ __forceinline__ float warp_allsumf(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    g += __shfl_xor_sync(0xffffffffu, g, o);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One pair (p, q) handled by two warps (interleaved 32-element stretches); the dot
+// products meet in shared memory in half order so both warps take the same rotation.
+// All threads of the block call this (three synchronisations).  Half 0 also rotates the
+// columns p, q of the accumulated rotation R.
+__device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __restrict__ cq,
+                                            float* __restrict__ R, int p, int q, bool valid,
+                                            int64_t l, float tol, int lane, int half,
+                                            float* xch, int& rot) {
+  float a = 0.f, b = 0.f, g = 0.f;
+  if (valid) {
+    for (int64_t i = lane + 32 * half; i < l; i += 64) {
+      const float x = cp[i], y = cq[i];
+      a = fmaf(x, x, a);
+      b = fmaf(y, y, b);
+      g = fmaf(x, y, g);
+    }
   }
-  if (!(a > 0.f && b > 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b))) return;
+  a = warp_allsumf(a);
+  b = warp_allsumf(b);
+  g = warp_allsumf(g);
+  if (lane == 0) { xch[3 * half] = a; xch[3 * half + 1] = b; xch[3 * half + 2] = g; }
+  __syncthreads();
+  a = xch[0] + xch[3];
+  b = xch[1] + xch[4];
+  g = xch[2] + xch[5];
+  __syncthreads();
+  if (!(valid && a > 0.f && b > 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b))) {
+    __syncthreads();
+    return;
+  }
   const float zeta = (b - a) / (2.f * g);
   const float az = fabsf(zeta);
   // tan of the rotation angle, the smaller root; 1 / (2 zeta) once zeta^2 would overflow
   float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
   t = zeta >= 0.f ? t : -t;
   const float c = rsqrtf(1.f + t * t), sn = c * t;
-  for (int64_t i = lane; i < l; i += 32) {
+  for (int64_t i = lane + 32 * half; i < l; i += 64) {
     const float x = cp[i], y = cq[i];
     cp[i] = c * x - sn * y;
     cq[i] = sn * x + c * y;
   }
-  if (lane < JW2) {
-    const float u = R[lane * JW2 + p], v = R[lane * JW2 + q];
-    R[lane * JW2 + p] = c * u - sn * v;
-    R[lane * JW2 + q] = sn * u + c * v;
+  if (half == 0) {
+    if (lane < JW2) {
+      const float u = R[lane * JW2 + p], v = R[lane * JW2 + q];
+      R[lane * JW2 + p] = c * u - sn * v;
+      R[lane * JW2 + q] = sn * u + c * v;
+    }
+    ++rot;
   }
-  ++rot;
+  __syncthreads();
 }
 
-// grid NB/2, block 32 * JW threads, dynamic shared memory JW2 * l floats + R
-__global__ void __launch_bounds__(32 * JW) jacobi32_block_kernel(int64_t l, int64_t NB,
+// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory JW2 * l
+// floats + R
+__global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int64_t NB,
                                                                  int64_t r, float* __restrict__ B,
                                                                  float* __restrict__ W,
                                                                  float tol, int* rotated) {
@@ -695,7 +719,9 @@ __global__ void __launch_bounds__(32 * JW) jacobi32_block_kernel(int64_t l, int6
   float* R = jsm + (size_t)JW2 * l;   // JW2 x JW2, row-major R[row * JW2 + col]
   __shared__ int gcol[JW2];
   __shared__ int cta_rot;
+  __shared__ float xch[JW][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pw = warp >> 1, half = warp & 1;
   const int64_t k = blockIdx.x;
   const int64_t bp = rr_elem(k, r, NB), bq = rr_elem(NB - 1 - k, r, NB);
   if (threadIdx.x < JW2) {
@@ -720,44 +746,46 @@ __global__ void __launch_bounds__(32 * JW) jacobi32_block_kernel(int64_t l, int6
   if (r == 0) {
     // pairs inside each block: JW - 1 round-robin rounds of JW/2 pairs per block
     for (int ir = 0; ir < JW - 1; ++ir) {
-      const int t = warp % (JW / 2), side = warp / (JW / 2);
+      const int t = pw % (JW / 2), side = pw / (JW / 2);
       int p = (int)rr_elem(t, ir, JW), q = (int)rr_elem(JW - 1 - t, ir, JW);
       if (p > q) { const int z = p; p = q; q = z; }
       p += side * JW;
       q += side * JW;
-      if (gcol[p] >= 0 && gcol[q] >= 0)
-        jac32_pair(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q, l, tol, lane, rot);
-      __syncthreads();
+      jac32_pair2(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q,
+                  gcol[p] >= 0 && gcol[q] >= 0, l, tol, lane, half, xch[pw], rot);
     }
   }
   for (int ir = 0; ir < JW; ++ir) {
-    const int p = warp, q = JW + (warp + ir) % JW;
-    if (gcol[p] >= 0 && gcol[q] >= 0)
-      jac32_pair(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q, l, tol, lane, rot);
-    __syncthreads();
+    const int p = pw, q = JW + (pw + ir) % JW;
+    jac32_pair2(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q,
+                gcol[p] >= 0 && gcol[q] >= 0, l, tol, lane, half, xch[pw], rot);
   }
   if (lane == 0 && rot) atomicAdd(&cta_rot, rot);
   __syncthreads();
   if (cta_rot == 0) return;
   if (threadIdx.x == 0) atomicAdd(rotated, cta_rot);
-  // write back the columns and W(:, cols) <- W(:, cols) R, one row per thread and pass
+  // write back the columns and W(:, cols) <- W(:, cols) R, one row per thread and pass,
+  // the 16 outputs in two halves of 8 to bound registers
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < JW2; ++c)
-      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * l + i];
-    float w[JW2], o[JW2];
+    float w[JW2];
 #pragma unroll
     for (int c = 0; c < JW2; ++c) {
+      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * l + i];
       w[c] = gcol[c] >= 0 ? W[(int64_t)gcol[c] * l + i] : 0.f;
-      o[c] = 0.f;
     }
 #pragma unroll
-    for (int c = 0; c < JW2; ++c)
+    for (int h = 0; h < 2; ++h) {
+      float o[JW];
 #pragma unroll
-      for (int j = 0; j < JW2; ++j) o[j] = fmaf(w[c], R[c * JW2 + j], o[j]);
+      for (int j = 0; j < JW; ++j) o[j] = 0.f;
 #pragma unroll
-    for (int c = 0; c < JW2; ++c)
-      if (gcol[c] >= 0) W[(int64_t)gcol[c] * l + i] = o[c];
+      for (int c = 0; c < JW2; ++c)
+#pragma unroll
+        for (int j = 0; j < JW; ++j) o[j] = fmaf(w[c], R[c * JW2 + h * JW + j], o[j]);
+#pragma unroll
+      for (int j = 0; j < JW; ++j)
+        if (gcol[h * JW + j] >= 0) W[(int64_t)gcol[h * JW + j] * l + i] = o[j];
+    }
   }
 }
 
@@ -792,61 +820,135 @@ __device__ __forceinline__ void df_dot_add(float& s, float& c, float xh, float x
   c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, cross)));
 }
 
-__device__ __forceinline__ double warp_allsum_d(double v) {
+// (s, c) + (t, d) as unevaluated FP32 pairs; TwoSum's error term is exact, so the sum is
+// the same bitwise in either operand order (butterfly reductions agree on every lane).
+__device__ __forceinline__ void df_add(float& s, float& c, float t, float d) {
+  float h, e;
+  df_two_sum(s, t, h, e);
+  const float lo = __fadd_rn(e, __fadd_rn(c, d));
+  s = __fadd_rn(h, lo);
+  c = __fsub_rn(lo, __fsub_rn(s, h));
+}
+__device__ __forceinline__ void df_warp_allsum(float& s, float& c) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float t = __shfl_xor_sync(0xffffffffu, s, o);
+    const float d = __shfl_xor_sync(0xffffffffu, c, o);
+    df_add(s, c, t, d);
+  }
+}
+// 1/sqrt(v) for v = vh + vl as a pair, by two Newton steps from the FP32 estimate; the
+// result (ch, cl) satisfies ch^2 (vh + vl) = 1 to about 2^-46.
+__device__ __forceinline__ void df_rsqrt(float vh, float vl, float& ch, float& cl) {
+  float y = rsqrtf(vh), yl = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    // r = 1 - v y^2 (small), y <- y + y r / 2
+    const float q = __fmul_rn(y, y);
+    const float qe = __fmaf_rn(y, y, -q);
+    const float q2 = __fmaf_rn(2.f * y, yl, qe);  // low part of (y + yl)^2
+    const float p = __fmul_rn(vh, q);
+    const float pe = __fmaf_rn(vh, q, -p);
+    const float plo = __fmaf_rn(vh, q2, __fmaf_rn(vl, q, pe));
+    const float r = __fsub_rn(__fsub_rn(1.f, p), plo);
+    const float corr = __fmul_rn(0.5f * y, r);
+    float h, e;
+    df_two_sum(y, __fadd_rn(yl, corr), h, e);
+    y = h;
+    yl = e;
+  }
+  ch = y;
+  cl = yl;
 }
 
-__device__ __forceinline__ void jacdf_pair(float2* __restrict__ cp, float2* __restrict__ cq,
-                                           int64_t l, double tol, int lane, int& rot) {
+// One pair (p, q) of columns handled by two warps (half 0 and half 1 take interleaved
+// 32-element stretches); the compensated dot products meet in shared memory in half
+// order, so both warps form the same rotation.  The angle comes from FP32 arithmetic on
+// the compensated sums (an approximate angle only slows convergence); its cosine and sine
+// are formed as pairs with c^2 + s^2 = 1 to about 2^-46, so every rotation is orthogonal
+// to that accuracy.  All threads of the block must call this: it synchronises three
+// times (dot exchange, exchange reuse, end of the rotation).
+__device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __restrict__ cq,
+                                            bool valid, int64_t l, float tol, int lane,
+                                            int half, float* xch, int& rot, float& mx) {
   float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, gs = 0.f, gc = 0.f;
-  for (int64_t i = lane; i < l; i += 32) {
-    const float2 x = cp[i], y = cq[i];
-    df_dot_add(as, ac, x.x, x.y, x.x, x.y);
-    df_dot_add(bs, bc, y.x, y.y, y.x, y.y);
-    df_dot_add(gs, gc, x.x, x.y, y.x, y.y);
+  if (valid) {
+    for (int64_t i = lane + 32 * half; i < l; i += 64) {
+      const float2 x = cp[i], y = cq[i];
+      df_dot_add(as, ac, x.x, x.y, x.x, x.y);
+      df_dot_add(bs, bc, y.x, y.y, y.x, y.y);
+      df_dot_add(gs, gc, x.x, x.y, y.x, y.y);
+    }
   }
-  // lane sums to FP64, then a butterfly (identical on every lane)
-  const double a = warp_allsum_d((double)as + (double)ac);
-  const double b = warp_allsum_d((double)bs + (double)bc);
-  const double g = warp_allsum_d((double)gs + (double)gc);
-  if (!(a > 0.0 && b > 0.0 && fabs(g) > tol * sqrt(a) * sqrt(b))) return;
-  const double zeta = (b - a) / (2.0 * g);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cd = 1.0 / sqrt(1.0 + t * t), sd = cd * t;
-  const float ch = __double2float_rn(cd), cl = __double2float_rn(cd - (double)ch);
-  const float sh = __double2float_rn(sd), sl = __double2float_rn(sd - (double)sh);
-  for (int64_t i = lane; i < l; i += 32) {
+  df_warp_allsum(as, ac);
+  df_warp_allsum(bs, bc);
+  df_warp_allsum(gs, gc);
+  if (lane == 0) {
+    float* o = xch + 6 * half;
+    o[0] = as; o[1] = ac; o[2] = bs; o[3] = bc; o[4] = gs; o[5] = gc;
+  }
+  __syncthreads();
+  float A = xch[0], Al = xch[1], Bv = xch[2], Bl = xch[3], G = xch[4], Gl = xch[5];
+  df_add(A, Al, xch[6], xch[7]);
+  df_add(Bv, Bl, xch[8], xch[9]);
+  df_add(G, Gl, xch[10], xch[11]);
+  __syncthreads();  // xch is reused by the next inner round
+  const float relg = (valid && A > 0.f && Bv > 0.f) ? fabsf(G) / (sqrtf(A) * sqrtf(Bv)) : 0.f;
+  if (!(relg > tol)) {
+    __syncthreads();  // the next inner round reads columns other warps may still rotate
+    return;
+  }
+  mx = fmaxf(mx, relg);
+  // zeta = (b - a) / (2 g) with b - a formed from the pairs (no cancellation loss)
+  float dh = Bv, dl = Bl;
+  df_add(dh, dl, -A, -Al);
+  const float zeta = __fdiv_rn(__fadd_rn(dh, dl), 2.f * G);
+  const float az = fabsf(zeta);
+  float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
+  t = zeta >= 0.f ? t : -t;
+  // c = 1 / sqrt(1 + t^2), s = c t, as pairs
+  const float t2 = __fmul_rn(t, t);
+  const float t2e = __fmaf_rn(t, t, -t2);
+  float vh, vl;
+  df_two_sum(1.f, t2, vh, vl);
+  vl = __fadd_rn(vl, t2e);
+  float ch, cl;
+  df_rsqrt(vh, vl, ch, cl);
+  const float sh = __fmul_rn(ch, t);
+  const float sl = __fmaf_rn(cl, t, __fmaf_rn(ch, t, -sh));
+  for (int64_t i = lane + 32 * half; i < l; i += 64) {
     const float2 x = cp[i], y = cq[i];
     float cxh, cxl, syh, syl, sxh, sxl, cyh, cyl;
     df_scale(ch, cl, x.x, x.y, cxh, cxl);
     df_scale(sh, sl, y.x, y.y, syh, syl);
     df_scale(sh, sl, x.x, x.y, sxh, sxl);
     df_scale(ch, cl, y.x, y.y, cyh, cyl);
-    float r, er;
+    float r, er, h2, l2;
     df_two_sum(cxh, -syh, r, er);  // x' = c x - s y
-    float lo = __fadd_rn(er, __fsub_rn(cxl, syl));
-    float h2, l2;
-    df_two_sum(r, lo, h2, l2);
+    df_two_sum(r, __fadd_rn(er, __fsub_rn(cxl, syl)), h2, l2);
     cp[i] = make_float2(h2, l2);
     df_two_sum(sxh, cyh, r, er);   // y' = s x + c y
-    lo = __fadd_rn(er, __fadd_rn(sxl, cyl));
-    df_two_sum(r, lo, h2, l2);
+    df_two_sum(r, __fadd_rn(er, __fadd_rn(sxl, cyl)), h2, l2);
     cq[i] = make_float2(h2, l2);
   }
-  ++rot;
+  if (half == 0) ++rot;
+  __syncthreads();
 }
 
-// grid NB/2, block 32 * JW threads, dynamic shared memory JW2 * l float2
-__global__ void __launch_bounds__(32 * JW) jacobi_df_block_kernel(int64_t l, int64_t NB,
+// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory JW2 * l
+// float2.  rotated[0] counts rotations, rotated[1] holds the largest rotated |cos| of the
+// sweep (as float bits; non-negative floats order like their bits).
+__global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int64_t NB,
                                                                   int64_t r, double* __restrict__ B,
-                                                                  int64_t ldb, double tol,
+                                                                  int64_t ldb, float tol,
                                                                   int* rotated) {
   extern __shared__ float2 dsm[];
   __shared__ int gcol[JW2];
   __shared__ int cta_rot;
+  __shared__ unsigned int cta_max;
+  __shared__ float xch[JW][12];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pw = warp >> 1, half = warp & 1;  // pair slot and half of this warp
   const int64_t k = blockIdx.x;
   const int64_t bp = rr_elem(k, r, NB), bq = rr_elem(NB - 1 - k, r, NB);
   if (threadIdx.x < JW2) {
@@ -854,7 +956,7 @@ __global__ void __launch_bounds__(32 * JW) jacobi_df_block_kernel(int64_t l, int
     const int64_t c = blk * JW + (threadIdx.x % JW);
     gcol[threadIdx.x] = c < l ? (int)c : -1;
   }
-  if (threadIdx.x == 0) cta_rot = 0;
+  if (threadIdx.x == 0) { cta_rot = 0; cta_max = 0u; }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     double v[JW2];
@@ -868,28 +970,33 @@ __global__ void __launch_bounds__(32 * JW) jacobi_df_block_kernel(int64_t l, int
   }
   __syncthreads();
   int rot = 0;
+  float mx = 0.f;
   if (r == 0) {
     for (int ir = 0; ir < JW - 1; ++ir) {
-      const int t = warp % (JW / 2), side = warp / (JW / 2);
+      const int t = pw % (JW / 2), side = pw / (JW / 2);
       int p = (int)rr_elem(t, ir, JW), q = (int)rr_elem(JW - 1 - t, ir, JW);
       if (p > q) { const int z = p; p = q; q = z; }
       p += side * JW;
       q += side * JW;
-      if (gcol[p] >= 0 && gcol[q] >= 0)
-        jacdf_pair(dsm + (size_t)p * l, dsm + (size_t)q * l, l, tol, lane, rot);
-      __syncthreads();
+      jacdf_pair2(dsm + (size_t)p * l, dsm + (size_t)q * l, gcol[p] >= 0 && gcol[q] >= 0, l,
+                  tol, lane, half, xch[pw], rot, mx);
     }
   }
   for (int ir = 0; ir < JW; ++ir) {
-    const int p = warp, q = JW + (warp + ir) % JW;
-    if (gcol[p] >= 0 && gcol[q] >= 0)
-      jacdf_pair(dsm + (size_t)p * l, dsm + (size_t)q * l, l, tol, lane, rot);
-    __syncthreads();
+    const int p = pw, q = JW + (pw + ir) % JW;
+    jacdf_pair2(dsm + (size_t)p * l, dsm + (size_t)q * l, gcol[p] >= 0 && gcol[q] >= 0, l, tol,
+                lane, half, xch[pw], rot, mx);
   }
-  if (lane == 0 && rot) atomicAdd(&cta_rot, rot);
+  if (lane == 0 && half == 0 && rot) {
+    atomicAdd(&cta_rot, rot);
+    atomicMax(&cta_max, __float_as_uint(mx));
+  }
   __syncthreads();
   if (cta_rot == 0) return;
-  if (threadIdx.x == 0) atomicAdd(rotated, cta_rot);
+  if (threadIdx.x == 0) {
+    atomicAdd(rotated, cta_rot);
+    atomicMax(reinterpret_cast<unsigned int*>(rotated + 1), cta_max);
+  }
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
 #pragma unroll
     for (int c = 0; c < JW2; ++c)
@@ -920,7 +1027,8 @@ __global__ void eye32_kernel(int64_t n, float* W) {
 // until a sweep rotates nothing; returns the sweep count.
 template <typename F>
 int run_sweeps(cudaStream_t st, int64_t N, int max_sweeps, int* flag_dev, F&& round,
-               int prof_cat, double flops_per_sweep, double flops_per_rot) {
+               int prof_cat, double flops_per_sweep, double flops_per_rot,
+               double stop_max = 0.0) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   APL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -944,17 +1052,23 @@ int run_sweeps(cudaStream_t st, int64_t N, int max_sweeps, int* flag_dev, F&& ro
   } guard{exec};
   int sweeps = 0;
   for (; sweeps < max_sweeps;) {
-    APL_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int), st));
+    APL_CUDA(cudaMemsetAsync(flag_dev, 0, 2 * sizeof(int), st));
     const int tok = prof_cat >= 0 ? prof_begin(st) : -1;
     APL_CUDA(cudaGraphLaunch(exec, st));
     add_launches(N - 1);
     if (tok >= 0) prof_end(st, tok, prof_cat, 0.0);
     ++sweeps;
-    int rot = 0;
-    APL_CUDA(cudaMemcpyAsync(&rot, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int fl[2] = {0, 0};
+    APL_CUDA(cudaMemcpyAsync(fl, flag_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     APL_CUDA(cudaStreamSynchronize(st));
+    const int rot = fl[0];
     if (tok >= 0) prof_set_work(tok, flops_per_sweep + flops_per_rot * rot);
     if (rot == 0) break;
+    // every rotation of this sweep was below stop_max: the cyclic sweep converges
+    // quadratically, so what remains is of order stop_max^2, far under the threshold
+    float mx;
+    std::memcpy(&mx, &fl[1], sizeof(float));
+    if (stop_max > 0.0 && (double)mx <= stop_max) break;
   }
   return sweeps;
 }
@@ -994,7 +1108,7 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     const double flops32 = 12.0 * (double)l * (double)l * (double)(l - 1) / 2.0;
     sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
-      jacobi32_block_kernel<<<(unsigned)(NB / 2), 32 * JW, smem, st>>>(l, NB, r, B32, W32,
+      jacobi32_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem, st>>>(l, NB, r, B32, W32,
                                                                       (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI32, flops32, 0.0);
@@ -1017,19 +1131,21 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
   }
   const size_t smem_df = (size_t)JW2 * l * sizeof(float2);
   if (l > 1 && !dense_work().fp64_gemm && smem_df <= (size_t)kJac32SmemCap) {
-    // Stage 2 in compensated FP32 (block-cyclic): threshold above the noise of the
-    // compensated dot products, about (l/32 + 5) 2^-46 relative
-    const double tol = std::max(1e-13, 4.0 * ((double)l / 32.0 + 5.0) * 1.4210854715202004e-14);
+    // Stage 2 in compensated FP32 (default): block-cyclic sweeps on hi/lo columns.
+    // Threshold above the noise of the compensated dot products, about (l/64 + 6) 2^-46
+    // relative; a sweep whose rotations were all below 1e-2 sqrt(tol) ends the iteration
+    // (the next sweep would find at most about the square of that).
+    const double tol = std::max(1e-13, 4.0 * ((double)l / 64.0 + 6.0) * 1.4210854715202004e-14);
     const int64_t nb = cdiv(l, (int64_t)JW);
     const int64_t NB = nb + (nb % 2);
     APL_CUDA(cudaFuncSetAttribute(jacobi_df_block_kernel,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     const double pairs = (double)(l * (l - 1)) / 2.0;
     sweeps += run_sweeps(st, NB, 60, flag_dev, [&](int64_t r) {
-      jacobi_df_block_kernel<<<(unsigned)(NB / 2), 32 * JW, smem_df, st>>>(l, NB, r, B, ldb, tol,
-                                                                          flag_dev);
+      jacobi_df_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem_df, st>>>(l, NB, r, B, ldb,
+                                                                          (float)tol, flag_dev);
       APL_LAUNCH_CHECK();
-    }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l);
+    }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l, 1e-2 * std::sqrt(tol));
   } else if (l > 1) {
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
