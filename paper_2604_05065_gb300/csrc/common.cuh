@@ -122,6 +122,7 @@ struct DBuf {
 struct DenseWork {
   DBuf<double> splitk, qrtmp, jw64, jtmp, jw2;
   DBuf<float> jb32, jw32;
+  DBuf<float> gah, gal, gbh, gbl;  // hi / lo operands of the compensated GEMM
   bool fp64_gemm = false;  // GEMMs on the FP64 units instead of compensated FP32
 };
 DenseWork& dense_work();  // the workspace installed on the calling thread (throws if none)

@@ -58,22 +58,30 @@ __global__ void sketch_csc_kernel(int64_t n, const int* __restrict__ colptr,
 
 // ---- LUPP -----------------------------------------------------------------------------
 
+// A pivot candidate.  |value| is carried as its IEEE bit pattern: for non-negative
+// doubles the patterns order like the values, so every comparison and maximum of the
+// argmax reduction is an integer operation (GB300 issues FP64 compares at 1/64 of the
+// integer rate).  -1 marks "no candidate".
 struct Cand {
-  double v;   // |value| of the best candidate, -1 if none
-  int pos;    // its position in the current row order
-  double sec; // second-best |value|, -1 if none
+  long long v;    // bits of |value| of the best candidate, -1 if none
+  int pos;        // its position in the current row order
+  long long sec;  // bits of the second-best |value|, -1 if none
 };
 
-__device__ __forceinline__ bool cand_better(double v1, int p1, double v2, int p2) {
+__device__ __forceinline__ long long abs_key(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+
+__device__ __forceinline__ bool cand_better(long long v1, int p1, long long v2, int p2) {
   return v1 > v2 || (v1 == v2 && p1 < p2);
 }
 
 __device__ __forceinline__ Cand cand_merge(Cand a, Cand b) {
   Cand r;
   if (cand_better(a.v, a.pos, b.v, b.pos)) {
-    r.v = a.v; r.pos = a.pos; r.sec = fmax(a.sec, b.v);
+    r.v = a.v; r.pos = a.pos; r.sec = a.sec > b.v ? a.sec : b.v;
   } else {
-    r.v = b.v; r.pos = b.pos; r.sec = fmax(b.sec, a.v);
+    r.v = b.v; r.pos = b.pos; r.sec = b.sec > a.v ? b.sec : a.v;
   }
   return r;
 }
@@ -91,13 +99,13 @@ __device__ __forceinline__ Cand warp_cand(Cand c) {
 }
 
 __device__ Cand block_cand(Cand c) {
-  __shared__ double sv[32], ss[32];
+  __shared__ long long sv[32], ss[32];
   __shared__ int sp[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   c = warp_cand(c);
   if (lane == 0) { sv[wid] = c.v; sp[wid] = c.pos; ss[wid] = c.sec; }
   __syncthreads();
-  Cand r{-1.0, INT_MAX, -1.0};
+  Cand r{-1, INT_MAX, -1};
   if (wid == 0) {
     const int nw = (blockDim.x + 31) >> 5;
     if (lane < nw) { r.v = sv[lane]; r.pos = sp[lane]; r.sec = ss[lane]; }
@@ -129,9 +137,13 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
   double* xi = X + i * rs;
   double l = 0.0;
   __syncthreads();
-  if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] / prow[0];
+  // multipliers by the pivot's reciprocal, formed once per block (as LAPACK's getf2
+  // scales the column by 1 / pivot)
+  if (j > 0 && threadIdx.x == 0) prow[K - (j - 1)] = 1.0 / prow[0];
+  __syncthreads();
+  if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] * prow[K - (j - 1)];
   __syncthreads();  // every warp has read X(i, j-1) before it is overwritten
-  Cand mine{-1.0, INT_MAX, -1.0};
+  Cand mine{-1, INT_MAX, -1};
   if (live) {
     if (j > 0 && wid == 0) xi[(int64_t)(j - 1) * cs] = l;
     for (int64_t c = j + wid; c < K; c += nw) {
@@ -141,26 +153,27 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
         xi[c * cs] = v;
       }
       if (c == j) {
-        Cand cd{fabs(v), pos_of[i], -1.0};
+        Cand cd{abs_key(v), pos_of[i], -1};
         mine = cd;
       }
     }
   }
   Cand b = block_cand(mine);
   if (threadIdx.x == 0) {
-    pval[blockIdx.x] = b.v;
+    pval[blockIdx.x] = __longlong_as_double(b.v);
     ppos[blockIdx.x] = b.pos;
-    psec[blockIdx.x] = b.sec;
+    psec[blockIdx.x] = __longlong_as_double(b.sec);
   }
   if (!last_block_done(counter)) return;
-  Cand t{-1.0, INT_MAX, -1.0};
+  Cand t{-1, INT_MAX, -1};
   for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
-    Cand c{__ldcg(pval + q), __ldcg(ppos + q), __ldcg(psec + q)};
+    Cand c{__double_as_longlong(__ldcg(pval + q)), __ldcg(ppos + q),
+           __double_as_longlong(__ldcg(psec + q))};
     t = cand_merge(t, c);
   }
   t = block_cand(t);
   if (threadIdx.x == 0) {
-    if (!(t.v > 0.0)) {
+    if (!(t.v > 0)) {
       iscal[1] = 1;  // zero pivot (or no candidates): rank exhausted
     } else {
       const int pr = row_at[t.pos];
@@ -171,7 +184,10 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
       pos_of[pr] = j;
       piv[j] = pr;
       iscal[0] = j + 1;
-      if (t.sec >= 0.0) *margin = fmin(*margin, (t.v - t.sec) / t.v);
+      if (t.sec >= 0) {
+        const double tv = __longlong_as_double(t.v), ts = __longlong_as_double(t.sec);
+        *margin = fmin(*margin, (tv - ts) / tv);
+      }
     }
   }
 }

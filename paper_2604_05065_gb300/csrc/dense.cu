@@ -164,17 +164,31 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
   }
 }
 
-// The same tiling with compensated FP32 arithmetic: every FP64 operand is split into
-// FP32 hi + lo when its tile is staged (hi + lo keeps 48 of its 53 bits), a product is
-// formed exactly in its hi * hi part (an FMA gives the rounding error) plus the two cross
-// terms, and the running sum is an unevaluated FP32 pair updated by Knuth's TwoSum.  The
-// result is accurate to about 2^-46 relative to sum |a_i b_i| with only FP32 instructions,
-// which GB300 issues at 64 times its FP64 rate.
+// The same tiling with compensated FP32 arithmetic.  Every FP64 operand is split once per
+// call into FP32 hi + lo arrays (split_kernel; hi + lo keeps 48 of its 53 bits), a product
+// is formed exactly in its hi * hi part (an FMA gives the rounding error) plus the two
+// cross terms, and the running sum is an unevaluated FP32 pair updated by Knuth's TwoSum.
+// The result is accurate to about 2^-46 relative to sum |a_i b_i| and the inner loop has
+// only FP32 instructions, which GB300 issues at 64 times its FP64 rate.  The operands
+// arrive compact: op(A) source rows x cols with leading dimension = rows (same for B).
+__global__ void split_kernel(int64_t rows, int64_t cols, const double* __restrict__ src,
+                             int64_t ld, float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e % rows, c = e / rows;
+  const double v = src[r + c * ld];
+  const float h = __double2float_rn(v);
+  hi[e] = h;
+  lo[e] = __double2float_rn(v - (double)h);
+}
+
 __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, int64_t M,
                                                        int64_t N, int64_t K, double alpha,
-                                                       const double* __restrict__ A,
+                                                       const float* __restrict__ Ahi,
+                                                       const float* __restrict__ Alo,
                                                        int64_t lda,
-                                                       const double* __restrict__ B,
+                                                       const float* __restrict__ Bhi,
+                                                       const float* __restrict__ Blo,
                                                        int64_t ldb, double beta,
                                                        double* __restrict__ C, int64_t ldc,
                                                        int64_t kchunk,
@@ -198,19 +212,25 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
       int mm, kk;
       if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
-      double v = 0.0;
-      if (gm < M && gk < kend) v = transA ? A[gk + gm * lda] : A[gm + gk * lda];
-      const float vh = __double2float_rn(v);
+      float vh = 0.f, vl = 0.f;
+      if (gm < M && gk < kend) {
+        const int64_t o = transA ? gk + gm * lda : gm + gk * lda;
+        vh = Ahi[o];
+        vl = Alo[o];
+      }
       Ah[kk][mm] = vh;
-      Al[kk][mm] = __double2float_rn(v - (double)vh);
+      Al[kk][mm] = vl;
       int nn;
       if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
       const int64_t gn = n0 + nn, gk2 = k0 + kk;
-      double w = 0.0;
-      if (gn < N && gk2 < kend) w = transB ? B[gn + gk2 * ldb] : B[gk2 + gn * ldb];
-      const float wh = __double2float_rn(w);
+      float wh = 0.f, wl = 0.f;
+      if (gn < N && gk2 < kend) {
+        const int64_t o = transB ? gn + gk2 * ldb : gk2 + gn * ldb;
+        wh = Bhi[o];
+        wl = Blo[o];
+      }
       Bh[kk][nn] = wh;
-      Bl[kk][nn] = __double2float_rn(w - (double)wh);
+      Bl[kk][nn] = wl;
     }
     __syncthreads();
 #pragma unroll 4
@@ -294,6 +314,25 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   }
   const bool fp64 = dense_work().fp64_gemm;
   const int tok = prof_begin(st);
+  // compensated FP32: operands split once into compact hi / lo arrays
+  const float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
+  int64_t lda2 = lda, ldb2 = ldb;
+  if (!fp64) {
+    DenseWork& wk = dense_work();
+    const int64_t ar = transA ? K : M, ac = transA ? M : K;
+    const int64_t br = transB ? N : K, bc = transB ? K : N;
+    wk.gah.alloc((size_t)ar * ac, st);
+    wk.gal.alloc((size_t)ar * ac, st);
+    wk.gbh.alloc((size_t)br * bc, st);
+    wk.gbl.alloc((size_t)br * bc, st);
+    split_kernel<<<(unsigned)cdiv(ar * ac, 256), 256, 0, st>>>(ar, ac, A, lda, wk.gah.p, wk.gal.p);
+    APL_LAUNCH_CHECK();
+    split_kernel<<<(unsigned)cdiv(br * bc, 256), 256, 0, st>>>(br, bc, B, ldb, wk.gbh.p, wk.gbl.p);
+    APL_LAUNCH_CHECK();
+    Ah = wk.gah.p; Al = wk.gal.p; Bh = wk.gbh.p; Bl = wk.gbl.p;
+    lda2 = ar;
+    ldb2 = br;
+  }
   if (splits > 1) {
     const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
     splits = cdiv(K, kchunk);
@@ -303,8 +342,8 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
       dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
                                          ldc, kchunk, dense_work().splitk.p);
     else
-      df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
-                                            ldc, kchunk, dense_work().splitk.p);
+      df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, Ah, Al, lda2, Bh, Bl,
+                                            ldb2, 0.0, C, ldc, kchunk, dense_work().splitk.p);
     APL_LAUNCH_CHECK();
     splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
                                                                      dense_work().splitk.p, alpha, beta, C,
@@ -313,8 +352,8 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
                                        ldc, K, nullptr);
   } else {
-    df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta,
-                                          C, ldc, K, nullptr);
+    df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, Ah, Al, lda2, Bh, Bl,
+                                          ldb2, beta, C, ldc, K, nullptr);
   }
   APL_LAUNCH_CHECK();
   prof_end(st, tok, PROF_GEMM, 2.0 * (double)M * (double)N * (double)K);
