@@ -307,8 +307,8 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   // split K when the output tiles alone cannot fill the GPU (tall inner dimension)
   const int64_t tiles = (int64_t)grid.x * grid.y;
   int64_t splits = 1;
-  if (tiles < 2 * 152 && K >= 4 * 256) {
-    splits = std::min<int64_t>(cdiv(4 * 152, tiles), K / 256);
+  if (tiles < 2 * 152 && K >= 256) {
+    splits = std::min<int64_t>(cdiv(4 * 152, tiles), K / 128);
     splits = std::min<int64_t>(splits, 64);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, (int64_t)(1 << 24) / (M * N)));
   }
@@ -705,6 +705,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
                                             float* xch, int& rot) {
   float a = 0.f, b = 0.f, g = 0.f;
   if (valid) {
+#pragma unroll 4
     for (int64_t i = lane + 32 * half; i < l; i += 64) {
       const float x = cp[i], y = cq[i];
       a = fmaf(x, x, a);
@@ -731,6 +732,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
   t = zeta >= 0.f ? t : -t;
   const float c = rsqrtf(1.f + t * t), sn = c * t;
+#pragma unroll 4
   for (int64_t i = lane + 32 * half; i < l; i += 64) {
     const float x = cp[i], y = cq[i];
     cp[i] = c * x - sn * y;
@@ -912,6 +914,7 @@ __device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __r
                                             int half, float* xch, int& rot, float& mx) {
   float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, gs = 0.f, gc = 0.f;
   if (valid) {
+#pragma unroll 2
     for (int64_t i = lane + 32 * half; i < l; i += 64) {
       const float2 x = cp[i], y = cq[i];
       df_dot_add(as, ac, x.x, x.y, x.x, x.y);
