@@ -322,6 +322,65 @@ ALU = {3: (DF32_PEAK_TFLOPS, "derived compensated-FP32 ceiling: 152 SMs x 128 la
        6: (FP32_PEAK_TFLOPS, "nominal GB300 FP32 (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)")}
 
 
+def batched_measure(args, dev):
+    """The batched workload (uneven dense and CSR FP32 problems, 16 right-hand sides each,
+    mu 1e-5, sketch dimension 50): one warm-up and one timed APLICUR batch solve to the
+    time-to-tol target, then the same batch by plain LSQR with the same grouped kernels.
+    Throughput counts solved (problem, right-hand side) pairs per second."""
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+    from paper_2604_05065_gb300 import workloads as wl
+
+    nprob, R = args.batched_nprob, 16
+    t0 = time.perf_counter()
+    mats, rhs, sizes = wl.batched_device(dev, nprob=nprob, nrhs=R)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    abytes = sum(4 * m * n for (m, n, f) in sizes if f == "dense")
+    abytes += sum(8 * a.values().numel() for a, (m, n, f) in zip(mats, sizes) if f == "csr")
+    t0 = time.perf_counter()
+    s = pkg.BatchSolver(mats, rhs, 1e-5, 50, seed=1)
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"batched_{nprob}x{R}", "problems": nprob, "nrhs": R,
+           "note": ("the full 512-problem configuration" if nprob == 512 else
+                    f"{nprob} problems drawn by the 512-problem recipe (--batched-nprob 512 "
+                    "runs the full configuration)"),
+           "pairs": nprob * R, "a_bytes": int(abytes), "generate_s": round(gen_s, 2),
+           "create_s": round(create_s, 2)}
+
+    def timed(fn, warm=True):
+        if warm:
+            fn(TOL, args.maxit)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(TOL, args.maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0
+
+    secs = timed(s.solve)
+    st = s.stats()
+    out.update(solve_s=round(secs, 3), solves_per_s=round(nprob * R / secs, 2),
+               converged=st["converged"], ne_max=st["ne_max"], iters_max=st["iters_max"],
+               iters_sum=st["iters_sum"], ms_rank=round(st["time_rank_ms"], 1),
+               ms_build=round(st["time_build_ms"], 1), ms_lsqr=round(st["time_lsqr_ms"], 1),
+               tuned={"rows_per_warp": st["rows_per_warp"], "cols_per_lane": st["cols_per_lane"]},
+               launches_per_iter=st["launches_per_iter"])
+    if not args.no_plain:
+        psecs = timed(s.plain_lsqr, warm=False)  # kernels already warm from the solves
+        pst = s.stats()
+        out["plain_lsqr"] = {"solve_s": round(psecs, 3), "solves_per_s": round(nprob * R / psecs, 2),
+                             "converged": pst["converged"], "ne_max": pst["ne_max"],
+                             "iters_max": pst["iters_max"]}
+        out["speedup_vs_plain"] = round(psecs / secs, 3)
+    s.close()
+    return out
+
+
 def roofline(prof):
     nf = len(prof["ms"])
     k = max(range(nf), key=lambda q: prof["ms"][q])

@@ -47,3 +47,15 @@ def test_single_process_aggregate():
     import bench
     ms, v = bench.aggregate(500.0, steps=2, world=1)
     assert ms == 500.0 and v == pytest.approx(4.0)
+
+
+def test_bench_defines_every_leg():
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    for name in ("gpu_arm", "spmv_measure", "batched_measure", "roofline", "traffic_for",
+                 "oracle_sample", "reference_arm", "make_config", "aggregate"):
+        assert callable(getattr(mod, name)), name
