@@ -369,26 +369,39 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     if (h->A.fmt == 0) {
       gather_cols(st, h->A, h->Jp_d.p, k, nullptr, h->Cbuf.p + (int64_t)ell * m, m);
       append_rows(st, h->A, h->Ip_d.p, k, h->Rbuf.p, cap, ell);
-      dgemm(st, 1, 0, ln, k, m, 1.0, h->Cbuf.p, m, h->Cbuf.p + (int64_t)ell * m, m, 0.0, h->Gb.p, cap);
     } else {
       gather_cols(st, h->A, h->Jp_d.p, k, h->colpos_plus.p, h->Cp.p, m);
-      gram_csr(st, h->A, h->J_d.p, ln, h->Cp.p, k, h->Gb.p, cap);
     }
     set_map(st, h->rowpos.p, h->Ip_d.p, k, ell);
     set_map(st, h->colpos.p, h->Jp_d.p, k, ell);
     fill_int(st, h->colpos_plus.p, n, -1);
-    // ---- T_C: bordered Cholesky of C^T C
-    if (ell > 0) {
-      dtrsm(st, true, 'U', true, false, ell, k, h->TC.p, cap, h->Gb.p, cap);
-      dcopy2d(st, ell, k, h->Gb.p, cap, h->TC.p + (int64_t)ell * cap, cap, false);
-      dgemm(st, 1, 0, k, k, ell, -1.0, h->Gb.p, cap, h->Gb.p, cap, 1.0, h->Gb.p + ell, cap);
-    }
+    // ---- T_C: Gram of the new columns and bordered Cholesky of C^T C.  C^T C squares
+    // the condition of C: when the compensated-FP32 products leave a non-positive pivot
+    // the update is redone with FP64 products (a breakdown then is the FP64 one).
     double* T22 = h->TC.p + ell + (int64_t)ell * cap;
-    dcopy2d(st, k, k, h->Gb.p + ell, cap, T22, cap, false);
-    dpotrf_upper(st, k, T22, cap, h->info.p);
-    int info = 0;
-    APL_CUDA(cudaMemcpyAsync(&info, h->info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    APL_CUDA(cudaStreamSynchronize(st));
+    auto tc_update = [&]() -> int {
+      if (h->A.fmt == 0)
+        dgemm(st, 1, 0, ln, k, m, 1.0, h->Cbuf.p, m, h->Cbuf.p + (int64_t)ell * m, m, 0.0,
+              h->Gb.p, cap);
+      else
+        gram_csr(st, h->A, h->J_d.p, ln, h->Cp.p, k, h->Gb.p, cap);
+      if (ell > 0) {
+        dtrsm(st, true, 'U', true, false, ell, k, h->TC.p, cap, h->Gb.p, cap);
+        dcopy2d(st, ell, k, h->Gb.p, cap, h->TC.p + (int64_t)ell * cap, cap, false);
+        dgemm(st, 1, 0, k, k, ell, -1.0, h->Gb.p, cap, h->Gb.p, cap, 1.0, h->Gb.p + ell, cap);
+      }
+      dcopy2d(st, k, k, h->Gb.p + ell, cap, T22, cap, false);
+      dpotrf_upper(st, k, T22, cap, h->info.p);
+      int inf = 0;
+      APL_CUDA(cudaMemcpyAsync(&inf, h->info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      APL_CUDA(cudaStreamSynchronize(st));
+      return inf;
+    };
+    int info = tc_update();
+    if (info && !dense_work().fp64_gemm) {
+      Fp64Scope f64;
+      info = tc_update();
+    }
     if (info) throw Error(ST_EBREAKDOWN, "Cholesky of C^T C met a non-positive pivot");
     // ---- augmentQR(Q_R, T_R, A(I+, :)^T) with two Gram-Schmidt passes
     double* Cn = h->QR.p + (int64_t)ell * n;

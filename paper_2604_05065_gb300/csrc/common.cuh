@@ -126,6 +126,12 @@ struct DenseWork {
   bool fp64_gemm = false;  // GEMMs on the FP64 units instead of compensated FP32
 };
 DenseWork& dense_work();  // the workspace installed on the calling thread (throws if none)
+// Run the dense products of a scope on the FP64 units (retry of a breakdown).
+struct Fp64Scope {
+  bool prev;
+  Fp64Scope() : prev(dense_work().fp64_gemm) { dense_work().fp64_gemm = true; }
+  ~Fp64Scope() { dense_work().fp64_gemm = prev; }
+};
 struct DenseWorkScope {
   DenseWork* prev;
   explicit DenseWorkScope(DenseWork* w);

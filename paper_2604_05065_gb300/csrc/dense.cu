@@ -563,10 +563,18 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
   double* R1 = work + k * k;
   double* Ti = work + 2 * k * k;
   int info = 0;
-  dgemm(st, 1, 0, k, k, n, 1.0, E, lde, E, lde, 0.0, G, k);
-  dpotrf_upper(st, k, G, k, info_dev);
-  APL_CUDA(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-  APL_CUDA(cudaStreamSynchronize(st));
+  auto first_gram = [&]() {
+    dgemm(st, 1, 0, k, k, n, 1.0, E, lde, E, lde, 0.0, G, k);
+    dpotrf_upper(st, k, G, k, info_dev);
+    APL_CUDA(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    APL_CUDA(cudaStreamSynchronize(st));
+  };
+  first_gram();
+  if (info && !dense_work().fp64_gemm) {
+    // E is untouched so far: redo the first Gram with FP64 products
+    Fp64Scope f64;
+    first_gram();
+  }
   if (info) return false;
   dcopy2d(st, k, k, G, k, R1, k, false);
   right_upper_inverse_apply(st, n, k, E, lde, R1, k, Ti);
