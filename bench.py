@@ -364,6 +364,7 @@ def batched_measure(args, dev):
 
     secs = timed(s.solve)
     st = s.stats()
+    out["breakdowns"] = sum(1 for q in range(nprob) if s.problem(q)["breakdown"])
     out.update(solve_s=round(secs, 3), solves_per_s=round(nprob * R / secs, 2),
                converged=st["converged"], ne_max=st["ne_max"], iters_max=st["iters_max"],
                iters_sum=st["iters_sum"], ms_rank=round(st["time_rank_ms"], 1),

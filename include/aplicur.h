@@ -314,11 +314,12 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
                                     const aplicur_options* opt, void* stream);
 
 /* Solve every pair to the relative normal-equation residual tol (as aplicur_solve), at
- * most maxit LSQR iterations per pair.  After the rank steps, phases without the dynamic
+ * most maxit LSQR iterations per pair.  Unlike aplicur_solve, a breakdown in one problem
+ * does not fail the batch (see aplicur_batch_get_problem).  After the rank steps, phases without the dynamic
  * test continue until tol, the budget, 4 * max_extra_phases phases, or a phase that gains
  * less than 10%.  x_out: host array of nprob device pointers, each
  * n_p x nrhs FP64 column-major (overwritten).  ENOTCONV when a pair missed tol (x still
- * written); EBREAKDOWN when a preconditioner build of some problem broke down. */
+ * written). */
 aplicur_status aplicur_batch_solve(aplicur_batch_handle h, double tol, int64_t maxit,
                                    double* const* x_out);
 
@@ -330,11 +331,14 @@ aplicur_status aplicur_batch_plain_lsqr(aplicur_batch_handle h, double tol, int6
 aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t r,
                                       int64_t* iters, double* ne_res, int32_t* converged);
 
-/* CUR state of problem p after the last solve: rank, rank steps, phases, and the row
- * and column indices in selection order (I, J: host, >= ell entries, or NULL). */
+/* CUR state of problem p after the last solve: rank, rank steps, phases, whether a
+ * factorisation broke down (1: the Cholesky of C^T C or of the Q_R update met a non-positive
+ * pivot even with FP64 products; the problem's rank growth stopped there and its right-hand
+ * sides finished with the last preconditioner it had), and the row and column indices in
+ * selection order (I, J: host, >= ell entries, or NULL).  Any output may be NULL. */
 aplicur_status aplicur_batch_get_problem(aplicur_batch_handle h, int32_t p, int32_t* ell,
-                                         int32_t* nsteps, int32_t* nphases, int32_t* I,
-                                         int32_t* J);
+                                         int32_t* nsteps, int32_t* nphases, int32_t* broke,
+                                         int32_t* I, int32_t* J);
 
 aplicur_status aplicur_batch_get_stats(aplicur_batch_handle h, aplicur_batch_stats* st);
 

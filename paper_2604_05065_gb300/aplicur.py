@@ -99,7 +99,7 @@ SIGNATURES = {
     "aplicur_batch_solve": (C.c_int, [_VP, _D, _I64, _VP]),
     "aplicur_batch_plain_lsqr": (C.c_int, [_VP, _D, _I64, _VP]),
     "aplicur_batch_get_pair": (C.c_int, [_VP, _I32, _I32, C.POINTER(_I64), C.POINTER(_D), _PI32]),
-    "aplicur_batch_get_problem": (C.c_int, [_VP, _I32, _PI32, _PI32, _PI32, _VP, _VP]),
+    "aplicur_batch_get_problem": (C.c_int, [_VP, _I32, _PI32, _PI32, _PI32, _PI32, _VP, _VP]),
     "aplicur_batch_get_stats": (C.c_int, [_VP, C.POINTER(BatchStats)]),
     "aplicur_batch_last_error": (C.c_char_p, [_VP]),
     "aplicur_batch_destroy": (None, [_VP]),
@@ -533,14 +533,15 @@ class BatchSolver:
 
     def problem(self, p: int) -> dict:
         import numpy as np
-        ell, ns, nph = C.c_int32(), C.c_int32(), C.c_int32()
-        _check_b(self._lib, self._lib.aplicur_batch_get_problem(self._h, p, C.byref(ell), C.byref(ns),
-                                                                  C.byref(nph), None, None), self._h)
+        ell, ns, nph, br = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check_b(self._lib, self._lib.aplicur_batch_get_problem(
+            self._h, p, C.byref(ell), C.byref(ns), C.byref(nph), C.byref(br), None, None), self._h)
         I = np.zeros(max(ell.value, 1), np.int32)
         J = np.zeros(max(ell.value, 1), np.int32)
         _check_b(self._lib, self._lib.aplicur_batch_get_problem(
-            self._h, p, None, None, None, I.ctypes.data, J.ctypes.data), self._h)
+            self._h, p, None, None, None, None, I.ctypes.data, J.ctypes.data), self._h)
         return {"ell": ell.value, "nsteps": ns.value, "nphases": nph.value,
+                "breakdown": bool(br.value),
                 "I": I[:ell.value].astype(np.int64), "J": J[:ell.value].astype(np.int64)}
 
     def stats(self) -> dict:

@@ -1083,6 +1083,7 @@ struct aplicur_batch_ctx {
   std::vector<long long> iters;  // per pair p * R + r
   std::vector<double> ne;
   std::vector<char> conv;
+  std::vector<char> broke;       // per problem: a rank step or build broke down
   aplicur_batch_stats stats{};
   std::string err;
   int nthreads = 1;
@@ -1173,6 +1174,7 @@ int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
   h->iters.assign(npairs, 0);
   h->ne.assign(npairs, INFINITY);
   h->conv.assign(npairs, 0);
+  h->broke.assign(np, 0);
   h->stats.time_rank_ms = h->stats.time_build_ms = h->stats.time_lsqr_ms = 0.0;
   h->stats.time_check_ms = 0.0;
   h->eng.zero_x();
@@ -1208,7 +1210,17 @@ int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
         aplicur_ctx* c = h->pc[p];
         double rh = 0, mg = INFINITY;
         bool ex = false;
-        rank_step(c, &rh, &ex, &mg);
+        try {
+          rank_step(c, &rh, &ex, &mg);
+        } catch (const Error& e) {
+          // a breakdown ends this problem's rank growth; its pairs finish with the last
+          // preconditioner it built (or none)
+          if (e.code != ST_EBREAKDOWN) throw;
+          h->broke[p] = 1;
+          last[p] = 1;
+          rebuild[p] = 0;
+          return;
+        }
         const bool full = c->ell >= c->kmax;
         const double rho_eff = ex ? 0.0 : rh;
         last[p] = (rho_eff <= c->eps_cur || full || ex) ? 1 : 0;
@@ -1223,8 +1235,21 @@ int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
       for (int p : act)
         if (rebuild[p] && h->pc[p]->ell > 0) reb.push_back(p);
       t0 = clk::now();
-      parallel_for((int)reb.size(), h->nthreads, h->device,
-                   [&](int k) { build_preconditioner(h->pc[reb[k]]); });
+      parallel_for((int)reb.size(), h->nthreads, h->device, [&](int k) {
+        try {
+          build_preconditioner(h->pc[reb[k]]);
+        } catch (const Error& e) {
+          if (e.code != ST_EBREAKDOWN) throw;
+          h->broke[reb[k]] = 1;
+          last[reb[k]] = 1;
+        }
+      });
+      {
+        std::vector<int> ok;
+        for (int p : reb)
+          if (!h->broke[p]) ok.push_back(p);
+        reb.swap(ok);
+      }
       for (int p : reb) h->eng.set_precond(p, h->pc[p]->P);
       h->stats.time_build_ms += ms_since(t0);
       std::vector<char> mask(npairs, 0);
@@ -1403,10 +1428,11 @@ aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t
 }
 
 aplicur_status aplicur_batch_get_problem(aplicur_batch_handle h, int32_t p, int32_t* ell,
-                                         int32_t* nsteps, int32_t* nphases, int32_t* I,
-                                         int32_t* J) {
+                                         int32_t* nsteps, int32_t* nphases, int32_t* broke,
+                                         int32_t* I, int32_t* J) {
   if (!h || p < 0 || p >= h->np) return APLICUR_EINVAL;
   const aplicur_ctx* c = h->pc[p];
+  if (broke) *broke = h->broke.empty() ? 0 : h->broke[p];
   if (ell) *ell = c->ell;
   if (nsteps) *nsteps = (int32_t)c->steps.size();
   if (nphases) *nphases = (int32_t)c->phases.size();
