@@ -7,6 +7,7 @@
 #include <numeric>
 
 #include "dense.cuh"
+#include "df32.cuh"
 
 namespace apl {
 
@@ -368,7 +369,9 @@ constexpr int TNB = 64;
 
 // Solve T x = b for `nvec` vectors of length `len` (<= 64), one warp per vector; lane q
 // holds x_q and x_{q+32}.  T(r, c) = Tm[r * trs + c * tcs]; lower: forward substitution,
-// else backward.  Vector v element i at X[v * vstride + i * estride].
+// else backward.  Vector v element i at X[v * vstride + i * estride].  Column (axpy)
+// form: at step i the lane holding x_i finishes it, broadcasts it, and every lane removes
+// T(q, i) x_i from its later entries, so no step needs a warp reduction.
 __global__ void __launch_bounds__(256) trsv_block_kernel(int64_t nvec, int len,
                                                          double* __restrict__ X,
                                                          int64_t vstride, int64_t estride,
@@ -387,28 +390,96 @@ __global__ void __launch_bounds__(256) trsv_block_kernel(int64_t nvec, int len,
   double* x = X + v * vstride;
   double x0 = lane < len ? x[lane * estride] : 0.0;
   double x1 = lane + 32 < len ? x[(lane + 32) * estride] : 0.0;
+  const int c0 = lane, c1 = lane + 32;
   for (int t = 0; t < len; ++t) {
     const int i = lower ? t : len - 1 - t;
-    // dot over the already solved entries (c < i for lower, c > i for upper)
-    double part = 0.0;
-    const int c0 = lane, c1 = lane + 32;
-    if (lower) {
-      if (c0 < i) part = fma(Ts[i][c0], x0, part);
-      if (c1 < i) part = fma(Ts[i][c1], x1, part);
-    } else {
-      if (c0 > i && c0 < len) part = fma(Ts[i][c0], x0, part);
-      if (c1 > i && c1 < len) part = fma(Ts[i][c1], x1, part);
+    if (!unit && lane == (i & 31)) {
+      if (i < 32) x0 /= Ts[i][i]; else x1 /= Ts[i][i];
     }
-    part = warp_sum(part);
-    part = __shfl_sync(0xffffffffu, part, 0);
-    if (lane == (i & 31)) {
-      double& xi = (i < 32) ? x0 : x1;
-      const double s = xi - part;
-      xi = unit ? s : s / Ts[i][i];
+    const double xi = __shfl_sync(0xffffffffu, i < 32 ? x0 : x1, i & 31);
+    if (lower) {
+      if (c0 > i && c0 < len) x0 = fma(-Ts[c0][i], xi, x0);
+      if (c1 > i && c1 < len) x1 = fma(-Ts[c1][i], xi, x1);
+    } else {
+      if (c0 < i) x0 = fma(-Ts[c0][i], xi, x0);
+      if (c1 < i) x1 = fma(-Ts[c1][i], xi, x1);
     }
   }
   if (lane < len) x[lane * estride] = x0;
   if (lane + 32 < len) x[(lane + 32) * estride] = x1;
+}
+
+// The same solve in compensated FP32: T as FP32 hi/lo in shared memory, the diagonal's
+// reciprocals formed once in FP64 and split, x carried as hi/lo pairs; each update
+// x_q -= T(q, i) x_i is an exact hi product plus cross terms, combined by TwoSum (about
+// 2^-46 relative per operation), with no FP64 instruction in the substitution loop.
+__device__ __forceinline__ void df_mul_sub(float& xh, float& xl, float th, float tl, float yh,
+                                           float yl) {
+  // (xh, xl) -= (th + tl) (yh + yl)
+  const float p = __fmul_rn(th, yh);
+  const float e = __fmaf_rn(th, yh, -p);
+  const float cross = __fmaf_rn(th, yl, __fmul_rn(tl, yh));
+  float s1, e1;
+  df_two_sum(xh, -p, s1, e1);
+  const float lo = __fsub_rn(__fadd_rn(e1, xl), __fadd_rn(e, cross));
+  df_two_sum(s1, lo, xh, xl);
+}
+__device__ __forceinline__ void df_mul(float& xh, float& xl, float rh, float rl) {
+  const float p = __fmul_rn(xh, rh);
+  const float e = __fmaf_rn(xh, rh, -p);
+  const float lo = __fmaf_rn(xh, rl, __fmaf_rn(xl, rh, e));
+  df_two_sum(p, lo, xh, xl);
+}
+
+__global__ void __launch_bounds__(256) trsv_block_df_kernel(int64_t nvec, int len,
+                                                            double* __restrict__ X,
+                                                            int64_t vstride, int64_t estride,
+                                                            const double* __restrict__ Tm,
+                                                            int64_t trs, int64_t tcs, int lower,
+                                                            int unit) {
+  __shared__ float Th[TNB][TNB + 1], Tl[TNB][TNB + 1];
+  __shared__ float Rh[TNB], Rl[TNB];
+  for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
+    const int r = e % len, c = e / len;
+    const double v = Tm[r * trs + c * tcs];
+    const float h = __double2float_rn(v);
+    Th[r][c] = h;
+    Tl[r][c] = __double2float_rn(v - (double)h);
+  }
+  if (threadIdx.x < len) {
+    const double rv = unit ? 1.0 : 1.0 / Tm[threadIdx.x * trs + threadIdx.x * tcs];
+    const float h = __double2float_rn(rv);
+    Rh[threadIdx.x] = h;
+    Rl[threadIdx.x] = __double2float_rn(rv - (double)h);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (v >= nvec) return;
+  double* x = X + v * vstride;
+  const double d0 = lane < len ? x[lane * estride] : 0.0;
+  const double d1 = lane + 32 < len ? x[(lane + 32) * estride] : 0.0;
+  float x0h = __double2float_rn(d0), x0l = __double2float_rn(d0 - (double)x0h);
+  float x1h = __double2float_rn(d1), x1l = __double2float_rn(d1 - (double)x1h);
+  const int c0 = lane, c1 = lane + 32;
+  for (int t = 0; t < len; ++t) {
+    const int i = lower ? t : len - 1 - t;
+    if (!unit && lane == (i & 31)) {
+      if (i < 32) df_mul(x0h, x0l, Rh[i], Rl[i]);
+      else df_mul(x1h, x1l, Rh[i], Rl[i]);
+    }
+    const float yh = __shfl_sync(0xffffffffu, i < 32 ? x0h : x1h, i & 31);
+    const float yl = __shfl_sync(0xffffffffu, i < 32 ? x0l : x1l, i & 31);
+    if (lower) {
+      if (c0 > i && c0 < len) df_mul_sub(x0h, x0l, Th[c0][i], Tl[c0][i], yh, yl);
+      if (c1 > i && c1 < len) df_mul_sub(x1h, x1l, Th[c1][i], Tl[c1][i], yh, yl);
+    } else {
+      if (c0 < i) df_mul_sub(x0h, x0l, Th[c0][i], Tl[c0][i], yh, yl);
+      if (c1 < i) df_mul_sub(x1h, x1l, Th[c1][i], Tl[c1][i], yh, yl);
+    }
+  }
+  if (lane < len) x[lane * estride] = (double)x0h + (double)x0l;
+  if (lane + 32 < len) x[(lane + 32) * estride] = (double)x1h + (double)x1l;
 }
 
 // Pointer/trans to the sub-block op(A)[r0:, c0:] for use as a GEMM operand.
@@ -429,13 +500,21 @@ void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t
     int64_t rs = trans ? lda : 1, cs = trans ? 1 : lda;
     if (left) {
       const int64_t nvec = N;
-      trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
-          nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
+      if (dense_work().fp64_gemm)
+        trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
+            nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
+      else
+        trsv_block_df_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
+            nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
     } else {
       // X T = B  <=>  T^T x^T = b^T : matrix element (r, c) of T^T = T(c, r)
       const int64_t nvec = M;
-      trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
-          nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
+      if (dense_work().fp64_gemm)
+        trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
+            nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
+      else
+        trsv_block_df_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
+            nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
     }
     APL_LAUNCH_CHECK();
   };
@@ -845,11 +924,6 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
 // Singular values depend on the off-diagonal only to second order, so the threshold
 // (set above the dot-product noise, about 1e-12) leaves them accurate to rounding; the
 // vectors carry first-order errors at the threshold.
-__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bv = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
-}
 // (h, l) <- c * x with c = ch + cl and x = xh + xl
 __device__ __forceinline__ void df_scale(float ch, float cl, float xh, float xl, float& h,
                                          float& l) {

@@ -24,4 +24,11 @@ __device__ __forceinline__ void df_fma(DF& acc, float a, float h, float l) {
 
 __device__ __forceinline__ double df_val(const DF& a) { return (double)a.s + (double)a.c; }
 
+// Knuth's TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
 }  // namespace apl

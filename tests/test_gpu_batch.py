@@ -120,3 +120,20 @@ def test_batch_rejects_bad_arguments():
     A64 = A.double() if A.layout == torch.strided else A.to_dense().double()
     with pytest.raises(pkg.AplicurError):
         pkg.BatchSolver([A64], [b[:, :1]], MU, 8)  # FP64 values
+
+
+def test_batch_sixteen_rhs_matches_the_direct_solution():
+    """16 right-hand sides (the 16-wide kernel instances of the batched workload) on a
+    small uneven batch; every pair against the oracle's direct ridge solution."""
+    probs = wl.batched(nprob=4, m_range=(300, 700), n_range=(30, 70), density=0.03, nrhs=16,
+                       mu=MU, sketch_dim=8, seed=21)
+    sol = _solver(probs)
+    xs = sol.solve(1e-10)
+    assert sol.stats()["converged"] == 4 * 16
+    for p, prob in enumerate(probs):
+        A64 = _dense64(prob)
+        x = xs[p].cpu().numpy()
+        assert x.shape == (prob.n, 16)
+        for r in range(16):
+            _check_solution(x[:, r], A64, prob.b[:, r], MU, sol.pair(p, r)["ne_res"])
+    sol.close()
