@@ -168,7 +168,26 @@ __global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
       const float4* p1 = reinterpret_cast<const float4*>(a1);
       const float4* hv = reinterpret_cast<const float4*>(zh);
       const float4* lv = reinterpret_cast<const float4*>(zl);
-      for (int64_t q = lane; q < n4; q += 32) {
+      int64_t q = lane;
+      // two stretches per pass with every load issued first: 1 KB of A in flight per warp
+      for (; q + 32 < n4; q += 64) {
+        float4 x0[2], x1[2], h[2], l[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          x0[u] = __ldcs(p0 + q + 32 * u);
+          x1[u] = __ldcs(p1 + q + 32 * u);
+          h[u] = hv[q + 32 * u];
+          l[u] = MODE == 2 ? lv[q + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          s0.add(x0[u].x, 0.0, h[u].x, l[u].x); s0.add(x0[u].y, 0.0, h[u].y, l[u].y);
+          s0.add(x0[u].z, 0.0, h[u].z, l[u].z); s0.add(x0[u].w, 0.0, h[u].w, l[u].w);
+          s1.add(x1[u].x, 0.0, h[u].x, l[u].x); s1.add(x1[u].y, 0.0, h[u].y, l[u].y);
+          s1.add(x1[u].z, 0.0, h[u].z, l[u].z); s1.add(x1[u].w, 0.0, h[u].w, l[u].w);
+        }
+      }
+      for (; q < n4; q += 32) {
         const float4 x0 = __ldcs(p0 + q);
         const float4 x1 = __ldcs(p1 + q);
         const float4 h = hv[q];
@@ -340,7 +359,26 @@ __global__ void __launch_bounds__(NT) k2a_dense(int64_t m, int64_t n, int64_t ld
     const int64_t j = 4 * t;
     if (j + 3 < n) {
       Acc<MODE> a0, a1, a2, a3;
-      for (int64_t i = r0; i < r1; ++i) {
+      int64_t i = r0;
+      // four rows per pass with their loads issued first (same summation order)
+      for (; i + 3 < r1; i += 4) {
+        float4 x[4];
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = __ldcs(reinterpret_cast<const float4*>(A + (i + u) * ld + j));
+          h[u] = uh[i + u];
+          l[u] = MODE == 2 ? ul[i + u] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a0.add(x[u].x, 0.0, h[u], l[u]);
+          a1.add(x[u].y, 0.0, h[u], l[u]);
+          a2.add(x[u].z, 0.0, h[u], l[u]);
+          a3.add(x[u].w, 0.0, h[u], l[u]);
+        }
+      }
+      for (; i < r1; ++i) {
         const float4 x = __ldcs(reinterpret_cast<const float4*>(A + i * ld + j));
         const float h = uh[i];
         const float l = MODE == 2 ? ul[i] : 0.f;
