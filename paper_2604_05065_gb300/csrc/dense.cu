@@ -206,34 +206,50 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
 
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+  // the next K chunk is fetched into registers while the current one is multiplied
+  float pah[4], pal[4], pbh[4], pbl[4];
+  auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int lin = threadIdx.x + e * 256;
       int mm, kk;
       if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
-      float vh = 0.f, vl = 0.f;
+      pah[e] = 0.f;
+      pal[e] = 0.f;
       if (gm < M && gk < kend) {
         const int64_t o = transA ? gk + gm * lda : gm + gk * lda;
-        vh = Ahi[o];
-        vl = Alo[o];
+        pah[e] = Ahi[o];
+        pal[e] = Alo[o];
       }
-      Ah[kk][mm] = vh;
-      Al[kk][mm] = vl;
       int nn;
       if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
       const int64_t gn = n0 + nn, gk2 = k0 + kk;
-      float wh = 0.f, wl = 0.f;
+      pbh[e] = 0.f;
+      pbl[e] = 0.f;
       if (gn < N && gk2 < kend) {
         const int64_t o = transB ? gn + gk2 * ldb : gk2 + gn * ldb;
-        wh = Bhi[o];
-        wl = Blo[o];
+        pbh[e] = Bhi[o];
+        pbl[e] = Blo[o];
       }
-      Bh[kk][nn] = wh;
-      Bl[kk][nn] = wl;
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = threadIdx.x + e * 256;
+      int mm, kk;
+      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
+      Ah[kk][mm] = pah[e];
+      Al[kk][mm] = pal[e];
+      int nn;
+      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
+      Bh[kk][nn] = pbh[e];
+      Bl[kk][nn] = pbl[e];
     }
     __syncthreads();
+    if (k0 + GBK < kend) fetch(k0 + GBK);
 #pragma unroll 4
     for (int kk = 0; kk < GBK; ++kk) {
       float ah[4], al[4], bh[4], bl[4];
@@ -784,7 +800,7 @@ __device__ __forceinline__ float warp_allsumf(float v) {
 
 // One pair (p, q) handled by two warps (interleaved 32-element stretches); the dot
 // products meet in shared memory in half order so both warps take the same rotation.
-// All threads of the block call this (three synchronisations).  Half 0 also rotates the
+// All threads of the block call this (two synchronisations).  Half 0 also rotates the
 // columns p, q of the accumulated rotation R.
 __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __restrict__ cq,
                                             float* __restrict__ R, int p, int q, bool valid,
@@ -808,7 +824,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   a = xch[0] + xch[3];
   b = xch[1] + xch[4];
   g = xch[2] + xch[5];
-  __syncthreads();
+  // no barrier before xch is written again: that happens after the closing barrier below
   if (!(valid && a > 0.f && b > 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b))) {
     __syncthreads();
     return;
@@ -989,8 +1005,8 @@ __device__ __forceinline__ void df_rsqrt(float vh, float vl, float& ch, float& c
 // order, so both warps form the same rotation.  The angle comes from FP32 arithmetic on
 // the compensated sums (an approximate angle only slows convergence); its cosine and sine
 // are formed as pairs with c^2 + s^2 = 1 to about 2^-46, so every rotation is orthogonal
-// to that accuracy.  All threads of the block must call this: it synchronises three
-// times (dot exchange, exchange reuse, end of the rotation).
+// to that accuracy.  All threads of the block must call this: it synchronises twice
+// (dot exchange, end of the rotation).
 __device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __restrict__ cq,
                                             bool valid, int64_t l, float tol, int lane,
                                             int half, float* xch, int& rot, float& mx) {
@@ -1016,7 +1032,7 @@ __device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __r
   df_add(A, Al, xch[6], xch[7]);
   df_add(Bv, Bl, xch[8], xch[9]);
   df_add(G, Gl, xch[10], xch[11]);
-  __syncthreads();  // xch is reused by the next inner round
+  // no barrier before xch is written again: that happens after the closing barrier below
   const float relg = (valid && A > 0.f && Bv > 0.f) ? fabsf(G) / (sqrtf(A) * sqrtf(Bv)) : 0.f;
   if (!(relg > tol)) {
     __syncthreads();  // the next inner round reads columns other warps may still rotate
