@@ -29,7 +29,6 @@ namespace apl {
 namespace {
 
 constexpr int NT = 256;
-constexpr int CSC_LANES = 8;  // lanes per column in the CSC A^T u pass
 
 __device__ __forceinline__ void split(double v, float* hi, float* lo, int64_t i) {
   const float h = __double2float_rn(v);
@@ -322,30 +321,16 @@ __global__ void __launch_bounds__(NT) k2_csr(int64_t m, int64_t n, const int* __
   if (ctl->done) return;
   const double us = ctl->us, delta = ctl->delta;
   double ss = 0.0;
-  // CSC_LANES consecutive lanes share a column (strided over its nonzeros, then a shuffle
-  // tree in fixed order), so short columns still give the GPU enough threads
-  const int sub = threadIdx.x % CSC_LANES;
-  const int64_t per_pass = (int64_t)gridDim.x * (NT / CSC_LANES);
-  const int64_t jfirst = (int64_t)blockIdx.x * (NT / CSC_LANES) + threadIdx.x / CSC_LANES;
-  const int64_t jspan = (n + per_pass - 1) / per_pass * per_pass;  // uniform trip count
-  for (int64_t j = jfirst; j < jspan; j += per_pass) {
-    const bool ok = j < n;
+  for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
     Acc<MODE> acc;
-    if (ok) {
-      const int e1 = colptr[j + 1];
-      for (int e = colptr[j] + sub; e < e1; e += CSC_LANES) {
-        const int r = rowidx[e];
-        if constexpr (MODE == 0) acc.add((double)cvals[e], u[r], 0.f, 0.f);
-        else acc.add((float)cvals[e], 0.0, uh[r], MODE == 2 ? ul[r] : 0.f);
-      }
+    const int e1 = colptr[j + 1];
+    for (int e = colptr[j]; e < e1; ++e) {
+      const int r = rowidx[e];
+      if constexpr (MODE == 0) acc.add((double)cvals[e], u[r], 0.f, 0.f);
+      else acc.add((float)cvals[e], 0.0, uh[r], MODE == 2 ? ul[r] : 0.f);
     }
-    double part = acc.get();
-#pragma unroll
-    for (int o = CSC_LANES / 2; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o, CSC_LANES);
-    if (ok && sub == 0) {
-      const double gj = us * (part + delta * u[m + j]);
-      ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x, zh, zl);
-    }
+    const double gj = us * (acc.get() + delta * u[m + j]);
+    ss += k2_tail(j, gj, ctl, init, fused, g, v, z, d, x, zh, zl);
   }
   if (!fused) return;
   const double b = block_sum(ss, sh);
@@ -787,9 +772,11 @@ void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_it
     k2_blocks_ = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
     part_.alloc((size_t)k2_rchunks_ * n_, st);
   } else {
-    // two rows per thread halve the FP64 block reductions (FP64 issues at 1/64 rate)
+    // two rows per thread halve the FP64 block reductions (FP64 issues at 1/64 rate); the
+    // CSC pass keeps one column per thread: splitting a column over lanes adds FP64
+    // shuffle-reductions, which cost more than the latency they hide
     k1_blocks_ = (int)std::min<int64_t>(cdiv(m_ + n_, 2 * NT), sm_blocks());
-    k2_blocks_ = (int)std::min<int64_t>(cdiv(n_ * CSC_LANES, NT), sm_blocks());
+    k2_blocks_ = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
   }
   red_cap_ = sm_blocks() + 64;
   red_.alloc(red_cap_, st);
