@@ -782,15 +782,19 @@ namespace {
 // FP32 stage, block-cyclic: the l columns form NB (even) blocks of JW columns; in block
 // round r the blocks form NB/2 disjoint pairs (round robin) and one CTA takes one pair.
 // The CTA holds its 2 JW columns in shared memory and rotates every (P-column, Q-column)
-// pair in JW inner rounds of JW disjoint pairs (one warp per pair); in block round 0 it
+// pair in JW inner rounds of JW disjoint pairs (two warps per pair); in block round 0 it
 // first rotates the pairs inside P and inside Q.  Over the NB - 1 block rounds of a sweep
 // every pair of columns meets once, as in a scalar cyclic sweep.  The rotations are
 // accumulated in a 2JW x 2JW matrix R and applied to the matching columns of W at the
 // end (W <- W R).  Angles are computed in FP32: this stage only has to bring the columns
-// close to orthogonal; the FP64 stage decides the accuracy.
+// close to orthogonal; the second (compensated or FP64) stage decides the accuracy.
 constexpr int JW = 8;
 constexpr int JW2 = 2 * JW;
 constexpr int kJac32SmemCap = 220 * 1024;  // dynamic shared memory cap of the FP32 stage
+
+// Column stride of the FP32 stage's shared copy: l rounded up to a multiple of 4, so every
+// column starts on a 16-byte boundary and is read as float4; the pad holds zeros.
+inline int64_t jac32_ld(int64_t l) { return (l + 3) & ~int64_t(3); }
 
 __device__ __forceinline__ float warp_allsumf(float v) {
 #pragma unroll
@@ -798,48 +802,84 @@ __device__ __forceinline__ float warp_allsumf(float v) {
   return v;
 }
 
-// One pair (p, q) handled by two warps (interleaved 32-element stretches); the dot
-// products meet in shared memory in half order so both warps take the same rotation.
-// All threads of the block call this (two synchronisations).  Half 0 also rotates the
-// columns p, q of the accumulated rotation R.
+// Barrier of the two warps (64 threads) of pair slot pw; id 0 is __syncthreads'.
+__device__ __forceinline__ void pair_bar(int pw) {
+  asm volatile("bar.sync %0, 64;" ::"r"(pw + 1) : "memory");
+}
+
+// One pair (p, q) handled by two warps (interleaved float4 stretches).  Only g = x^T y is
+// a dot product: the squared norms a, b of the CTA's columns live in nrm and follow the
+// rotation exactly in exact arithmetic (a - t g, b + t g); a norm that the update would
+// lose to cancellation (below 1/16 of its old value) is summed again from the rotated
+// column.  The two warps meet at their own named barrier and add their halves in the
+// same order, so both take the same rotation.  All threads of the block call this; it
+// ends with a block-wide barrier, since the next inner round reads columns that other
+// pairs rotated.  Half 0 also rotates the columns p, q of the accumulated rotation R.
 __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __restrict__ cq,
-                                            float* __restrict__ R, int p, int q, bool valid,
-                                            int64_t l, float tol, int lane, int half,
-                                            float* xch, int& rot) {
-  float a = 0.f, b = 0.f, g = 0.f;
+                                            float* __restrict__ R, float* __restrict__ nrm,
+                                            int p, int q, bool valid, int64_t n4, float tol,
+                                            int lane, int half, int pw, float* xch, int& rot,
+                                            float& mx) {
+  float4* p4 = reinterpret_cast<float4*>(cp);
+  float4* q4 = reinterpret_cast<float4*>(cq);
+  float g0 = 0.f, g1 = 0.f;
   if (valid) {
-#pragma unroll 4
-    for (int64_t i = lane + 32 * half; i < l; i += 64) {
-      const float x = cp[i], y = cq[i];
-      a = fmaf(x, x, a);
-      b = fmaf(y, y, b);
-      g = fmaf(x, y, g);
+#pragma unroll 2
+    for (int64_t k = lane + 32 * half; k < n4; k += 64) {
+      const float4 x = p4[k], y = q4[k];
+      g0 = fmaf(x.x, y.x, g0);
+      g1 = fmaf(x.y, y.y, g1);
+      g0 = fmaf(x.z, y.z, g0);
+      g1 = fmaf(x.w, y.w, g1);
     }
   }
-  a = warp_allsumf(a);
-  b = warp_allsumf(b);
-  g = warp_allsumf(g);
-  if (lane == 0) { xch[3 * half] = a; xch[3 * half + 1] = b; xch[3 * half + 2] = g; }
-  __syncthreads();
-  a = xch[0] + xch[3];
-  b = xch[1] + xch[4];
-  g = xch[2] + xch[5];
+  float g = warp_allsumf(g0 + g1);
+  if (lane == 0) xch[half] = g;
+  pair_bar(pw);
+  g = xch[0] + xch[1];
+  const float a = nrm[p], b = nrm[q];
   // no barrier before xch is written again: that happens after the closing barrier below
-  if (!(valid && a > 0.f && b > 0.f && fabsf(g) > tol * sqrtf(a) * sqrtf(b))) {
+  const float relg = (valid && a > 0.f && b > 0.f) ? fabsf(g) / (sqrtf(a) * sqrtf(b)) : 0.f;
+  if (!(relg > tol)) {
     __syncthreads();
     return;
   }
+  mx = fmaxf(mx, relg);
   const float zeta = (b - a) / (2.f * g);
   const float az = fabsf(zeta);
   // tan of the rotation angle, the smaller root; 1 / (2 zeta) once zeta^2 would overflow
   float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
   t = zeta >= 0.f ? t : -t;
   const float c = rsqrtf(1.f + t * t), sn = c * t;
-#pragma unroll 4
-  for (int64_t i = lane + 32 * half; i < l; i += 64) {
-    const float x = cp[i], y = cq[i];
-    cp[i] = c * x - sn * y;
-    cq[i] = sn * x + c * y;
+  float na = a - t * g, nb = b + t * g;
+  const bool refresh = !(na >= 0.0625f * a) || !(nb >= 0.0625f * b);
+  float sa = 0.f, sb = 0.f;
+#pragma unroll 2
+  for (int64_t k = lane + 32 * half; k < n4; k += 64) {
+    const float4 x = p4[k], y = q4[k];
+    float4 u, v;
+    u.x = c * x.x - sn * y.x;
+    u.y = c * x.y - sn * y.y;
+    u.z = c * x.z - sn * y.z;
+    u.w = c * x.w - sn * y.w;
+    v.x = sn * x.x + c * y.x;
+    v.y = sn * x.y + c * y.y;
+    v.z = sn * x.z + c * y.z;
+    v.w = sn * x.w + c * y.w;
+    p4[k] = u;
+    q4[k] = v;
+    if (refresh) {
+      sa = fmaf(u.x, u.x, fmaf(u.y, u.y, fmaf(u.z, u.z, fmaf(u.w, u.w, sa))));
+      sb = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sb))));
+    }
+  }
+  if (refresh) {  // the same decision on both warps of the pair
+    sa = warp_allsumf(sa);
+    sb = warp_allsumf(sb);
+    if (lane == 0) { xch[2 + 2 * half] = sa; xch[3 + 2 * half] = sb; }
+    pair_bar(pw);
+    na = xch[2] + xch[4];
+    nb = xch[3] + xch[5];
   }
   if (half == 0) {
     if (lane < JW2) {
@@ -847,22 +887,27 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
       R[lane * JW2 + p] = c * u - sn * v;
       R[lane * JW2 + q] = sn * u + c * v;
     }
+    if (lane == 0) { nrm[p] = na; nrm[q] = nb; }
     ++rot;
   }
   __syncthreads();
 }
 
-// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory JW2 * l
-// floats + R
+// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory
+// JW2 * jac32_ld(l) floats + R.  rotated[0] counts rotations, rotated[1] holds the largest
+// rotated |cos| of the sweep (as float bits; non-negative floats order like their bits).
 __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int64_t NB,
                                                                  int64_t r, float* __restrict__ B,
                                                                  float* __restrict__ W,
                                                                  float tol, int* rotated) {
-  extern __shared__ float jsm[];
-  float* cols = jsm;                  // JW2 columns of length l
-  float* R = jsm + (size_t)JW2 * l;   // JW2 x JW2, row-major R[row * JW2 + col]
+  extern __shared__ __align__(16) float jsm[];
+  const int64_t ls = (l + 3) & ~int64_t(3);
+  float* cols = jsm;                   // JW2 columns of stride ls
+  float* R = jsm + (size_t)JW2 * ls;   // JW2 x JW2, row-major R[row * JW2 + col]
   __shared__ int gcol[JW2];
+  __shared__ float nrm[JW2];
   __shared__ int cta_rot;
+  __shared__ unsigned int cta_max;
   __shared__ float xch[JW][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pw = warp >> 1, half = warp & 1;
@@ -873,9 +918,12 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
     const int64_t c = blk * JW + (threadIdx.x % JW);
     gcol[threadIdx.x] = c < l ? (int)c : -1;
   }
-  if (threadIdx.x == 0) cta_rot = 0;
+  if (threadIdx.x == 0) { cta_rot = 0; cta_max = 0u; }
   for (int e = threadIdx.x; e < JW2 * JW2; e += blockDim.x)
     R[e] = (e / JW2 == e % JW2) ? 1.f : 0.f;
+  const int pad = (int)(ls - l);
+  for (int e = threadIdx.x; e < JW2 * pad; e += blockDim.x)
+    cols[(size_t)(e / pad) * ls + l + e % pad] = 0.f;
   __syncthreads();
   // one row index per thread and pass, all JW2 column loads in flight together
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
@@ -883,10 +931,25 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
 #pragma unroll
     for (int c = 0; c < JW2; ++c) v[c] = gcol[c] >= 0 ? B[(int64_t)gcol[c] * l + i] : 0.f;
 #pragma unroll
-    for (int c = 0; c < JW2; ++c) cols[(size_t)c * l + i] = v[c];
+    for (int c = 0; c < JW2; ++c) cols[(size_t)c * ls + i] = v[c];
+  }
+  __syncthreads();
+  const int64_t n4 = ls / 4;
+  {
+    // squared column norms, one warp per column (the block has JW2 warps)
+    const float4* c4 = reinterpret_cast<const float4*>(cols + (size_t)warp * ls);
+    float s0 = 0.f, s1 = 0.f;
+    for (int64_t q = lane; q < n4; q += 32) {
+      const float4 x = c4[q];
+      s0 = fmaf(x.x, x.x, fmaf(x.z, x.z, s0));
+      s1 = fmaf(x.y, x.y, fmaf(x.w, x.w, s1));
+    }
+    const float s = warp_allsumf(s0 + s1);
+    if (lane == 0) nrm[warp] = s;
   }
   __syncthreads();
   int rot = 0;
+  float mx = 0.f;
   if (r == 0) {
     // pairs inside each block: JW - 1 round-robin rounds of JW/2 pairs per block
     for (int ir = 0; ir < JW - 1; ++ir) {
@@ -895,26 +958,32 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
       if (p > q) { const int z = p; p = q; q = z; }
       p += side * JW;
       q += side * JW;
-      jac32_pair2(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q,
-                  gcol[p] >= 0 && gcol[q] >= 0, l, tol, lane, half, xch[pw], rot);
+      jac32_pair2(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
+                  gcol[p] >= 0 && gcol[q] >= 0, n4, tol, lane, half, pw, xch[pw], rot, mx);
     }
   }
   for (int ir = 0; ir < JW; ++ir) {
     const int p = pw, q = JW + (pw + ir) % JW;
-    jac32_pair2(cols + (size_t)p * l, cols + (size_t)q * l, R, p, q,
-                gcol[p] >= 0 && gcol[q] >= 0, l, tol, lane, half, xch[pw], rot);
+    jac32_pair2(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
+                gcol[p] >= 0 && gcol[q] >= 0, n4, tol, lane, half, pw, xch[pw], rot, mx);
   }
-  if (lane == 0 && rot) atomicAdd(&cta_rot, rot);
+  if (lane == 0 && half == 0 && rot) {
+    atomicAdd(&cta_rot, rot);
+    atomicMax(&cta_max, __float_as_uint(mx));
+  }
   __syncthreads();
   if (cta_rot == 0) return;
-  if (threadIdx.x == 0) atomicAdd(rotated, cta_rot);
+  if (threadIdx.x == 0) {
+    atomicAdd(rotated, cta_rot);
+    atomicMax(reinterpret_cast<unsigned int*>(rotated + 1), cta_max);
+  }
   // write back the columns and W(:, cols) <- W(:, cols) R, one row per thread and pass,
   // the 16 outputs in two halves of 8 to bound registers
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     float w[JW2];
 #pragma unroll
     for (int c = 0; c < JW2; ++c) {
-      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * l + i];
+      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * ls + i];
       w[c] = gcol[c] >= 0 ? W[(int64_t)gcol[c] * l + i] : 0.f;
     }
 #pragma unroll
@@ -934,9 +1003,8 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
 }
 
 // Stage 2 in compensated FP32, block-cyclic like stage 1: the CTA's 16 columns live in
-// shared memory as FP32 hi/lo pairs (48 of the 53 bits of B); the three dot products of a
-// pair are summed as unevaluated FP32 pairs (TwoSum) and the angle is formed in FP64 from
-// them, so c^2 + s^2 = 1 to FP64 accuracy; the rotation is applied in compensated FP32.
+// shared memory as FP32 hi/lo pairs (48 of the 53 bits of B); dot products are summed as
+// unevaluated FP32 pairs (TwoSum) and the rotation is applied in compensated FP32.
 // Singular values depend on the off-diagonal only to second order, so the threshold
 // (set above the dot-product noise, about 1e-12) leaves them accurate to rounding; the
 // vectors carry first-order errors at the threshold.
@@ -1000,38 +1068,54 @@ __device__ __forceinline__ void df_rsqrt(float vh, float vl, float& ch, float& c
   cl = yl;
 }
 
-// One pair (p, q) of columns handled by two warps (half 0 and half 1 take interleaved
-// 32-element stretches); the compensated dot products meet in shared memory in half
-// order, so both warps form the same rotation.  The angle comes from FP32 arithmetic on
-// the compensated sums (an approximate angle only slows convergence); its cosine and sine
-// are formed as pairs with c^2 + s^2 = 1 to about 2^-46, so every rotation is orthogonal
-// to that accuracy.  All threads of the block must call this: it synchronises twice
-// (dot exchange, end of the rotation).
-__device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __restrict__ cq,
-                                            bool valid, int64_t l, float tol, int lane,
-                                            int half, float* xch, int& rot, float& mx) {
-  float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, gs = 0.f, gc = 0.f;
+// x' = c x - s y and y' = s x + c y for one hi/lo element, c = (ch, cl), s = (sh, sl)
+__device__ __forceinline__ void df_rotate(float ch, float cl, float sh, float sl, float xh,
+                                          float xl, float yh, float yl, float& uh, float& ul,
+                                          float& vh, float& vl) {
+  float cxh, cxl, syh, syl, sxh, sxl, cyh, cyl;
+  df_scale(ch, cl, xh, xl, cxh, cxl);
+  df_scale(sh, sl, yh, yl, syh, syl);
+  df_scale(sh, sl, xh, xl, sxh, sxl);
+  df_scale(ch, cl, yh, yl, cyh, cyl);
+  float r, er;
+  df_two_sum(cxh, -syh, r, er);
+  df_two_sum(r, __fadd_rn(er, __fsub_rn(cxl, syl)), uh, ul);
+  df_two_sum(sxh, cyh, r, er);
+  df_two_sum(r, __fadd_rn(er, __fadd_rn(sxl, cyl)), vh, vl);
+}
+
+// One pair (p, q) of columns handled by two warps (interleaved stretches of float4 = two
+// hi/lo elements).  Only g = x^T y is a compensated dot product: the squared norms, kept
+// as pairs (nh, nl) for the CTA's columns, follow the rotation as a - t g and b + t g.
+// That is exact for the exact root t; the FP32 t is off only to second order in its
+// rounding, as the angle is a stationary point of |x'|^2.  A norm that the update would
+// lose to cancellation (below 1/16 of its old value) is summed again from the rotated
+// column.  The halves meet at the pair's own named barrier and add in half order, so both
+// warps form the same rotation.  The angle comes from FP32 arithmetic on the compensated
+// sums (an approximate angle only slows convergence); its cosine and sine are formed as
+// pairs with c^2 + s^2 = 1 to about 2^-46, so every rotation is orthogonal to that
+// accuracy.  All threads of the block call this; it ends with a block-wide barrier.
+__device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __restrict__ cq,
+                                            float* __restrict__ nh, float* __restrict__ nl,
+                                            int p, int q, bool valid, int64_t n2, float tol,
+                                            int lane, int half, int pw, float* xch, int& rot,
+                                            float& mx) {
+  float gs = 0.f, gc = 0.f, hs = 0.f, hc = 0.f;
   if (valid) {
 #pragma unroll 2
-    for (int64_t i = lane + 32 * half; i < l; i += 64) {
-      const float2 x = cp[i], y = cq[i];
-      df_dot_add(as, ac, x.x, x.y, x.x, x.y);
-      df_dot_add(bs, bc, y.x, y.y, y.x, y.y);
+    for (int64_t k = lane + 32 * half; k < n2; k += 64) {
+      const float4 x = cp[k], y = cq[k];
       df_dot_add(gs, gc, x.x, x.y, y.x, y.y);
+      df_dot_add(hs, hc, x.z, x.w, y.z, y.w);
     }
   }
-  df_warp_allsum(as, ac);
-  df_warp_allsum(bs, bc);
+  df_add(gs, gc, hs, hc);
   df_warp_allsum(gs, gc);
-  if (lane == 0) {
-    float* o = xch + 6 * half;
-    o[0] = as; o[1] = ac; o[2] = bs; o[3] = bc; o[4] = gs; o[5] = gc;
-  }
-  __syncthreads();
-  float A = xch[0], Al = xch[1], Bv = xch[2], Bl = xch[3], G = xch[4], Gl = xch[5];
-  df_add(A, Al, xch[6], xch[7]);
-  df_add(Bv, Bl, xch[8], xch[9]);
-  df_add(G, Gl, xch[10], xch[11]);
+  if (lane == 0) { xch[2 * half] = gs; xch[2 * half + 1] = gc; }
+  pair_bar(pw);
+  float G = xch[0], Gl = xch[1];
+  df_add(G, Gl, xch[2], xch[3]);
+  const float A = nh[p], Al = nl[p], Bv = nh[q], Bl = nl[q];
   // no barrier before xch is written again: that happens after the closing barrier below
   const float relg = (valid && A > 0.f && Bv > 0.f) ? fabsf(G) / (sqrtf(A) * sqrtf(Bv)) : 0.f;
   if (!(relg > tol)) {
@@ -1056,34 +1140,65 @@ __device__ __forceinline__ void jacdf_pair2(float2* __restrict__ cp, float2* __r
   df_rsqrt(vh, vl, ch, cl);
   const float sh = __fmul_rn(ch, t);
   const float sl = __fmaf_rn(cl, t, __fmaf_rn(ch, t, -sh));
-  for (int64_t i = lane + 32 * half; i < l; i += 64) {
-    const float2 x = cp[i], y = cq[i];
-    float cxh, cxl, syh, syl, sxh, sxl, cyh, cyl;
-    df_scale(ch, cl, x.x, x.y, cxh, cxl);
-    df_scale(sh, sl, y.x, y.y, syh, syl);
-    df_scale(sh, sl, x.x, x.y, sxh, sxl);
-    df_scale(ch, cl, y.x, y.y, cyh, cyl);
-    float r, er, h2, l2;
-    df_two_sum(cxh, -syh, r, er);  // x' = c x - s y
-    df_two_sum(r, __fadd_rn(er, __fsub_rn(cxl, syl)), h2, l2);
-    cp[i] = make_float2(h2, l2);
-    df_two_sum(sxh, cyh, r, er);   // y' = s x + c y
-    df_two_sum(r, __fadd_rn(er, __fadd_rn(sxl, cyl)), h2, l2);
-    cq[i] = make_float2(h2, l2);
+  // t g as a pair, then the updated norms
+  const float tg = __fmul_rn(t, G);
+  const float tgl = __fmaf_rn(t, Gl, __fmaf_rn(t, G, -tg));
+  float NA = A, NAl = Al, NB = Bv, NBl = Bl;
+  df_add(NA, NAl, -tg, -tgl);
+  df_add(NB, NBl, tg, tgl);
+  const bool refresh = !(NA >= 0.0625f * A) || !(NB >= 0.0625f * Bv);
+  float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f;
+#pragma unroll 2
+  for (int64_t k = lane + 32 * half; k < n2; k += 64) {
+    const float4 x = cp[k];
+    const float4 y = cq[k];
+    float4 u, v;
+    df_rotate(ch, cl, sh, sl, x.x, x.y, y.x, y.y, u.x, u.y, v.x, v.y);
+    df_rotate(ch, cl, sh, sl, x.z, x.w, y.z, y.w, u.z, u.w, v.z, v.w);
+    cp[k] = u;
+    cq[k] = v;
+    if (refresh) {
+      df_dot_add(as, ac, u.x, u.y, u.x, u.y);
+      df_dot_add(as, ac, u.z, u.w, u.z, u.w);
+      df_dot_add(bs, bc, v.x, v.y, v.x, v.y);
+      df_dot_add(bs, bc, v.z, v.w, v.z, v.w);
+    }
   }
-  if (half == 0) ++rot;
+  if (refresh) {  // the same decision on both warps of the pair
+    df_warp_allsum(as, ac);
+    df_warp_allsum(bs, bc);
+    if (lane == 0) {
+      float* o = xch + 4 + 4 * half;
+      o[0] = as; o[1] = ac; o[2] = bs; o[3] = bc;
+    }
+    pair_bar(pw);
+    NA = xch[4]; NAl = xch[5];
+    df_add(NA, NAl, xch[8], xch[9]);
+    NB = xch[6]; NBl = xch[7];
+    df_add(NB, NBl, xch[10], xch[11]);
+  }
+  if (half == 0) {
+    if (lane == 0) { nh[p] = NA; nl[p] = NAl; nh[q] = NB; nl[q] = NBl; }
+    ++rot;
+  }
   __syncthreads();
 }
 
-// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory JW2 * l
-// float2.  rotated[0] counts rotations, rotated[1] holds the largest rotated |cos| of the
-// sweep (as float bits; non-negative floats order like their bits).
+// Column stride (in hi/lo elements) of the compensated stage's shared copy: l rounded up
+// to even, so every column starts on a 16-byte boundary; the pad holds zeros.
+inline int64_t jacdf_ld(int64_t l) { return (l + 1) & ~int64_t(1); }
+
+// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory
+// JW2 * jacdf_ld(l) float2.  rotated[0] counts rotations, rotated[1] holds the largest
+// rotated |cos| of the sweep (as float bits; non-negative floats order like their bits).
 __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int64_t NB,
                                                                   int64_t r, double* __restrict__ B,
                                                                   int64_t ldb, float tol,
                                                                   int* rotated) {
-  extern __shared__ float2 dsm[];
+  extern __shared__ __align__(16) float2 dsm[];
+  const int64_t ls = (l + 1) & ~int64_t(1);
   __shared__ int gcol[JW2];
+  __shared__ float nh[JW2], nl[JW2];
   __shared__ int cta_rot;
   __shared__ unsigned int cta_max;
   __shared__ float xch[JW][12];
@@ -1097,6 +1212,7 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
     gcol[threadIdx.x] = c < l ? (int)c : -1;
   }
   if (threadIdx.x == 0) { cta_rot = 0; cta_max = 0u; }
+  if (ls != l && threadIdx.x < JW2) dsm[(size_t)threadIdx.x * ls + l] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     double v[JW2];
@@ -1105,10 +1221,26 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
 #pragma unroll
     for (int c = 0; c < JW2; ++c) {
       const float h = __double2float_rn(v[c]);
-      dsm[(size_t)c * l + i] = make_float2(h, __double2float_rn(v[c] - (double)h));
+      dsm[(size_t)c * ls + i] = make_float2(h, __double2float_rn(v[c] - (double)h));
     }
   }
   __syncthreads();
+  const int64_t n2 = ls / 2;
+  {
+    // squared column norms as pairs, one warp per column (the block has JW2 warps)
+    const float4* c4 = reinterpret_cast<const float4*>(dsm + (size_t)warp * ls);
+    float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+    for (int64_t q = lane; q < n2; q += 32) {
+      const float4 x = c4[q];
+      df_dot_add(s0, e0, x.x, x.y, x.x, x.y);
+      df_dot_add(s1, e1, x.z, x.w, x.z, x.w);
+    }
+    df_add(s0, e0, s1, e1);
+    df_warp_allsum(s0, e0);
+    if (lane == 0) { nh[warp] = s0; nl[warp] = e0; }
+  }
+  __syncthreads();
+  float4* d4 = reinterpret_cast<float4*>(dsm);
   int rot = 0;
   float mx = 0.f;
   if (r == 0) {
@@ -1118,14 +1250,14 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
       if (p > q) { const int z = p; p = q; q = z; }
       p += side * JW;
       q += side * JW;
-      jacdf_pair2(dsm + (size_t)p * l, dsm + (size_t)q * l, gcol[p] >= 0 && gcol[q] >= 0, l,
-                  tol, lane, half, xch[pw], rot, mx);
+      jacdf_pair2(d4 + (size_t)p * n2, d4 + (size_t)q * n2, nh, nl, p, q,
+                  gcol[p] >= 0 && gcol[q] >= 0, n2, tol, lane, half, pw, xch[pw], rot, mx);
     }
   }
   for (int ir = 0; ir < JW; ++ir) {
     const int p = pw, q = JW + (pw + ir) % JW;
-    jacdf_pair2(dsm + (size_t)p * l, dsm + (size_t)q * l, gcol[p] >= 0 && gcol[q] >= 0, l, tol,
-                lane, half, xch[pw], rot, mx);
+    jacdf_pair2(d4 + (size_t)p * n2, d4 + (size_t)q * n2, nh, nl, p, q,
+                gcol[p] >= 0 && gcol[q] >= 0, n2, tol, lane, half, pw, xch[pw], rot, mx);
   }
   if (lane == 0 && half == 0 && rot) {
     atomicAdd(&cta_rot, rot);
@@ -1141,7 +1273,7 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
 #pragma unroll
     for (int c = 0; c < JW2; ++c)
       if (gcol[c] >= 0) {
-        const float2 v = dsm[(size_t)c * l + i];
+        const float2 v = dsm[(size_t)c * ls + i];
         B[(int64_t)gcol[c] * ldb + i] = (double)v.x + (double)v.y;
       }
   }
@@ -1219,7 +1351,7 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
   if (l <= 0) return 0;
   const int64_t N = (l % 2) ? l + 1 : l;
   int sweeps = 0;
-  const size_t smem = ((size_t)JW2 * l + JW2 * JW2) * sizeof(float);
+  const size_t smem = ((size_t)JW2 * jac32_ld(l) + JW2 * JW2) * sizeof(float);
   if (l > 1 && smem <= (size_t)kJac32SmemCap) {
     // Stage 1 (FP32): sweeps on an FP32 copy that accumulate the rotation W until the
     // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.  Skipped when the
@@ -1246,12 +1378,17 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     // lower the cap under each other's launches
     APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
-    const double flops32 = 12.0 * (double)l * (double)l * (double)(l - 1) / 2.0;
+    // per pair and sweep: the dot product g (2 l) and the rotation (6 l); the norms follow
+    // the rotations
+    const double flops32 = 8.0 * (double)l * (double)l * (double)(l - 1) / 2.0;
+    // A sweep whose rotations all had |cos| <= 5e-3 ends the stage: the next would find
+    // about the square of that, and the compensated stage converges from there in as
+    // many sweeps as from the fully converged FP32 start.
     sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
       jacobi32_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem, st>>>(l, NB, r, B32, W32,
                                                                       (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
-    }, PROF_JACOBI32, flops32, 0.0);
+    }, PROF_JACOBI32, flops32, 0.0, 5e-3);
     f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, wk.jw64.p);
     APL_LAUNCH_CHECK();
     // W is orthogonal only to FP32 accuracy; two Newton-Schulz steps
@@ -1269,7 +1406,7 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, G, l);
     dcopy2d(st, l, l, G, l, B, ldb, false);
   }
-  const size_t smem_df = (size_t)JW2 * l * sizeof(float2);
+  const size_t smem_df = (size_t)JW2 * jacdf_ld(l) * sizeof(float2);
   if (l > 1 && !dense_work().fp64_gemm && smem_df <= (size_t)kJac32SmemCap) {
     // Stage 2 in compensated FP32 (default): block-cyclic sweeps on hi/lo columns.
     // Threshold above the noise of the compensated dot products, about (l/64 + 6) 2^-46
@@ -1285,7 +1422,7 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
       jacobi_df_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem_df, st>>>(l, NB, r, B, ldb,
                                                                           (float)tol, flag_dev);
       APL_LAUNCH_CHECK();
-    }, PROF_JACOBI, 6.0 * (double)l * pairs, 6.0 * (double)l, 1e-2 * std::sqrt(tol));
+    }, PROF_JACOBI, 2.0 * (double)l * pairs, 6.0 * (double)l, 1e-2 * std::sqrt(tol));
   } else if (l > 1) {
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);
