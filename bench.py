@@ -313,7 +313,7 @@ NAMES = ["A z pass (k1_dense)", "A^T u pass (k2a_dense + k2b_dense)",
          "preconditioner passes (pre_qt, pre_qsum, pre_vt, pre_v, pre_expand)",
          "dense GEMM (df32gemm_kernel, compensated FP32)",
          "Jacobi stage 2 (jacobi_df_block_kernel, compensated FP32)",
-         "LUPP selection (lupp_step_kernel)",
+         "LUPP selection (lupp_coop_kernel; lupp_step_kernel in batched builds)",
          "Jacobi stage 1 (jacobi32_block_kernel, FP32)"]
 ALU = {3: (DF32_PEAK_TFLOPS, "derived compensated-FP32 ceiling: 152 SMs x 128 lanes x 2.07 GHz "
                              "FP32 instructions / 6 per FP64-equivalent flop"),

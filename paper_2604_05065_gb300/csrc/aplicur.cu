@@ -1368,6 +1368,9 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     for (int p = 0; p < nprob; ++p) {
       h->pc[p] = new (std::nothrow) aplicur_ctx();
       APL_REQUIRE(h->pc[p] != nullptr, "out of host memory");
+      // the problems' selections run concurrently on several streams: one launch per
+      // LUPP step rather than grid-resident cooperative launches
+      h->pc[p]->lw.cooperative = false;
     }
     parallel_for(nprob, h->nthreads, h->device, [&](int p) {
       aplicur_options op = o;

@@ -66,6 +66,7 @@ struct Cand {
   long long v;    // bits of |value| of the best candidate, -1 if none
   int pos;        // its position in the current row order
   long long sec;  // bits of the second-best |value|, -1 if none
+  int row;        // its row index (-1 if none)
 };
 
 __device__ __forceinline__ long long abs_key(double x) {
@@ -79,9 +80,9 @@ __device__ __forceinline__ bool cand_better(long long v1, int p1, long long v2, 
 __device__ __forceinline__ Cand cand_merge(Cand a, Cand b) {
   Cand r;
   if (cand_better(a.v, a.pos, b.v, b.pos)) {
-    r.v = a.v; r.pos = a.pos; r.sec = a.sec > b.v ? a.sec : b.v;
+    r.v = a.v; r.pos = a.pos; r.sec = a.sec > b.v ? a.sec : b.v; r.row = a.row;
   } else {
-    r.v = b.v; r.pos = b.pos; r.sec = b.sec > a.v ? b.sec : a.v;
+    r.v = b.v; r.pos = b.pos; r.sec = b.sec > a.v ? b.sec : a.v; r.row = b.row;
   }
   return r;
 }
@@ -93,6 +94,7 @@ __device__ __forceinline__ Cand warp_cand(Cand c) {
     d.v = __shfl_down_sync(0xffffffffu, c.v, o);
     d.pos = __shfl_down_sync(0xffffffffu, c.pos, o);
     d.sec = __shfl_down_sync(0xffffffffu, c.sec, o);
+    d.row = __shfl_down_sync(0xffffffffu, c.row, o);
     c = cand_merge(c, d);
   }
   return c;
@@ -100,15 +102,15 @@ __device__ __forceinline__ Cand warp_cand(Cand c) {
 
 __device__ Cand block_cand(Cand c) {
   __shared__ long long sv[32], ss[32];
-  __shared__ int sp[32];
+  __shared__ int sp[32], sr[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   c = warp_cand(c);
-  if (lane == 0) { sv[wid] = c.v; sp[wid] = c.pos; ss[wid] = c.sec; }
+  if (lane == 0) { sv[wid] = c.v; sp[wid] = c.pos; ss[wid] = c.sec; sr[wid] = c.row; }
   __syncthreads();
-  Cand r{-1, INT_MAX, -1};
+  Cand r{-1, INT_MAX, -1, -1};
   if (wid == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    if (lane < nw) { r.v = sv[lane]; r.pos = sp[lane]; r.sec = ss[lane]; }
+    if (lane < nw) { r.v = sv[lane]; r.pos = sp[lane]; r.sec = ss[lane]; r.row = sr[lane]; }
     r = warp_cand(r);
   }
   return r;
@@ -118,6 +120,8 @@ __device__ Cand block_cand(Cand c) {
 // split the columns j-1.. K-1 (warp w takes columns j + w, j + w + 8, ...), so every
 // access X(i, c) is coalesced when rs = 1.  Step j applies the elimination of column
 // j-1 by the pivot row chosen at step j-1, then looks for the pivot of column j.
+constexpr int LUPP_U = 8;
+
 __global__ void __launch_bounds__(256) lupp_step_kernel(
     int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int j,
     int* __restrict__ pos_of, int* __restrict__ row_at, int* __restrict__ piv,
@@ -143,18 +147,30 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
   __syncthreads();
   if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] * prow[K - (j - 1)];
   __syncthreads();  // every warp has read X(i, j-1) before it is overwritten
-  Cand mine{-1, INT_MAX, -1};
+  Cand mine{-1, INT_MAX, -1, -1};
   if (live) {
     if (j > 0 && wid == 0) xi[(int64_t)(j - 1) * cs] = l;
-    for (int64_t c = j + wid; c < K; c += nw) {
-      double v = xi[c * cs];
-      if (j > 0) {
-        v = v - l * prow[c - (j - 1)];
-        xi[c * cs] = v;
+    // LUPP_U columns per warp are loaded before any is updated and stored, so their L2
+    // round trips overlap instead of following one another
+    for (int64_t c0 = j + wid; c0 < K; c0 += (int64_t)nw * LUPP_U) {
+      double v[LUPP_U];
+#pragma unroll
+      for (int u = 0; u < LUPP_U; ++u) {
+        const int64_t c = c0 + (int64_t)u * nw;
+        v[u] = c < K ? xi[c * cs] : 0.0;
       }
-      if (c == j) {
-        Cand cd{abs_key(v), pos_of[i], -1};
-        mine = cd;
+#pragma unroll
+      for (int u = 0; u < LUPP_U; ++u) {
+        const int64_t c = c0 + (int64_t)u * nw;
+        if (c >= K) continue;
+        if (j > 0) {
+          v[u] = v[u] - l * prow[c - (j - 1)];
+          xi[c * cs] = v[u];
+        }
+        if (c == j) {
+          Cand cd{abs_key(v[u]), pos_of[i], -1, (int)i};
+          mine = cd;
+        }
       }
     }
   }
@@ -165,10 +181,10 @@ __global__ void __launch_bounds__(256) lupp_step_kernel(
     psec[blockIdx.x] = __longlong_as_double(b.sec);
   }
   if (!last_block_done(counter)) return;
-  Cand t{-1, INT_MAX, -1};
+  Cand t{-1, INT_MAX, -1, -1};
   for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
     Cand c{__double_as_longlong(__ldcg(pval + q)), __ldcg(ppos + q),
-           __double_as_longlong(__ldcg(psec + q))};
+           __double_as_longlong(__ldcg(psec + q)), -1};
     t = cand_merge(t, c);
   }
   t = block_cand(t);
@@ -196,7 +212,164 @@ __global__ void lupp_init_kernel(int64_t N, int* pos_of, int* row_at, double* ma
                                  unsigned int* counter) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) { pos_of[i] = (int)i; row_at[i] = (int)i; }
-  if (i == 0) { *margin = INFINITY; iscal[0] = 0; iscal[1] = 0; *counter = 0u; }
+  if (i == 0) {
+    *margin = INFINITY;
+    iscal[0] = 0;
+    iscal[1] = 0;
+    iscal[2] = 0;
+    counter[0] = 0u;
+    counter[1] = 0u;
+  }
+}
+
+// ---- LUPP as one cooperative launch ----------------------------------------------------
+//
+// All k elimination steps in one kernel whose blocks are resident together (cooperative
+// launch).  Block b owns the 32-row tiles b, b + G, b + 2G, ... (G blocks); a step updates
+// the owned rows and finds each block's best candidate (phase A), the blocks meet at a
+// grid barrier, and every block merges the G partial candidates itself (phase B), so all
+// of them know the pivot without a second barrier.  Only the owner of a row reads or
+// writes its position: the swap of step j (pivot row to position j, the row that held
+// position j to the pivot's old position) is applied by the owners when they read the
+// positions in step j + 1.  Partial candidates alternate between two buffers by step
+// parity: a block can run at most one step ahead of the slowest.
+
+constexpr long long kLuppSpin = 1LL << 22;  // polls of the grid barrier before it gives up
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier: bar[0] counts arrivals, bar[1] is the generation.  Returns false
+// (and sets *err) when the wait ran past its bound or another block already gave up;
+// every later barrier then gives up too, so the launch ends in bounded time.
+__device__ bool lupp_grid_sync(unsigned* bar, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();  // this block's writes are visible before its arrival
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (++it > kLuppSpin || *(volatile int*)err) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) lupp_coop_kernel(
+    int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int k,
+    int* __restrict__ pos_of, int* __restrict__ piv, long long* __restrict__ pv,
+    int* __restrict__ pp, long long* __restrict__ ps, int* __restrict__ pr, unsigned* bar,
+    double* margin, int* iscal) {
+  extern __shared__ double prow[];  // pivot row values for columns j-1 .. K-1, then 1/pivot
+  __shared__ long long s_v, s_sec;
+  __shared__ int s_pos, s_row;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int64_t ntiles = (N + 31) / 32;
+  int p = -1;     // pivot row of the previous step
+  int ppos = -1;  // its position before that step's swap
+  for (int j = 0; j < k; ++j) {
+    if (j > 0) {
+      // written by the pivot row's owner before the last barrier: read through L2
+      for (int64_t c = j - 1 + threadIdx.x; c < K; c += blockDim.x)
+        prow[c - (j - 1)] = __ldcg(X + (int64_t)p * rs + c * cs);
+      __syncthreads();
+      if (threadIdx.x == 0) prow[K - (j - 1)] = 1.0 / prow[0];
+      __syncthreads();
+    }
+    Cand mine{-1, INT_MAX, -1, -1};
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int64_t i = tile * 32 + lane;
+      int pi = -1;
+      if (i < N) {
+        pi = pos_of[i];
+        if (j > 0) {
+          // the swap of step j - 1 (idempotent, so every warp may apply it)
+          const int q = (i == p) ? j - 1 : (pi == j - 1 ? ppos : pi);
+          if (q != pi) {
+            pi = q;
+            if (wid == 0) pos_of[i] = q;
+          }
+        }
+      }
+      const bool live = i < N && pi >= j;
+      double* xi = X + i * rs;
+      double l = 0.0;
+      if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] * prow[K - (j - 1)];
+      __syncthreads();  // every warp has read X(i, j-1) before it is overwritten
+      if (live) {
+        if (j > 0 && wid == 0) xi[(int64_t)(j - 1) * cs] = l;
+        for (int64_t c0 = j + wid; c0 < K; c0 += (int64_t)nw * LUPP_U) {
+          double v[LUPP_U];
+#pragma unroll
+          for (int u = 0; u < LUPP_U; ++u) {
+            const int64_t c = c0 + (int64_t)u * nw;
+            v[u] = c < K ? xi[c * cs] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < LUPP_U; ++u) {
+            const int64_t c = c0 + (int64_t)u * nw;
+            if (c >= K) continue;
+            if (j > 0) {
+              v[u] = v[u] - l * prow[c - (j - 1)];
+              xi[c * cs] = v[u];
+            }
+            if (c == j) mine = cand_merge(mine, Cand{abs_key(v[u]), pi, -1, (int)i});
+          }
+        }
+      }
+    }
+    const Cand b = block_cand(mine);
+    const int64_t base = (int64_t)(j & 1) * gridDim.x;
+    if (threadIdx.x == 0) {
+      pv[base + blockIdx.x] = b.v;
+      pp[base + blockIdx.x] = b.pos;
+      ps[base + blockIdx.x] = b.sec;
+      pr[base + blockIdx.x] = b.row;
+    }
+    if (!lupp_grid_sync(bar, iscal + 2)) return;
+    Cand t{-1, INT_MAX, -1, -1};
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
+      t = cand_merge(t, Cand{__ldcg(pv + base + q), __ldcg(pp + base + q),
+                             __ldcg(ps + base + q), __ldcg(pr + base + q)});
+    t = block_cand(t);
+    if (threadIdx.x == 0) { s_v = t.v; s_pos = t.pos; s_sec = t.sec; s_row = t.row; }
+    __syncthreads();
+    const long long tv_bits = s_v, ts_bits = s_sec;
+    const int tpos = s_pos, trow = s_row;
+    if (!(tv_bits > 0)) {  // zero pivot (or no candidates): rank exhausted
+      if (blockIdx.x == 0 && threadIdx.x == 0) iscal[1] = 1;
+      break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      piv[j] = trow;
+      iscal[0] = j + 1;
+      if (ts_bits >= 0) {
+        const double tv = __longlong_as_double(tv_bits), ts = __longlong_as_double(ts_bits);
+        *margin = fmin(*margin, (tv - ts) / tv);
+      }
+    }
+    p = trow;
+    ppos = tpos;
+  }
 }
 
 // ---- gathers --------------------------------------------------------------------------
@@ -422,30 +595,69 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
   w.pval.alloc(blocks, st);
   w.psec.alloc(blocks, st);
   w.ppos.alloc(blocks, st);
-  w.counter.alloc(1, st);
+  w.counter.alloc(2, st);
   w.scal.alloc(1, st);
-  w.iscal.alloc(2, st);
+  w.iscal.alloc(3, st);
   lupp_init_kernel<<<(unsigned)cdiv(N, 256), 256, 0, st>>>(N, w.pos_of.p, w.row_at.p, w.scal.p,
                                                           w.iscal.p, w.counter.p);
   APL_LAUNCH_CHECK();
   const size_t shm = (size_t)(K + 1) * sizeof(double);
-  const int tok = prof_begin(st);
-  for (int j = 0; j < k; ++j) {
-    lupp_step_kernel<<<blocks, threads, shm, st>>>(N, K, X, rs, cs, j, w.pos_of.p, w.row_at.p,
-                                                   w.piv.p, w.pval.p, w.ppos.p, w.psec.p,
-                                                   w.counter.p, w.scal.p, w.iscal.p);
+  // one cooperative launch when the device offers it and the caller runs no concurrent
+  // selections; one launch per step otherwise
+  int coop_grid = 0;
+  if (w.cooperative) {
+    int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    APL_CUDA(cudaGetDevice(&dev));
+    APL_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    APL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    APL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lupp_coop_kernel, threads,
+                                                           shm));
+    if (coop && per_sm > 0) {
+      // as few blocks as give the same number of tiles to the busiest block
+      const int64_t per_block = cdiv(blocks64, (int64_t)per_sm * nsm);
+      coop_grid = (int)cdiv(blocks64, per_block);
+    }
   }
-  APL_LAUNCH_CHECK();
+  const int tok = prof_begin(st);
+  if (coop_grid > 0) {
+    w.cv.alloc(2 * (size_t)coop_grid, st);
+    w.cs.alloc(2 * (size_t)coop_grid, st);
+    w.cp.alloc(2 * (size_t)coop_grid, st);
+    w.cr.alloc(2 * (size_t)coop_grid, st);
+    int* pos_of = w.pos_of.p;
+    int* piv = w.piv.p;
+    long long* pv = w.cv.p;
+    int* pp = w.cp.p;
+    long long* ps = w.cs.p;
+    int* pr = w.cr.p;
+    unsigned* bar = w.counter.p;
+    double* mg = w.scal.p;
+    int* isc = w.iscal.p;
+    void* args[] = {(void*)&N, (void*)&K, (void*)&X, (void*)&rs, (void*)&cs, (void*)&k,
+                    (void*)&pos_of, (void*)&piv, (void*)&pv, (void*)&pp, (void*)&ps,
+                    (void*)&pr, (void*)&bar, (void*)&mg, (void*)&isc};
+    APL_CUDA(cudaLaunchCooperativeKernel((const void*)lupp_coop_kernel, dim3(coop_grid),
+                                         dim3(threads), args, shm, st));
+    APL_LAUNCH_CHECK();
+  } else {
+    for (int j = 0; j < k; ++j) {
+      lupp_step_kernel<<<blocks, threads, shm, st>>>(N, K, X, rs, cs, j, w.pos_of.p, w.row_at.p,
+                                                     w.piv.p, w.pval.p, w.ppos.p, w.psec.p,
+                                                     w.counter.p, w.scal.p, w.iscal.p);
+      APL_LAUNCH_CHECK();
+    }
+  }
   {
     // algorithmic bytes: step j reads and writes the N x (K - j) trailing block
     double bytes = 0.0;
     for (int j = 0; j < k; ++j) bytes += 16.0 * (double)N * (double)(K - j);
     prof_end(st, tok, PROF_LUPP, bytes);
   }
-  int isc[2];
-  APL_CUDA(cudaMemcpyAsync(isc, w.iscal.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int isc[3];
+  APL_CUDA(cudaMemcpyAsync(isc, w.iscal.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaMemcpyAsync(margin, w.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaStreamSynchronize(st));
+  if (isc[2]) throw Error(ST_ETIMEOUT, "LUPP: a grid barrier wait ran past its bound");
   const int nz = isc[0];
   piv_host.resize(nz);
   if (nz)

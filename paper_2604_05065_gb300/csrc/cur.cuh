@@ -35,9 +35,14 @@ struct LuppWork {
   DBuf<int> pos_of, row_at, piv;
   DBuf<double> pval, psec;
   DBuf<int> ppos;
-  DBuf<unsigned int> counter;
+  DBuf<long long> cv, cs;  // cooperative form: partial candidates, two buffers
+  DBuf<int> cp, cr;
+  DBuf<unsigned int> counter;  // [0] arrivals / last-block counter, [1] barrier generation
   DBuf<double> scal;   // [0] margin
-  DBuf<int> iscal;     // [0] nz, [1] stopped
+  DBuf<int> iscal;     // [0] nz, [1] stopped, [2] a barrier wait gave up
+  // all steps in one cooperative launch; owners that run selections concurrently on
+  // several streams keep this off (one launch per step)
+  bool cooperative = true;
 };
 int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, int64_t cs, int k,
                 LuppWork& w, std::vector<int>& piv_host, double* margin);

@@ -1068,6 +1068,15 @@ __device__ __forceinline__ void df_rsqrt(float vh, float vl, float& ch, float& c
   cl = yl;
 }
 
+// (h, l) <- (xh + xl) + d for a small FP32 d, renormalised
+__device__ __forceinline__ void df_nudge(float xh, float xl, float d, float& h, float& l) {
+  float r, e;
+  df_two_sum(xh, d, r, e);
+  const float lo = __fadd_rn(e, xl);
+  h = __fadd_rn(r, lo);
+  l = __fsub_rn(lo, __fsub_rn(h, r));
+}
+
 // x' = c x - s y and y' = s x + c y for one hi/lo element, c = (ch, cl), s = (sh, sl)
 __device__ __forceinline__ void df_rotate(float ch, float cl, float sh, float sl, float xh,
                                           float xl, float yh, float yl, float& uh, float& ul,
@@ -1148,13 +1157,25 @@ __device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __r
   df_add(NB, NBl, tg, tgl);
   const bool refresh = !(NA >= 0.0625f * A) || !(NB >= 0.0625f * Bv);
   float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f;
+  // |t| <= 2^-23: x' = x + (c - 1) x - s y with the small update formed in FP32 from the
+  // high parts; what it drops (s y_lo, s_lo y, the update's rounding) is below
+  // 2^-23 |s| |y|, the compensated rotation's own error level
+  const bool small = fabsf(t) <= 1.1920928955078125e-7f;
+  const float em = __fadd_rn(__fsub_rn(ch, 1.f), cl);  // c - 1
 #pragma unroll 2
   for (int64_t k = lane + 32 * half; k < n2; k += 64) {
     const float4 x = cp[k];
     const float4 y = cq[k];
     float4 u, v;
-    df_rotate(ch, cl, sh, sl, x.x, x.y, y.x, y.y, u.x, u.y, v.x, v.y);
-    df_rotate(ch, cl, sh, sl, x.z, x.w, y.z, y.w, u.z, u.w, v.z, v.w);
+    if (small) {
+      df_nudge(x.x, x.y, __fmaf_rn(-sh, y.x, __fmul_rn(em, x.x)), u.x, u.y);
+      df_nudge(x.z, x.w, __fmaf_rn(-sh, y.z, __fmul_rn(em, x.z)), u.z, u.w);
+      df_nudge(y.x, y.y, __fmaf_rn(sh, x.x, __fmul_rn(em, y.x)), v.x, v.y);
+      df_nudge(y.z, y.w, __fmaf_rn(sh, x.z, __fmul_rn(em, y.z)), v.z, v.w);
+    } else {
+      df_rotate(ch, cl, sh, sl, x.x, x.y, y.x, y.y, u.x, u.y, v.x, v.y);
+      df_rotate(ch, cl, sh, sl, x.z, x.w, y.z, y.w, u.z, u.w, v.z, v.w);
+    }
     cp[k] = u;
     cq[k] = v;
     if (refresh) {
