@@ -839,16 +839,25 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   g = xch[0] + xch[1];
   const float a = nrm[p], b = nrm[q];
   // no barrier before xch is written again: that happens after the closing barrier below
-  const float relg = (valid && a > 0.f && b > 0.f) ? fabsf(g) / (sqrtf(a) * sqrtf(b)) : 0.f;
+  // the angle needs only FP32 accuracy here (the next stage decides the final one), so
+  // it is formed with the approximate reciprocal square root and division
+  const float relg =
+      (valid && a > 0.f && b > 0.f) ? fabsf(g) * (rsqrtf(a) * rsqrtf(b)) : 0.f;
   if (!(relg > tol)) {
     __syncthreads();
     return;
   }
   mx = fmaxf(mx, relg);
-  const float zeta = (b - a) / (2.f * g);
+  const float zeta = __fdividef(b - a, 2.f * g);
   const float az = fabsf(zeta);
   // tan of the rotation angle, the smaller root; 1 / (2 zeta) once zeta^2 would overflow
-  float t = az < 1e15f ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
+  float t;
+  if (az < 1e15f) {
+    const float q = 1.f + zeta * zeta;
+    t = __fdividef(1.f, az + q * rsqrtf(q));
+  } else {
+    t = __fdividef(0.5f, az);
+  }
   t = zeta >= 0.f ? t : -t;
   const float c = rsqrtf(1.f + t * t), sn = c * t;
   float na = a - t * g, nb = b + t * g;
@@ -893,20 +902,80 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   __syncthreads();
 }
 
-// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory
-// JW2 * jac32_ld(l) floats + R.  rotated[0] counts rotations, rotated[1] holds the largest
-// rotated |cos| of the sweep (as float bits; non-negative floats order like their bits).
-__global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int64_t NB,
-                                                                 int64_t r, float* __restrict__ B,
+// Bulk-copy (TMA) helpers: one thread moves whole columns between global and shared
+// memory; loads complete on an mbarrier (transaction bytes), stores in a bulk group.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the phase with the given parity; false once the wait ran past its bound.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (long long it = 0; it < (1LL << 24); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_drain() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// generic-proxy writes to shared memory become visible to the bulk-copy (async) proxy
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// grid NB/2, block 64 * JW threads (two warps per pair).  B and W are l x l with column
+// stride ls = jac32_ld(l) (zero pad rows), so every column is one 16-byte aligned bulk
+// copy.  Dynamic shared memory: JW2 columns of B, with WPRE also JW2 columns of W
+// (fetched with B, so the fetch overlaps the rotations), then R.  Without WPRE the W
+// columns are fetched into the B area after B has been stored.  rotated[0] counts
+// rotations, rotated[1] holds the largest rotated |cos| of the sweep (as float bits;
+// non-negative floats order like their bits), rotated[2] is set when a wait gave up.
+template <bool WPRE>
+__global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int64_t ls,
+                                                                 int64_t NB, int64_t r,
+                                                                 float* __restrict__ B,
                                                                  float* __restrict__ W,
                                                                  float tol, int* rotated) {
-  extern __shared__ __align__(16) float jsm[];
-  const int64_t ls = (l + 3) & ~int64_t(3);
-  float* cols = jsm;                   // JW2 columns of stride ls
-  float* R = jsm + (size_t)JW2 * ls;   // JW2 x JW2, row-major R[row * JW2 + col]
+  extern __shared__ __align__(128) float jsm[];
+  float* cols = jsm;                                  // JW2 columns of B, stride ls
+  float* wsm = WPRE ? jsm + (size_t)JW2 * ls : jsm;   // JW2 columns of W
+  float* R = jsm + (size_t)(WPRE ? 2 : 1) * JW2 * ls;  // JW2 x JW2, R[row * JW2 + col]
+  __shared__ __align__(8) uint64_t mbar;
   __shared__ int gcol[JW2];
   __shared__ float nrm[JW2];
-  __shared__ int cta_rot;
+  __shared__ int cta_rot, nvalid;
   __shared__ unsigned int cta_max;
   __shared__ float xch[JW][6];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -918,22 +987,39 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
     const int64_t c = blk * JW + (threadIdx.x % JW);
     gcol[threadIdx.x] = c < l ? (int)c : -1;
   }
-  if (threadIdx.x == 0) { cta_rot = 0; cta_max = 0u; }
+  if (threadIdx.x == 0) {
+    cta_rot = 0;
+    cta_max = 0u;
+    mbar_init(&mbar, 1);
+  }
   for (int e = threadIdx.x; e < JW2 * JW2; e += blockDim.x)
     R[e] = (e / JW2 == e % JW2) ? 1.f : 0.f;
-  const int pad = (int)(ls - l);
-  for (int e = threadIdx.x; e < JW2 * pad; e += blockDim.x)
-    cols[(size_t)(e / pad) * ls + l + e % pad] = 0.f;
   __syncthreads();
-  // one row index per thread and pass, all JW2 column loads in flight together
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    float v[JW2];
-#pragma unroll
-    for (int c = 0; c < JW2; ++c) v[c] = gcol[c] >= 0 ? B[(int64_t)gcol[c] * l + i] : 0.f;
-#pragma unroll
-    for (int c = 0; c < JW2; ++c) cols[(size_t)c * ls + i] = v[c];
+  // columns past l (the last block of an odd count) stay zero
+  for (int c = 0; c < JW2; ++c)
+    if (gcol[c] < 0)
+      for (int64_t i = threadIdx.x; i < ls; i += blockDim.x) {
+        cols[(size_t)c * ls + i] = 0.f;
+        if (WPRE) wsm[(size_t)c * ls + i] = 0.f;
+      }
+  const unsigned colbytes = (unsigned)(ls * sizeof(float));
+  if (threadIdx.x == 0) {
+    int nv = 0;
+    for (int c = 0; c < JW2; ++c) nv += gcol[c] >= 0;
+    nvalid = nv;
+    mbar_expect_tx(&mbar, (unsigned)nv * colbytes * (WPRE ? 2u : 1u));
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0) {
+        bulk_load(cols + (size_t)c * ls, B + (int64_t)gcol[c] * ls, colbytes, &mbar);
+        if (WPRE) bulk_load(wsm + (size_t)c * ls, W + (int64_t)gcol[c] * ls, colbytes, &mbar);
+      }
   }
-  __syncthreads();
+  if (!mbar_wait_bounded(&mbar, 0)) {
+    if (threadIdx.x == 0) atomicExch(rotated + 2, 1);
+    mbar_wait_bounded(&mbar, 0);  // the copies in flight target this block's memory
+    return;
+  }
+  __syncthreads();  // the zero columns written by other threads
   const int64_t n4 = ls / 4;
   {
     // squared column norms, one warp per column (the block has JW2 warps)
@@ -972,33 +1058,66 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
     atomicMax(&cta_max, __float_as_uint(mx));
   }
   __syncthreads();
-  if (cta_rot == 0) return;
+  if (cta_rot == 0) return;  // nothing rotated: B and W stay as they are
   if (threadIdx.x == 0) {
     atomicAdd(rotated, cta_rot);
     atomicMax(reinterpret_cast<unsigned int*>(rotated + 1), cta_max);
   }
-  // write back the columns and W(:, cols) <- W(:, cols) R, one row per thread and pass,
-  // the 16 outputs in two halves of 8 to bound registers
+  if (!WPRE) {
+    // store B, then fetch W into the same columns
+    fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < JW2; ++c)
+        if (gcol[c] >= 0) bulk_store(B + (int64_t)gcol[c] * ls, cols + (size_t)c * ls, colbytes);
+      bulk_commit_and_drain();
+      mbar_expect_tx(&mbar, (unsigned)nvalid * colbytes);
+      for (int c = 0; c < JW2; ++c)
+        if (gcol[c] >= 0) bulk_load(cols + (size_t)c * ls, W + (int64_t)gcol[c] * ls, colbytes, &mbar);
+    }
+    if (!mbar_wait_bounded(&mbar, 1)) {
+      if (threadIdx.x == 0) atomicExch(rotated + 2, 1);
+      mbar_wait_bounded(&mbar, 1);
+      return;
+    }
+  }
+  // W(:, cols) <- W(:, cols) R in shared memory, one row per thread and pass, the 16
+  // outputs in two halves of 8; R rows are read as float4
+  const float4* R4 = reinterpret_cast<const float4*>(R);
   for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
     float w[JW2];
 #pragma unroll
-    for (int c = 0; c < JW2; ++c) {
-      if (gcol[c] >= 0) B[(int64_t)gcol[c] * l + i] = cols[(size_t)c * ls + i];
-      w[c] = gcol[c] >= 0 ? W[(int64_t)gcol[c] * l + i] : 0.f;
-    }
+    for (int c = 0; c < JW2; ++c) w[c] = wsm[(size_t)c * ls + i];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float o[JW];
 #pragma unroll
       for (int j = 0; j < JW; ++j) o[j] = 0.f;
 #pragma unroll
-      for (int c = 0; c < JW2; ++c)
+      for (int c = 0; c < JW2; ++c) {
+        const float4 r0 = R4[(c * JW2 + h * JW) / 4], r1 = R4[(c * JW2 + h * JW) / 4 + 1];
+        o[0] = fmaf(w[c], r0.x, o[0]);
+        o[1] = fmaf(w[c], r0.y, o[1]);
+        o[2] = fmaf(w[c], r0.z, o[2]);
+        o[3] = fmaf(w[c], r0.w, o[3]);
+        o[4] = fmaf(w[c], r1.x, o[4]);
+        o[5] = fmaf(w[c], r1.y, o[5]);
+        o[6] = fmaf(w[c], r1.z, o[6]);
+        o[7] = fmaf(w[c], r1.w, o[7]);
+      }
 #pragma unroll
-        for (int j = 0; j < JW; ++j) o[j] = fmaf(w[c], R[c * JW2 + h * JW + j], o[j]);
-#pragma unroll
-      for (int j = 0; j < JW; ++j)
-        if (gcol[h * JW + j] >= 0) W[(int64_t)gcol[h * JW + j] * l + i] = o[j];
+      for (int j = 0; j < JW; ++j) wsm[(size_t)(h * JW + j) * ls + i] = o[j];
     }
+  }
+  fence_async_shared();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0) {
+        if (WPRE) bulk_store(B + (int64_t)gcol[c] * ls, cols + (size_t)c * ls, colbytes);
+        bulk_store(W + (int64_t)gcol[c] * ls, wsm + (size_t)c * ls, colbytes);
+      }
+    bulk_commit_and_drain();
   }
 }
 
@@ -1205,19 +1324,46 @@ __device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __r
   __syncthreads();
 }
 
-// Column stride (in hi/lo elements) of the compensated stage's shared copy: l rounded up
-// to even, so every column starts on a 16-byte boundary; the pad holds zeros.
+// Column stride (in hi/lo elements) of the compensated stage's working copy: l rounded up
+// to even, so every column is one 16-byte aligned bulk copy; the pad holds zeros.
 inline int64_t jacdf_ld(int64_t l) { return (l + 1) & ~int64_t(1); }
 
-// grid NB/2, block 64 * JW threads (two warps per pair), dynamic shared memory
-// JW2 * jacdf_ld(l) float2.  rotated[0] counts rotations, rotated[1] holds the largest
-// rotated |cos| of the sweep (as float bits; non-negative floats order like their bits).
-__global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int64_t NB,
-                                                                  int64_t r, double* __restrict__ B,
-                                                                  int64_t ldb, float tol,
-                                                                  int* rotated) {
-  extern __shared__ __align__(16) float2 dsm[];
-  const int64_t ls = (l + 1) & ~int64_t(1);
+// D (hi/lo pairs, column stride ldd) <- B (l x l FP64, ld ldb); pad rows zero
+__global__ void split_df_kernel(int64_t l, const double* __restrict__ B, int64_t ldb,
+                                float2* __restrict__ D, int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ldd * l) return;
+  const int64_t r = e % ldd, c = e / ldd;
+  float2 v = make_float2(0.f, 0.f);
+  if (r < l) {
+    const double x = B[r + c * ldb];
+    v.x = __double2float_rn(x);
+    v.y = __double2float_rn(x - (double)v.x);
+  }
+  D[e] = v;
+}
+// B <- D as FP64 (hi + lo)
+__global__ void join_df_kernel(int64_t l, const float2* __restrict__ D, int64_t ldd,
+                               double* __restrict__ B, int64_t ldb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l * l) return;
+  const int64_t r = e % l, c = e / l;
+  const float2 v = D[r + c * ldd];
+  B[r + c * ldb] = (double)v.x + (double)v.y;
+}
+
+// grid NB/2, block 64 * JW threads (two warps per pair).  D holds the l columns as FP32
+// hi/lo pairs with column stride ls = jacdf_ld(l) (zero pad rows); the block's JW2
+// columns arrive in shared memory as bulk copies and leave the same way.  Dynamic shared
+// memory JW2 * ls float2.  rotated[0] counts rotations, rotated[1] holds the largest
+// rotated |cos| of the sweep (as float bits; non-negative floats order like their bits),
+// rotated[2] is set when a wait gave up.
+__global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int64_t ls,
+                                                                  int64_t NB, int64_t r,
+                                                                  float2* __restrict__ D,
+                                                                  float tol, int* rotated) {
+  extern __shared__ __align__(128) float2 dsm[];
+  __shared__ __align__(8) uint64_t mbar;
   __shared__ int gcol[JW2];
   __shared__ float nh[JW2], nl[JW2];
   __shared__ int cta_rot;
@@ -1232,20 +1378,31 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
     const int64_t c = blk * JW + (threadIdx.x % JW);
     gcol[threadIdx.x] = c < l ? (int)c : -1;
   }
-  if (threadIdx.x == 0) { cta_rot = 0; cta_max = 0u; }
-  if (ls != l && threadIdx.x < JW2) dsm[(size_t)threadIdx.x * ls + l] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-    double v[JW2];
-#pragma unroll
-    for (int c = 0; c < JW2; ++c) v[c] = gcol[c] >= 0 ? B[(int64_t)gcol[c] * ldb + i] : 0.0;
-#pragma unroll
-    for (int c = 0; c < JW2; ++c) {
-      const float h = __double2float_rn(v[c]);
-      dsm[(size_t)c * ls + i] = make_float2(h, __double2float_rn(v[c] - (double)h));
-    }
+  if (threadIdx.x == 0) {
+    cta_rot = 0;
+    cta_max = 0u;
+    mbar_init(&mbar, 1);
   }
   __syncthreads();
+  for (int c = 0; c < JW2; ++c)
+    if (gcol[c] < 0)
+      for (int64_t i = threadIdx.x; i < ls; i += blockDim.x)
+        dsm[(size_t)c * ls + i] = make_float2(0.f, 0.f);
+  const unsigned colbytes = (unsigned)(ls * sizeof(float2));
+  if (threadIdx.x == 0) {
+    int nv = 0;
+    for (int c = 0; c < JW2; ++c) nv += gcol[c] >= 0;
+    mbar_expect_tx(&mbar, (unsigned)nv * colbytes);
+    for (int c = 0; c < JW2; ++c)
+      if (gcol[c] >= 0)
+        bulk_load(dsm + (size_t)c * ls, D + (int64_t)gcol[c] * ls, colbytes, &mbar);
+  }
+  if (!mbar_wait_bounded(&mbar, 0)) {
+    if (threadIdx.x == 0) atomicExch(rotated + 2, 1);
+    mbar_wait_bounded(&mbar, 0);  // the copies in flight target this block's memory
+    return;
+  }
+  __syncthreads();  // the zero columns written by other threads
   const int64_t n2 = ls / 2;
   {
     // squared column norms as pairs, one warp per column (the block has JW2 warps)
@@ -1286,33 +1443,35 @@ __global__ void __launch_bounds__(64 * JW) jacobi_df_block_kernel(int64_t l, int
   }
   __syncthreads();
   if (cta_rot == 0) return;
+  fence_async_shared();
+  __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(rotated, cta_rot);
     atomicMax(reinterpret_cast<unsigned int*>(rotated + 1), cta_max);
-  }
-  for (int64_t i = threadIdx.x; i < l; i += blockDim.x) {
-#pragma unroll
     for (int c = 0; c < JW2; ++c)
-      if (gcol[c] >= 0) {
-        const float2 v = dsm[(size_t)c * ls + i];
-        B[(int64_t)gcol[c] * ldb + i] = (double)v.x + (double)v.y;
-      }
+      if (gcol[c] >= 0) bulk_store(D + (int64_t)gcol[c] * ls, dsm + (size_t)c * ls, colbytes);
+    bulk_commit_and_drain();
   }
 }
 
-__global__ void d2f_kernel(int64_t l, const double* s, int64_t lds, float* d) {
+// d (ldd x l, FP32) <- s (l x l, FP64, ld lds); rows l .. ldd-1 of d are zero
+__global__ void d2f_kernel(int64_t l, const double* s, int64_t lds, float* d, int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ldd * l) return;
+  const int64_t r = e % ldd, c = e / ldd;
+  d[e] = r < l ? (float)s[r + c * lds] : 0.f;
+}
+// d (l x l, FP64, ld l) <- s (l x l, FP32, ld lds)
+__global__ void f2d_kernel(int64_t l, const float* s, int64_t lds, double* d) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * l) return;
   const int64_t r = e % l, c = e / l;
-  d[e] = (float)s[r + c * lds];
+  d[e] = (double)s[r + c * lds];
 }
-__global__ void f2d_kernel(int64_t n, const float* s, double* d) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) d[i] = (double)s[i];
-}
-__global__ void eye32_kernel(int64_t n, float* W) {
+// W (ldw x n) <- the identity, zero pad rows
+__global__ void eye32_kernel(int64_t n, float* W, int64_t ldw) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n * n) W[e] = (e % n == e / n) ? 1.f : 0.f;
+  if (e < ldw * n) W[e] = (e % ldw == e / ldw) ? 1.f : 0.f;
 }
 
 
@@ -1345,15 +1504,16 @@ int run_sweeps(cudaStream_t st, int64_t N, int max_sweeps, int* flag_dev, F&& ro
   } guard{exec};
   int sweeps = 0;
   for (; sweeps < max_sweeps;) {
-    APL_CUDA(cudaMemsetAsync(flag_dev, 0, 2 * sizeof(int), st));
+    APL_CUDA(cudaMemsetAsync(flag_dev, 0, 3 * sizeof(int), st));
     const int tok = prof_cat >= 0 ? prof_begin(st) : -1;
     APL_CUDA(cudaGraphLaunch(exec, st));
     add_launches(N - 1);
     if (tok >= 0) prof_end(st, tok, prof_cat, 0.0);
     ++sweeps;
-    int fl[2] = {0, 0};
-    APL_CUDA(cudaMemcpyAsync(fl, flag_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int fl[3] = {0, 0, 0};
+    APL_CUDA(cudaMemcpyAsync(fl, flag_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     APL_CUDA(cudaStreamSynchronize(st));
+    if (fl[2]) throw Error(ST_ETIMEOUT, "Jacobi sweep: a bulk-copy wait ran past its bound");
     const int rot = fl[0];
     if (tok >= 0) prof_set_work(tok, flops_per_sweep + flops_per_rot * rot);
     if (rot == 0) break;
@@ -1378,26 +1538,35 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.  Skipped when the
     // CTA's two column blocks do not fit in shared memory (l above about 3600).
     const int64_t l2 = l * l;
+    const int64_t ls = jac32_ld(l);
     DenseWork& wk = dense_work();
-    wk.jb32.alloc(l2, st);
-    wk.jw32.alloc(l2, st);
+    wk.jb32.alloc(ls * l, st);
+    wk.jw32.alloc(ls * l, st);
     wk.jw64.alloc(l2, st);
     wk.jtmp.alloc(l2, st);
     wk.jw2.alloc(l2, st);
     float* B32 = wk.jb32.p;
     float* W32 = wk.jw32.p;
-    d2f_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, B, ldb, B32);
+    // the sweep kernels move whole columns with bulk copies: 16-byte aligned bases
+    APL_REQUIRE(((uintptr_t)B32 & 15) == 0 && ((uintptr_t)W32 & 15) == 0,
+                "jacobi_left: work buffers not 16-byte aligned");
+    d2f_kernel<<<(unsigned)cdiv(ls * l, 256), 256, 0, st>>>(l, B, ldb, B32, ls);
     APL_LAUNCH_CHECK();
-    eye32_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32);
+    eye32_kernel<<<(unsigned)cdiv(ls * l, 256), 256, 0, st>>>(l, W32, ls);
     APL_LAUNCH_CHECK();
     // FP32 dot products summed lane-wise then by a 5-level tree: the relative error of
     // g / sqrt(a b) stays below (l/32 + 5) u32; the threshold sits above twice that
     const double tol32 = std::max(6e-6, 2.0 * ((double)l / 32.0 + 5.0) * 5.960464477539063e-8);
     const int64_t nb = cdiv(l, (int64_t)JW);
     const int64_t NB = nb + (nb % 2);
+    // W's columns ride along with B's when both fit in shared memory
+    const size_t smem_pre = ((size_t)2 * JW2 * ls + JW2 * JW2) * sizeof(float);
+    const bool wpre = smem_pre <= (size_t)kJac32SmemCap;
     // one value for every call: threads that build preconditioners concurrently must not
     // lower the cap under each other's launches
-    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel,
+    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
+    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     // per pair and sweep: the dot product g (2 l) and the rotation (6 l); the norms follow
     // the rotations
@@ -1406,11 +1575,15 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     // about the square of that, and the compensated stage converges from there in as
     // many sweeps as from the fully converged FP32 start.
     sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
-      jacobi32_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem, st>>>(l, NB, r, B32, W32,
-                                                                      (float)tol32, flag_dev);
+      if (wpre)
+        jacobi32_block_kernel<true><<<(unsigned)(NB / 2), 64 * JW, smem_pre, st>>>(
+            l, ls, NB, r, B32, W32, (float)tol32, flag_dev);
+      else
+        jacobi32_block_kernel<false><<<(unsigned)(NB / 2), 64 * JW, smem, st>>>(
+            l, ls, NB, r, B32, W32, (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI32, flops32, 0.0, 5e-3);
-    f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l2, W32, wk.jw64.p);
+    f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32, ls, wk.jw64.p);
     APL_LAUNCH_CHECK();
     // W is orthogonal only to FP32 accuracy; two Newton-Schulz steps
     // W <- W (3 I - W^T W) / 2 make it orthogonal to FP64 accuracy, so B W keeps the
@@ -1439,11 +1612,21 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     APL_CUDA(cudaFuncSetAttribute(jacobi_df_block_kernel,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     const double pairs = (double)(l * (l - 1)) / 2.0;
+    // the sweeps work on a hi/lo copy of B: split once here, joined once after
+    const int64_t ls = jacdf_ld(l);
+    DenseWork& wk = dense_work();
+    wk.jb32.alloc(2 * ls * l, st);
+    float2* D = reinterpret_cast<float2*>(wk.jb32.p);
+    APL_REQUIRE(((uintptr_t)D & 15) == 0, "jacobi_left: work buffer not 16-byte aligned");
+    split_df_kernel<<<(unsigned)cdiv(ls * l, 256), 256, 0, st>>>(l, B, ldb, D, ls);
+    APL_LAUNCH_CHECK();
     sweeps += run_sweeps(st, NB, 60, flag_dev, [&](int64_t r) {
-      jacobi_df_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem_df, st>>>(l, NB, r, B, ldb,
+      jacobi_df_block_kernel<<<(unsigned)(NB / 2), 64 * JW, smem_df, st>>>(l, ls, NB, r, D,
                                                                           (float)tol, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI, 2.0 * (double)l * pairs, 6.0 * (double)l, 1e-2 * std::sqrt(tol));
+    join_df_kernel<<<(unsigned)cdiv(l * l, 256), 256, 0, st>>>(l, D, ls, B, ldb);
+    APL_LAUNCH_CHECK();
   } else if (l > 1) {
     // Stage 2 (FP64): sweeps from the nearly orthogonal start down to l * eps
     const double tol = std::max(1e-15, (double)l * 1.1102230246251565e-16);

@@ -27,7 +27,9 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
 // One-sided Jacobi on the columns of the square B (l x l, in place, destroyed).
 // sigma receives the singular values of B in descending order and U (l x l, ldu) the
 // matching left singular vectors (normalised columns).  With B = M^T these are the
-// singular values and right singular vectors of M.  Returns the sweep count.
+// singular values and right singular vectors of M.  flag_dev is device scratch of at
+// least 3 ints.  Returns the sweep count; throws ST_ETIMEOUT when a bounded wait of a
+// sweep kernel gave up.
 int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
                 double* sigma, int* flag_dev);
 
