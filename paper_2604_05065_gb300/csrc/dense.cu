@@ -791,6 +791,7 @@ namespace {
 constexpr int JW = 8;
 constexpr int JW2 = 2 * JW;
 constexpr int kJac32SmemCap = 220 * 1024;  // dynamic shared memory cap of the FP32 stage
+constexpr int kJac32Wpp = 2;                // warps per column pair in the FP32 stage (4 measured slower)
 
 // Column stride of the FP32 stage's shared copy: l rounded up to a multiple of 4, so every
 // column starts on a 16-byte boundary and is read as float4; the pad holds zeros.
@@ -802,19 +803,22 @@ __device__ __forceinline__ float warp_allsumf(float v) {
   return v;
 }
 
-// Barrier of the two warps (64 threads) of pair slot pw; id 0 is __syncthreads'.
-__device__ __forceinline__ void pair_bar(int pw) {
-  asm volatile("bar.sync %0, 64;" ::"r"(pw + 1) : "memory");
+// Barrier of the warps of pair slot pw (64 threads, or 32 * wpp); id 0 is
+// __syncthreads'.
+__device__ __forceinline__ void pair_bar(int pw, int nthreads = 64) {
+  asm volatile("bar.sync %0, %1;" ::"r"(pw + 1), "r"(nthreads) : "memory");
 }
 
-// One pair (p, q) handled by two warps (interleaved float4 stretches).  Only g = x^T y is
-// a dot product: the squared norms a, b of the CTA's columns live in nrm and follow the
-// rotation exactly in exact arithmetic (a - t g, b + t g); a norm that the update would
-// lose to cancellation (below 1/16 of its old value) is summed again from the rotated
-// column.  The two warps meet at their own named barrier and add their halves in the
-// same order, so both take the same rotation.  All threads of the block call this; it
-// ends with a block-wide barrier, since the next inner round reads columns that other
-// pairs rotated.  Half 0 also rotates the columns p, q of the accumulated rotation R.
+// One pair (p, q) handled by WPP warps (interleaved float4 stretches; `half` is the
+// warp's part).  Only g = x^T y is a dot product: the squared norms a, b of the CTA's
+// columns live in nrm and follow the rotation exactly in exact arithmetic (a - t g,
+// b + t g); a norm that the update would lose to cancellation (below 1/16 of its old
+// value) is summed again from the rotated column.  The warps meet at their own named
+// barrier and add their parts in the same order, so all take the same rotation.  All
+// threads of the block call this; it ends with a block-wide barrier, since the next
+// inner round reads columns that other pairs rotated.  Part 0 also rotates the columns
+// p, q of the accumulated rotation R.
+template <int WPP>
 __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __restrict__ cq,
                                             float* __restrict__ R, float* __restrict__ nrm,
                                             int p, int q, bool valid, int64_t n4, float tol,
@@ -825,7 +829,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   float g0 = 0.f, g1 = 0.f;
   if (valid) {
 #pragma unroll 2
-    for (int64_t k = lane + 32 * half; k < n4; k += 64) {
+    for (int64_t k = lane + 32 * half; k < n4; k += 32 * WPP) {
       const float4 x = p4[k], y = q4[k];
       g0 = fmaf(x.x, y.x, g0);
       g1 = fmaf(x.y, y.y, g1);
@@ -835,8 +839,10 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   }
   float g = warp_allsumf(g0 + g1);
   if (lane == 0) xch[half] = g;
-  pair_bar(pw);
-  g = xch[0] + xch[1];
+  pair_bar(pw, 32 * WPP);
+  g = xch[0];
+#pragma unroll
+  for (int w = 1; w < WPP; ++w) g += xch[w];
   const float a = nrm[p], b = nrm[q];
   // no barrier before xch is written again: that happens after the closing barrier below
   // the angle needs only FP32 accuracy here (the next stage decides the final one), so
@@ -864,7 +870,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   const bool refresh = !(na >= 0.0625f * a) || !(nb >= 0.0625f * b);
   float sa = 0.f, sb = 0.f;
 #pragma unroll 2
-  for (int64_t k = lane + 32 * half; k < n4; k += 64) {
+  for (int64_t k = lane + 32 * half; k < n4; k += 32 * WPP) {
     const float4 x = p4[k], y = q4[k];
     float4 u, v;
     u.x = c * x.x - sn * y.x;
@@ -882,13 +888,18 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
       sb = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sb))));
     }
   }
-  if (refresh) {  // the same decision on both warps of the pair
+  if (refresh) {  // the same decision on every warp of the pair
     sa = warp_allsumf(sa);
     sb = warp_allsumf(sb);
-    if (lane == 0) { xch[2 + 2 * half] = sa; xch[3 + 2 * half] = sb; }
-    pair_bar(pw);
-    na = xch[2] + xch[4];
-    nb = xch[3] + xch[5];
+    if (lane == 0) { xch[WPP + 2 * half] = sa; xch[WPP + 1 + 2 * half] = sb; }
+    pair_bar(pw, 32 * WPP);
+    na = xch[WPP];
+    nb = xch[WPP + 1];
+#pragma unroll
+    for (int w = 1; w < WPP; ++w) {
+      na += xch[WPP + 2 * w];
+      nb += xch[WPP + 1 + 2 * w];
+    }
   }
   if (half == 0) {
     if (lane < JW2) {
@@ -955,15 +966,15 @@ __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// grid NB/2, block 64 * JW threads (two warps per pair).  B and W are l x l with column
+// grid NB/2, block 32 * WPP * JW threads (WPP warps per pair).  B and W are l x l with column
 // stride ls = jac32_ld(l) (zero pad rows), so every column is one 16-byte aligned bulk
 // copy.  Dynamic shared memory: JW2 columns of B, with WPRE also JW2 columns of W
 // (fetched with B, so the fetch overlaps the rotations), then R.  Without WPRE the W
 // columns are fetched into the B area after B has been stored.  rotated[0] counts
 // rotations, rotated[1] holds the largest rotated |cos| of the sweep (as float bits;
 // non-negative floats order like their bits), rotated[2] is set when a wait gave up.
-template <bool WPRE>
-__global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int64_t ls,
+template <bool WPRE, int WPP>
+__global__ void __launch_bounds__(32 * WPP * JW) jacobi32_block_kernel(int64_t l, int64_t ls,
                                                                  int64_t NB, int64_t r,
                                                                  float* __restrict__ B,
                                                                  float* __restrict__ W,
@@ -977,9 +988,9 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
   __shared__ float nrm[JW2];
   __shared__ int cta_rot, nvalid;
   __shared__ unsigned int cta_max;
-  __shared__ float xch[JW][6];
+  __shared__ float xch[JW][3 * WPP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pw = warp >> 1, half = warp & 1;
+  const int pw = warp / WPP, half = warp % WPP;  // pair slot and part of this warp
   const int64_t k = blockIdx.x;
   const int64_t bp = rr_elem(k, r, NB), bq = rr_elem(NB - 1 - k, r, NB);
   if (threadIdx.x < JW2) {
@@ -1021,8 +1032,8 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
   }
   __syncthreads();  // the zero columns written by other threads
   const int64_t n4 = ls / 4;
-  {
-    // squared column norms, one warp per column (the block has JW2 warps)
+  if (warp < JW2) {
+    // squared column norms, one warp per column
     const float4* c4 = reinterpret_cast<const float4*>(cols + (size_t)warp * ls);
     float s0 = 0.f, s1 = 0.f;
     for (int64_t q = lane; q < n4; q += 32) {
@@ -1044,13 +1055,13 @@ __global__ void __launch_bounds__(64 * JW) jacobi32_block_kernel(int64_t l, int6
       if (p > q) { const int z = p; p = q; q = z; }
       p += side * JW;
       q += side * JW;
-      jac32_pair2(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
+      jac32_pair2<WPP>(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
                   gcol[p] >= 0 && gcol[q] >= 0, n4, tol, lane, half, pw, xch[pw], rot, mx);
     }
   }
   for (int ir = 0; ir < JW; ++ir) {
     const int p = pw, q = JW + (pw + ir) % JW;
-    jac32_pair2(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
+    jac32_pair2<WPP>(cols + (size_t)p * ls, cols + (size_t)q * ls, R, nrm, p, q,
                 gcol[p] >= 0 && gcol[q] >= 0, n4, tol, lane, half, pw, xch[pw], rot, mx);
   }
   if (lane == 0 && half == 0 && rot) {
@@ -1564,9 +1575,9 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     const bool wpre = smem_pre <= (size_t)kJac32SmemCap;
     // one value for every call: threads that build preconditioners concurrently must not
     // lower the cap under each other's launches
-    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<true>,
+    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<true, kJac32Wpp>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
-    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<false>,
+    APL_CUDA(cudaFuncSetAttribute(jacobi32_block_kernel<false, kJac32Wpp>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kJac32SmemCap));
     // per pair and sweep: the dot product g (2 l) and the rotation (6 l); the norms follow
     // the rotations
@@ -1576,11 +1587,13 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     // many sweeps as from the fully converged FP32 start.
     sweeps += run_sweeps(st, NB, 40, flag_dev, [&](int64_t r) {
       if (wpre)
-        jacobi32_block_kernel<true><<<(unsigned)(NB / 2), 64 * JW, smem_pre, st>>>(
-            l, ls, NB, r, B32, W32, (float)tol32, flag_dev);
+        jacobi32_block_kernel<true, kJac32Wpp><<<(unsigned)(NB / 2), 32 * kJac32Wpp * JW,
+                                                 smem_pre, st>>>(l, ls, NB, r, B32, W32,
+                                                                 (float)tol32, flag_dev);
       else
-        jacobi32_block_kernel<false><<<(unsigned)(NB / 2), 64 * JW, smem, st>>>(
-            l, ls, NB, r, B32, W32, (float)tol32, flag_dev);
+        jacobi32_block_kernel<false, kJac32Wpp><<<(unsigned)(NB / 2), 32 * kJac32Wpp * JW,
+                                                  smem, st>>>(l, ls, NB, r, B32, W32,
+                                                              (float)tol32, flag_dev);
       APL_LAUNCH_CHECK();
     }, PROF_JACOBI32, flops32, 0.0, 5e-3);
     f2d_kernel<<<(unsigned)cdiv(l2, 256), 256, 0, st>>>(l, W32, ls, wk.jw64.p);
