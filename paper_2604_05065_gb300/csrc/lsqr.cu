@@ -136,10 +136,16 @@ struct Acc<2> {
   __device__ __forceinline__ double get() const { return df_val(v); }
 };
 
-// ---- K1: rows of A, two rows per warp -------------------------------------------------
+// ---- K1: rows of A, K1_RPW rows per warp ----------------------------------------------
+
+// Rows per warp of the dense A z pass.  The grid gives every warp one group of rows
+// (while the rows fit in one resident wave: FP32 A is held to 48 registers, five blocks
+// per SM), so no warp streams a second group while the others idle, and each load of z
+// serves all rows of the group.
+constexpr int K1_RPW = 4;
 
 template <typename TA, int MODE, bool VEC>
-__global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
+__global__ void __launch_bounds__(NT, sizeof(TA) == 4 ? 5 : 1) k1_dense(int64_t m, int64_t n, int64_t ld,
                                                const TA* __restrict__ A,
                                                const double* __restrict__ z,
                                                const float* __restrict__ zh,
@@ -156,72 +162,59 @@ __global__ void __launch_bounds__(NT) k1_dense(int64_t m, int64_t n, int64_t ld,
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   double ss = 0.0;
-  for (int64_t i0 = 2 * warp; i0 < m; i0 += 2 * nwarps) {
-    const bool two = i0 + 1 < m;
-    const TA* a0 = A + i0 * ld;
-    const TA* a1 = A + (two ? i0 + 1 : i0) * ld;
-    Acc<MODE> s0, s1;
+  for (int64_t i0 = (int64_t)K1_RPW * warp; i0 < m; i0 += (int64_t)K1_RPW * nwarps) {
+    const int nr = (int)(m - i0 < K1_RPW ? m - i0 : K1_RPW);
+    const TA* ar[K1_RPW];
+#pragma unroll
+    for (int r = 0; r < K1_RPW; ++r) ar[r] = A + (i0 + (r < nr ? r : nr - 1)) * ld;
+    Acc<MODE> s[K1_RPW];
     int64_t jt = 0;
     if constexpr (VEC && MODE != 0 && sizeof(TA) == 4) {
       const int64_t n4 = n >> 2;
-      const float4* p0 = reinterpret_cast<const float4*>(a0);
-      const float4* p1 = reinterpret_cast<const float4*>(a1);
       const float4* hv = reinterpret_cast<const float4*>(zh);
       const float4* lv = reinterpret_cast<const float4*>(zl);
-      int64_t q = lane;
-      // two stretches per pass with every load issued first: 1 KB of A in flight per warp
-      for (; q + 32 < n4; q += 64) {
-        float4 x0[2], x1[2], h[2], l[2];
+      // one stretch of every row per pass, all loads issued first: 2 KB of A in flight per
+      // warp, and each z load serves K1_RPW rows
+#pragma unroll 1
+      for (int64_t q = lane; q < n4; q += 32) {
+        float4 x[K1_RPW];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          x0[u] = __ldcs(p0 + q + 32 * u);
-          x1[u] = __ldcs(p1 + q + 32 * u);
-          h[u] = hv[q + 32 * u];
-          l[u] = MODE == 2 ? lv[q + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          s0.add(x0[u].x, 0.0, h[u].x, l[u].x); s0.add(x0[u].y, 0.0, h[u].y, l[u].y);
-          s0.add(x0[u].z, 0.0, h[u].z, l[u].z); s0.add(x0[u].w, 0.0, h[u].w, l[u].w);
-          s1.add(x1[u].x, 0.0, h[u].x, l[u].x); s1.add(x1[u].y, 0.0, h[u].y, l[u].y);
-          s1.add(x1[u].z, 0.0, h[u].z, l[u].z); s1.add(x1[u].w, 0.0, h[u].w, l[u].w);
-        }
-      }
-      for (; q < n4; q += 32) {
-        const float4 x0 = __ldcs(p0 + q);
-        const float4 x1 = __ldcs(p1 + q);
+        for (int r = 0; r < K1_RPW; ++r) x[r] = __ldcs(reinterpret_cast<const float4*>(ar[r]) + q);
         const float4 h = hv[q];
-        float4 l = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (MODE == 2) l = lv[q];
-        s0.add(x0.x, 0.0, h.x, l.x); s0.add(x0.y, 0.0, h.y, l.y);
-        s0.add(x0.z, 0.0, h.z, l.z); s0.add(x0.w, 0.0, h.w, l.w);
-        s1.add(x1.x, 0.0, h.x, l.x); s1.add(x1.y, 0.0, h.y, l.y);
-        s1.add(x1.z, 0.0, h.z, l.z); s1.add(x1.w, 0.0, h.w, l.w);
+        const float4 l = MODE == 2 ? lv[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < K1_RPW; ++r) {
+          s[r].add(x[r].x, 0.0, h.x, l.x);
+          s[r].add(x[r].y, 0.0, h.y, l.y);
+          s[r].add(x[r].z, 0.0, h.z, l.z);
+          s[r].add(x[r].w, 0.0, h.w, l.w);
+        }
       }
       jt = n4 << 2;
     }
     for (int64_t j = jt + lane; j < n; j += 32) {
       if constexpr (MODE == 0) {
-        s0.add((double)a0[j], z[j], 0.f, 0.f);
-        s1.add((double)a1[j], z[j], 0.f, 0.f);
+        const double zj = z[j];
+#pragma unroll
+        for (int r = 0; r < K1_RPW; ++r) s[r].add((double)ar[r][j], zj, 0.f, 0.f);
       } else {
+        const float h = zh[j];
         const float l = MODE == 2 ? zl[j] : 0.f;
-        s0.add((float)a0[j], 0.0, zh[j], l);
-        s1.add((float)a1[j], 0.0, zh[j], l);
+#pragma unroll
+        for (int r = 0; r < K1_RPW; ++r) s[r].add((float)ar[r][j], 0.0, h, l);
       }
     }
-    const double d0 = warp_sum(s0.get());
-    const double d1 = warp_sum(s1.get());
+    double d[K1_RPW];
+#pragma unroll
+    for (int r = 0; r < K1_RPW; ++r) d[r] = warp_sum(s[r].get());
     if (lane == 0) {
-      const double v0 = ca * d0 + cu * u[i0];
-      u[i0] = v0;
-      ss += v0 * v0;
-      if (uh) split(v0, uh, ul, i0);
-      if (two) {
-        const double v1 = ca * d1 + cu * u[i0 + 1];
-        u[i0 + 1] = v1;
-        ss += v1 * v1;
-        if (uh) split(v1, uh, ul, i0 + 1);
+#pragma unroll
+      for (int r = 0; r < K1_RPW; ++r) {
+        if (r >= nr) break;
+        const double v = ca * d[r] + cu * u[i0 + r];
+        u[i0 + r] = v;
+        ss += v * v;
+        if (uh) split(v, uh, ul, i0 + r);
       }
     }
   }
@@ -766,7 +759,7 @@ void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_it
   vec_ = A.fmt == 0 && A.dtype == 1 && (A.ld % 4 == 0) &&
          ((reinterpret_cast<uintptr_t>(A.vals) & 15) == 0);
   if (A.fmt == 0) {
-    k1_blocks_ = (int)std::min<int64_t>(cdiv(cdiv(m_, 2) * 32, NT), sm_blocks());
+    k1_blocks_ = (int)std::min<int64_t>(cdiv(cdiv(m_, K1_RPW) * 32, NT), sm_blocks());
     const int64_t cb = vec_ ? cdiv(cdiv(n_, 4), NT) : cdiv(n_, NT);
     k2_rchunks_ = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, cb), cdiv(m_, 32)));
     k2_blocks_ = (int)std::min<int64_t>(cdiv(n_, NT), sm_blocks());
