@@ -14,20 +14,34 @@ __device__ __forceinline__ double ld_val(const void* p, int64_t i) {
 
 // ---- sketch ---------------------------------------------------------------------------
 
-// Dense: thread (r, j) sums the rows of A listed for sketch row r, ascending.
+// FP32 -> FP64 by moving the bits (exact for normal numbers; zero, subnormals, infinities
+// and NaN take the conversion instruction): GB300 runs conversions to FP64 at its FP64
+// rate, integer operations at full rate.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
+                        ((uint64_t)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// Dense: thread (r, j) sums the rows of A listed for sketch row r, ascending.  The sign is
+// applied before widening (negation is exact), so each term costs one FP64 add.
 template <typename T>
 __global__ void sketch_dense_kernel(int64_t n, int64_t ld, const T* __restrict__ A, int s,
                                     const int* __restrict__ tptr, const int* __restrict__ ti,
                                     const signed char* __restrict__ tsgn, double scale,
                                     double* __restrict__ Y) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  const int r = blockIdx.x;
   if (j >= n) return;
   double acc = 0.0;
   const int e0 = tptr[r], e1 = tptr[r + 1];
   for (int e = e0; e < e1; ++e) {
-    const double a = (double)A[(int64_t)ti[e] * ld + j];
-    acc = tsgn[e] > 0 ? acc + a : acc - a;
+    const T a = A[(int64_t)ti[e] * ld + j];
+    acc += widen(tsgn[e] > 0 ? a : -a);
   }
   Y[r + j * (int64_t)s] = acc * scale;
 }
@@ -39,8 +53,8 @@ __global__ void sketch_csc_kernel(int64_t n, const int* __restrict__ colptr,
                                   int s, int xi, const int* __restrict__ srows,
                                   const signed char* __restrict__ ssign, double scale,
                                   double* __restrict__ Y) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  const int r = blockIdx.x;
   if (j >= n) return;
   double acc = 0.0;
   for (int e = colptr[j]; e < colptr[j + 1]; ++e) {
@@ -228,10 +242,11 @@ __global__ void lupp_init_kernel(int64_t N, int* pos_of, int* row_at, double* ma
 // launch).  Block b owns the 32-row tiles b, b + G, b + 2G, ... (G blocks); a step updates
 // the owned rows and finds each block's best candidate (phase A), the blocks meet at a
 // grid barrier, and every block merges the G partial candidates itself (phase B), so all
-// of them know the pivot without a second barrier.  Only the owner of a row reads or
-// writes its position: the swap of step j (pivot row to position j, the row that held
+// of them know the pivot without a second barrier.  The positions of a block's rows live
+// in its shared memory: the swap of step j (pivot row to position j, the row that held
 // position j to the pivot's old position) is applied by the owners when they read the
-// positions in step j + 1.  Partial candidates alternate between two buffers by step
+// positions in step j + 1.  Column j of the owned rows, found while forming the
+// candidates, stays in shared memory for step j + 1's multipliers.  Partial candidates alternate between two buffers by step
 // parity: a block can run at most one step ahead of the slowest.
 
 constexpr long long kLuppSpin = 1LL << 22;  // polls of the grid barrier before it gives up
@@ -274,16 +289,26 @@ __device__ bool lupp_grid_sync(unsigned* bar, int* err) {
 }
 
 __global__ void __launch_bounds__(256) lupp_coop_kernel(
-    int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int k,
-    int* __restrict__ pos_of, int* __restrict__ piv, long long* __restrict__ pv,
-    int* __restrict__ pp, long long* __restrict__ ps, int* __restrict__ pr, unsigned* bar,
-    double* margin, int* iscal) {
-  extern __shared__ double prow[];  // pivot row values for columns j-1 .. K-1, then 1/pivot
+    int64_t N, int64_t K, double* __restrict__ X, int64_t rs, int64_t cs, int k, int tpb,
+    int* __restrict__ piv, long long* __restrict__ pv, int* __restrict__ pp,
+    long long* __restrict__ ps, int* __restrict__ pr, unsigned* bar, double* margin,
+    int* iscal) {
+  // dynamic shared memory: the pivot row for columns j-1 .. K-1 and 1/pivot (K + 1), then
+  // column j-1 / j of the owned rows by step parity (2 x tpb x 32), then the owned rows'
+  // positions (tpb x 32 ints); tpb bounds the tiles a block owns
+  extern __shared__ double prow[];
+  double* xcol = prow + (K + 1);
+  int* spos = reinterpret_cast<int*>(xcol + 2 * (int64_t)tpb * 32);
   __shared__ long long s_v, s_sec;
   __shared__ int s_pos, s_row;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int64_t ntiles = (N + 31) / 32;
+  for (int e = threadIdx.x; e < tpb * 32; e += blockDim.x) {
+    const int64_t i = (blockIdx.x + (int64_t)(e / 32) * gridDim.x) * 32 + (e % 32);
+    spos[e] = i < N ? (int)i : -1;
+  }
+  __syncthreads();
   int p = -1;     // pivot row of the previous step
   int ppos = -1;  // its position before that step's swap
   for (int j = 0; j < k; ++j) {
@@ -295,27 +320,31 @@ __global__ void __launch_bounds__(256) lupp_coop_kernel(
       if (threadIdx.x == 0) prow[K - (j - 1)] = 1.0 / prow[0];
       __syncthreads();
     }
+    const double* xprev = xcol + (int64_t)((j + 1) & 1) * tpb * 32;  // column j - 1
+    double* xnext = xcol + (int64_t)(j & 1) * tpb * 32;               // column j
     Cand mine{-1, INT_MAX, -1, -1};
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int lt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const int64_t i = tile * 32 + lane;
+      const int slot = lt * 32 + lane;
       int pi = -1;
       if (i < N) {
-        pi = pos_of[i];
+        pi = spos[slot];
         if (j > 0) {
           // the swap of step j - 1 (idempotent, so every warp may apply it)
           const int q = (i == p) ? j - 1 : (pi == j - 1 ? ppos : pi);
           if (q != pi) {
             pi = q;
-            if (wid == 0) pos_of[i] = q;
+            if (wid == 0) spos[slot] = q;
           }
         }
       }
       const bool live = i < N && pi >= j;
       double* xi = X + i * rs;
-      double l = 0.0;
-      if (live && j > 0) l = xi[(int64_t)(j - 1) * cs] * prow[K - (j - 1)];
-      __syncthreads();  // every warp has read X(i, j-1) before it is overwritten
       if (live) {
+        // X(i, j - 1) was kept from the previous step, so no warp reads it from memory
+        // and warp 0 may overwrite it with the multiplier at once
+        const double l = j > 0 ? xprev[slot] * prow[K - (j - 1)] : 0.0;
         if (j > 0 && wid == 0) xi[(int64_t)(j - 1) * cs] = l;
         for (int64_t c0 = j + wid; c0 < K; c0 += (int64_t)nw * LUPP_U) {
           double v[LUPP_U];
@@ -332,7 +361,10 @@ __global__ void __launch_bounds__(256) lupp_coop_kernel(
               v[u] = v[u] - l * prow[c - (j - 1)];
               xi[c * cs] = v[u];
             }
-            if (c == j) mine = cand_merge(mine, Cand{abs_key(v[u]), pi, -1, (int)i});
+            if (c == j) {
+              mine = cand_merge(mine, Cand{abs_key(v[u]), pi, -1, (int)i});
+              xnext[slot] = v[u];
+            }
           }
         }
       }
@@ -559,7 +591,11 @@ __global__ void fill_int_kernel(int* p, int64_t n, int v) {
 void sketch(cudaStream_t st, const MatView& A, int s, int xi, const int* tptr, const int* ti,
             const signed char* tsgn, const int* srows, const signed char* ssign, double scale,
             double* Y) {
-  dim3 grid((unsigned)cdiv(A.n, 128), (unsigned)s);
+  // sketch rows vary fastest across blocks: the blocks resident together cover every
+  // sketch row of a few 128-column strips of A, so a strip is read from HBM about once and
+  // its other reads (one per nonzero of the sketch column) hit L2
+  APL_REQUIRE(cdiv(A.n, 128) <= 65535, "sketch: n too large");
+  dim3 grid((unsigned)s, (unsigned)cdiv(A.n, 128));
   if (A.fmt == 0) {
     if (A.dtype == 0)
       sketch_dense_kernel<double><<<grid, 128, 0, st>>>(A.n, A.ld, (const double*)A.vals, s, tptr,
@@ -604,18 +640,27 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
   const size_t shm = (size_t)(K + 1) * sizeof(double);
   // one cooperative launch when the device offers it and the caller runs no concurrent
   // selections; one launch per step otherwise
-  int coop_grid = 0;
+  int coop_grid = 0, tpb = 0;
+  size_t coop_shm = 0;
   if (w.cooperative) {
     int dev = 0, coop = 0, nsm = 0, per_sm = 0;
     APL_CUDA(cudaGetDevice(&dev));
     APL_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     APL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    APL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lupp_coop_kernel, threads,
-                                                           shm));
-    if (coop && per_sm > 0) {
+    // shared memory for the most tiles a block can own (one block per SM)
+    const int64_t tpb_max = cdiv(blocks64, (int64_t)nsm);
+    coop_shm = shm + (size_t)tpb_max * 32 * (2 * sizeof(double) + sizeof(int));
+    if (coop && coop_shm <= 200 * 1024) {
+      APL_CUDA(cudaFuncSetAttribute(lupp_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      APL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lupp_coop_kernel, threads,
+                                                             coop_shm));
+    }
+    if (per_sm > 0) {
       // as few blocks as give the same number of tiles to the busiest block
       const int64_t per_block = cdiv(blocks64, (int64_t)per_sm * nsm);
       coop_grid = (int)cdiv(blocks64, per_block);
+      tpb = (int)cdiv(blocks64, (int64_t)coop_grid);
     }
   }
   const int tok = prof_begin(st);
@@ -624,7 +669,6 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
     w.cs.alloc(2 * (size_t)coop_grid, st);
     w.cp.alloc(2 * (size_t)coop_grid, st);
     w.cr.alloc(2 * (size_t)coop_grid, st);
-    int* pos_of = w.pos_of.p;
     int* piv = w.piv.p;
     long long* pv = w.cv.p;
     int* pp = w.cp.p;
@@ -634,10 +678,10 @@ int lupp_select(cudaStream_t st, int64_t N, int64_t K, double* X, int64_t rs, in
     double* mg = w.scal.p;
     int* isc = w.iscal.p;
     void* args[] = {(void*)&N, (void*)&K, (void*)&X, (void*)&rs, (void*)&cs, (void*)&k,
-                    (void*)&pos_of, (void*)&piv, (void*)&pv, (void*)&pp, (void*)&ps,
+                    (void*)&tpb, (void*)&piv, (void*)&pv, (void*)&pp, (void*)&ps,
                     (void*)&pr, (void*)&bar, (void*)&mg, (void*)&isc};
     APL_CUDA(cudaLaunchCooperativeKernel((const void*)lupp_coop_kernel, dim3(coop_grid),
-                                         dim3(threads), args, shm, st));
+                                         dim3(threads), args, coop_shm, st));
     APL_LAUNCH_CHECK();
   } else {
     for (int j = 0; j < k; ++j) {

@@ -829,7 +829,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   float g0 = 0.f, g1 = 0.f;
   if (valid) {
 #pragma unroll 2
-    for (int64_t k = lane + 32 * half; k < n4; k += 32 * WPP) {
+    for (int k = lane + 32 * half; k < (int)n4; k += 32 * WPP) {
       const float4 x = p4[k], y = q4[k];
       g0 = fmaf(x.x, y.x, g0);
       g1 = fmaf(x.y, y.y, g1);
@@ -870,7 +870,7 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
   const bool refresh = !(na >= 0.0625f * a) || !(nb >= 0.0625f * b);
   float sa = 0.f, sb = 0.f;
 #pragma unroll 2
-  for (int64_t k = lane + 32 * half; k < n4; k += 32 * WPP) {
+  for (int k = lane + 32 * half; k < (int)n4; k += 32 * WPP) {
     const float4 x = p4[k], y = q4[k];
     float4 u, v;
     u.x = c * x.x - sn * y.x;
@@ -1242,7 +1242,7 @@ __device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __r
   float gs = 0.f, gc = 0.f, hs = 0.f, hc = 0.f;
   if (valid) {
 #pragma unroll 2
-    for (int64_t k = lane + 32 * half; k < n2; k += 64) {
+    for (int k = lane + 32 * half; k < (int)n2; k += 64) {
       const float4 x = cp[k], y = cq[k];
       df_dot_add(gs, gc, x.x, x.y, y.x, y.y);
       df_dot_add(hs, hc, x.z, x.w, y.z, y.w);
@@ -1293,7 +1293,7 @@ __device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __r
   const bool small = fabsf(t) <= 1.1920928955078125e-7f;
   const float em = __fadd_rn(__fsub_rn(ch, 1.f), cl);  // c - 1
 #pragma unroll 2
-  for (int64_t k = lane + 32 * half; k < n2; k += 64) {
+  for (int k = lane + 32 * half; k < (int)n2; k += 64) {
     const float4 x = cp[k];
     const float4 y = cq[k];
     float4 u, v;
