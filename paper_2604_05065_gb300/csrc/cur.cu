@@ -2,6 +2,7 @@
 #include <climits>
 
 #include "cur.cuh"
+#include "df32.cuh"
 
 namespace apl {
 
@@ -13,19 +14,6 @@ __device__ __forceinline__ double ld_val(const void* p, int64_t i) {
 }
 
 // ---- sketch ---------------------------------------------------------------------------
-
-// FP32 -> FP64 by moving the bits (exact for normal numbers; zero, subnormals, infinities
-// and NaN take the conversion instruction): GB300 runs conversions to FP64 at its FP64
-// rate, integer operations at full rate.
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t ex = (u >> 23) & 0xffu;
-  if (ex == 0u || ex == 0xffu) return (double)f;
-  const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
-                        ((uint64_t)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)bits);
-}
-__device__ __forceinline__ double widen(double d) { return d; }
 
 // Dense: thread (r, j) sums the rows of A listed for sketch row r, ascending.  The sign is
 // applied before widening (negation is exact), so each term costs one FP64 add.

@@ -10,6 +10,20 @@ struct DF {
   float s, c;
 };
 
+// FP32 -> FP64 by moving the bits (exact for normal numbers; zero, subnormals, infinities
+// and NaN take the conversion instruction): GB300 runs conversions to FP64 at its FP64
+// rate, integer operations at full rate.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
+                        ((uint64_t)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+
 // s + c += a * (h + l).  Explicit round-to-nearest intrinsics keep the compiler from
 // contracting the error terms.
 __device__ __forceinline__ void df_fma(DF& acc, float a, float h, float l) {

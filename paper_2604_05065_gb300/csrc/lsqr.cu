@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(NT, sizeof(TA) == 4 ? 5 : 1) k1_dense(int64_t 
       if constexpr (MODE == 0) {
         const double zj = z[j];
 #pragma unroll
-        for (int r = 0; r < K1_RPW; ++r) s[r].add((double)ar[r][j], zj, 0.f, 0.f);
+        for (int r = 0; r < K1_RPW; ++r) s[r].add(widen(ar[r][j]), zj, 0.f, 0.f);
       } else {
         const float h = zh[j];
         const float l = MODE == 2 ? zl[j] : 0.f;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NT) k1_csr(int64_t m, int64_t n, const int* __
       const int e1 = rowptr[i + 1];
       for (int e = rowptr[i]; e < e1; ++e) {
         const int c = colidx[e];
-        if constexpr (MODE == 0) acc.add((double)vals[e], z[c], 0.f, 0.f);
+        if constexpr (MODE == 0) acc.add(widen(vals[e]), z[c], 0.f, 0.f);
         else acc.add((float)vals[e], 0.0, zh[c], MODE == 2 ? zl[c] : 0.f);
       }
       val = ca * acc.get() + cu * u[i];
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NT) k2_csr(int64_t m, int64_t n, const int* __
     const int e1 = colptr[j + 1];
     for (int e = colptr[j]; e < e1; ++e) {
       const int r = rowidx[e];
-      if constexpr (MODE == 0) acc.add((double)cvals[e], u[r], 0.f, 0.f);
+      if constexpr (MODE == 0) acc.add(widen(cvals[e]), u[r], 0.f, 0.f);
       else acc.add((float)cvals[e], 0.0, uh[r], MODE == 2 ? ul[r] : 0.f);
     }
     const double gj = us * (acc.get() + delta * u[m + j]);
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(NT) k2a_dense(int64_t m, int64_t n, int64_t ld
     if (j >= n) return;
     Acc<MODE> a;
     for (int64_t i = r0; i < r1; ++i) {
-      if constexpr (MODE == 0) a.add((double)A[i * ld + j], u[i], 0.f, 0.f);
+      if constexpr (MODE == 0) a.add(widen(A[i * ld + j]), u[i], 0.f, 0.f);
       else a.add((float)A[i * ld + j], 0.0, uh[i], MODE == 2 ? ul[i] : 0.f);
     }
     out[j] = a.get();
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(NT) mv_dense_rows(int64_t m, int64_t n, int64_
     const TA* a = A + i * ld;
     Acc<MODE> acc;
     for (int64_t j = lane; j < n; j += 32) {
-      if constexpr (MODE == 0) acc.add((double)a[j], x[j], 0.f, 0.f);
+      if constexpr (MODE == 0) acc.add(widen(a[j]), x[j], 0.f, 0.f);
       else acc.add((float)a[j], 0.0, xh[j], MODE == 2 ? xl[j] : 0.f);
     }
     const double s = warp_sum(acc.get());
@@ -610,7 +610,7 @@ __global__ void mv_csr_rows(int64_t m, const int* __restrict__ rowptr,
   Acc<MODE> acc;
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
     const int c = colidx[e];
-    if constexpr (MODE == 0) acc.add((double)vals[e], x[c], 0.f, 0.f);
+    if constexpr (MODE == 0) acc.add(widen(vals[e]), x[c], 0.f, 0.f);
     else acc.add((float)vals[e], 0.0, xh[c], MODE == 2 ? xl[c] : 0.f);
   }
   const double s = acc.get();
@@ -627,7 +627,7 @@ __global__ void mv_csc_cols(int64_t n, const int* __restrict__ colptr,
   Acc<MODE> acc;
   for (int e = colptr[j]; e < colptr[j + 1]; ++e) {
     const int r = rowidx[e];
-    if constexpr (MODE == 0) acc.add((double)cvals[e], x[r], 0.f, 0.f);
+    if constexpr (MODE == 0) acc.add(widen(cvals[e]), x[r], 0.f, 0.f);
     else acc.add((float)cvals[e], 0.0, xh[r], MODE == 2 ? xl[r] : 0.f);
   }
   y[j] = acc.get();
