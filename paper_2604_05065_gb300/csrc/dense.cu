@@ -838,12 +838,14 @@ __device__ __forceinline__ void jac32_pair2(float* __restrict__ cp, float* __res
     }
   }
   float g = warp_allsumf(g0 + g1);
+  // read before the pair barrier: part 0 rewrites them after it, so every warp of the
+  // pair sees the same values
+  const float a = nrm[p], b = nrm[q];
   if (lane == 0) xch[half] = g;
   pair_bar(pw, 32 * WPP);
   g = xch[0];
 #pragma unroll
   for (int w = 1; w < WPP; ++w) g += xch[w];
-  const float a = nrm[p], b = nrm[q];
   // no barrier before xch is written again: that happens after the closing barrier below
   // the angle needs only FP32 accuracy here (the next stage decides the final one), so
   // it is formed with the approximate reciprocal square root and division
@@ -1250,11 +1252,13 @@ __device__ __forceinline__ void jacdf_pair2(float4* __restrict__ cp, float4* __r
   }
   df_add(gs, gc, hs, hc);
   df_warp_allsum(gs, gc);
+  // read before the pair barrier: half 0 rewrites them after it, so both warps see the
+  // same values
+  const float A = nh[p], Al = nl[p], Bv = nh[q], Bl = nl[q];
   if (lane == 0) { xch[2 * half] = gs; xch[2 * half + 1] = gc; }
   pair_bar(pw);
   float G = xch[0], Gl = xch[1];
   df_add(G, Gl, xch[2], xch[3]);
-  const float A = nh[p], Al = nl[p], Bv = nh[q], Bl = nl[q];
   // no barrier before xch is written again: that happens after the closing barrier below
   const float relg = (valid && A > 0.f && Bv > 0.f) ? fabsf(G) / (sqrtf(A) * sqrtf(Bv)) : 0.f;
   if (!(relg > tol)) {
