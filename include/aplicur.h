@@ -122,11 +122,13 @@ typedef struct {
  * last aplicur_reset_profile (requires options.profile).  Families:
  *  0 the A z pass, 1 the A^T u pass, 2 the preconditioner passes (LSQR hot loop;
  *    timed by events inside the captured iteration graphs);
- *  3 FP64 GEMMs (including those inside triangular solves and Cholesky),
- *  4 FP64 Jacobi sweeps of the preconditioner SVD, 5 LUPP index selection,
- *  6 FP32 Jacobi sweeps (the first stage of the SVD).
- * work[k] is algorithmic bytes for families 0, 1, 2, 5, FP64 flops for 3, 4 and FP32
- * flops for 6. */
+ *  3 dense products (GEMMs, including those inside triangular solves and Cholesky;
+ *    compensated FP32 by default, FP64 with fp64_dense),
+ *  4 the second Jacobi stage of the preconditioner SVD (compensated FP32 by default,
+ *    FP64 with fp64_dense), 5 LUPP index selection,
+ *  6 the first, FP32 Jacobi stage of the SVD.
+ * work[k] is algorithmic bytes for families 0, 1, 2, 5, FP64-equivalent flops for 3, 4
+ * and FP32 flops for 6. */
 typedef struct {
   double ms[7];              /* summed event-to-event device time */
   int64_t launches[7];       /* timed regions (kernel launches, sweeps, selections) */

@@ -49,8 +49,8 @@ class Profile(C.Structure):
 
 # kernel families of aplicur_profile: (name, unit of work)
 PROFILE_FAMILIES = [("A z pass", "bytes"), ("A^T u pass", "bytes"),
-                    ("preconditioner passes", "bytes"), ("FP64 GEMM", "flops"),
-                    ("FP64 Jacobi sweeps", "flops"), ("LUPP selection", "bytes"),
+                    ("preconditioner passes", "bytes"), ("dense products", "flops"),
+                    ("second Jacobi stage", "flops"), ("LUPP selection", "bytes"),
                     ("FP32 Jacobi sweeps", "flops32")]
 
 
