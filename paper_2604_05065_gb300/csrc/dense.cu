@@ -87,296 +87,6 @@ void prof_set_work(int token, double work) {
 }
 
 // ------------------------------------------------------------------------------------
-// GEMM: 64 x 64 output tile per 256-thread block, 4 x 4 outputs per thread, K step 16.
-// Two arithmetic forms: FP64 (dgemm_kernel) and compensated FP32 (df32gemm_kernel, the
-// default; the context's DenseWork selects).
-// ------------------------------------------------------------------------------------
-namespace {
-constexpr int GBM = 64, GBN = 64, GBK = 16;
-
-// blockIdx.z selects a K range of length kchunk; with part != NULL the block writes its
-// unscaled partial product to part + z * M * N (leading dimension M) instead of C.
-__global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int64_t M,
-                                                    int64_t N, int64_t K, double alpha,
-                                                    const double* __restrict__ A, int64_t lda,
-                                                    const double* __restrict__ B, int64_t ldb,
-                                                    double beta, double* __restrict__ C,
-                                                    int64_t ldc, int64_t kchunk,
-                                                    double* __restrict__ part) {
-  __shared__ double As[GBK][GBM + 1];
-  __shared__ double Bs[GBK][GBN + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-
-  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
-  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int lin = threadIdx.x + e * 256;  // 0..1023
-      int mm, kk;
-      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
-      const int64_t gm = m0 + mm, gk = k0 + kk;
-      double v = 0.0;
-      if (gm < M && gk < kend) v = transA ? A[gk + gm * lda] : A[gm + gk * lda];
-      As[kk][mm] = v;
-      int nn;
-      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
-      const int64_t gn = n0 + nn, gk2 = k0 + kk;
-      double w = 0.0;
-      if (gn < N && gk2 < kend) w = transB ? B[gn + gk2 * ldb] : B[gk2 + gn * ldb];
-      Bs[kk][nn] = w;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
-      if (part) {
-        part[(int64_t)blockIdx.z * M * N + gm + gn * M] = acc[i][j];
-      } else {
-        double* c = C + gm + gn * ldc;
-        *c = (beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
-      }
-    }
-  }
-}
-
-// The same tiling with compensated FP32 arithmetic.  Every FP64 operand is split once per
-// call into FP32 hi + lo arrays (split_kernel; hi + lo keeps 48 of its 53 bits), a product
-// is formed exactly in its hi * hi part (an FMA gives the rounding error) plus the two
-// cross terms, and the running sum is an unevaluated FP32 pair updated by Knuth's TwoSum.
-// The result is accurate to about 2^-46 relative to sum |a_i b_i| and the inner loop has
-// only FP32 instructions, which GB300 issues at 64 times its FP64 rate.  The operands
-// arrive compact: op(A) source rows x cols with leading dimension = rows (same for B).
-__global__ void split_kernel(int64_t rows, int64_t cols, const double* __restrict__ src,
-                             int64_t ld, float* __restrict__ hi, float* __restrict__ lo) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= rows * cols) return;
-  const int64_t r = e % rows, c = e / rows;
-  const double v = src[r + c * ld];
-  const float h = __double2float_rn(v);
-  hi[e] = h;
-  lo[e] = __double2float_rn(v - (double)h);
-}
-
-__global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, int64_t M,
-                                                       int64_t N, int64_t K, double alpha,
-                                                       const float* __restrict__ Ahi,
-                                                       const float* __restrict__ Alo,
-                                                       int64_t lda,
-                                                       const float* __restrict__ Bhi,
-                                                       const float* __restrict__ Blo,
-                                                       int64_t ldb, double beta,
-                                                       double* __restrict__ C, int64_t ldc,
-                                                       int64_t kchunk,
-                                                       double* __restrict__ part) {
-  __shared__ float Ah[GBK][GBM + 1], Al[GBK][GBM + 1];
-  __shared__ float Bh[GBK][GBN + 1], Bl[GBK][GBN + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
-  float s[4][4], c[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
-
-  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
-  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
-  // the next K chunk is fetched into registers while the current one is multiplied
-  float pah[4], pal[4], pbh[4], pbl[4];
-  auto fetch = [&](int64_t k0) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int lin = threadIdx.x + e * 256;
-      int mm, kk;
-      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
-      const int64_t gm = m0 + mm, gk = k0 + kk;
-      pah[e] = 0.f;
-      pal[e] = 0.f;
-      if (gm < M && gk < kend) {
-        const int64_t o = transA ? gk + gm * lda : gm + gk * lda;
-        pah[e] = Ahi[o];
-        pal[e] = Alo[o];
-      }
-      int nn;
-      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
-      const int64_t gn = n0 + nn, gk2 = k0 + kk;
-      pbh[e] = 0.f;
-      pbl[e] = 0.f;
-      if (gn < N && gk2 < kend) {
-        const int64_t o = transB ? gn + gk2 * ldb : gk2 + gn * ldb;
-        pbh[e] = Bhi[o];
-        pbl[e] = Blo[o];
-      }
-    }
-  };
-  if (kbeg < kend) fetch(kbeg);
-  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int lin = threadIdx.x + e * 256;
-      int mm, kk;
-      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
-      Ah[kk][mm] = pah[e];
-      Al[kk][mm] = pal[e];
-      int nn;
-      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
-      Bh[kk][nn] = pbh[e];
-      Bl[kk][nn] = pbl[e];
-    }
-    __syncthreads();
-    if (k0 + GBK < kend) fetch(k0 + GBK);
-#pragma unroll 4
-    for (int kk = 0; kk < GBK; ++kk) {
-      float ah[4], al[4], bh[4], bl[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) { ah[i] = Ah[kk][ty + 16 * i]; al[i] = Al[kk][ty + 16 * i]; }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) { bh[j] = Bh[kk][tx + 16 * j]; bl[j] = Bl[kk][tx + 16 * j]; }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float p = __fmul_rn(ah[i], bh[j]);
-          float x = __fmaf_rn(ah[i], bh[j], -p);
-          x = __fmaf_rn(ah[i], bl[j], x);
-          x = __fmaf_rn(al[i], bh[j], x);
-          const float t = __fadd_rn(s[i][j], p);
-          const float bv = __fsub_rn(t, s[i][j]);
-          const float err = __fadd_rn(__fsub_rn(s[i][j], __fsub_rn(t, bv)), __fsub_rn(p, bv));
-          s[i][j] = t;
-          c[i][j] = __fadd_rn(c[i][j], __fadd_rn(err, x));
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
-      const double acc = (double)s[i][j] + (double)c[i][j];
-      if (part) {
-        part[(int64_t)blockIdx.z * M * N + gm + gn * M] = acc;
-      } else {
-        double* cp = C + gm + gn * ldc;
-        *cp = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *cp;
-      }
-    }
-  }
-}
-
-// C = alpha * sum_z part[z] + beta * C, summing the splits in a fixed order.
-__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const double* part,
-                                     double alpha, double beta, double* C, int64_t ldc) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M * N) return;
-  double acc = 0.0;
-  for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * M * N + e];
-  const int64_t r = e % M, c = e / M;
-  double* out = C + r + c * ldc;
-  *out = (beta == 0.0) ? alpha * acc : alpha * acc + beta * *out;
-}
-
-}  // namespace
-
-void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
-           double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
-           double beta, double* C, int64_t ldc) {
-  if (M <= 0 || N <= 0) return;
-  if (K <= 0) {
-    if (beta == 0.0) dset2d(st, M, N, 0.0, C, ldc);
-    else if (beta != 1.0) {
-      // scale C by beta through a zero-K gemm is not needed by callers
-      throw Error(ST_EINVAL, "dgemm: K == 0 with beta not in {0, 1}");
-    }
-    return;
-  }
-  dim3 grid((unsigned)cdiv(M, GBM), (unsigned)cdiv(N, GBN));
-  APL_REQUIRE(grid.y <= 65535, "dgemm: N too large");
-  // split K when the output tiles alone cannot fill the GPU (tall inner dimension)
-  const int64_t tiles = (int64_t)grid.x * grid.y;
-  int64_t splits = 1;
-  if (tiles < 2 * 152 && K >= 256) {
-    splits = std::min<int64_t>(cdiv(4 * 152, tiles), K / 128);
-    splits = std::min<int64_t>(splits, 64);
-    splits = std::max<int64_t>(1, std::min<int64_t>(splits, (int64_t)(1 << 24) / (M * N)));
-  }
-  const bool fp64 = dense_work().fp64_gemm;
-  const int tok = prof_begin(st);
-  // compensated FP32: operands split once into compact hi / lo arrays
-  const float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
-  int64_t lda2 = lda, ldb2 = ldb;
-  if (!fp64) {
-    DenseWork& wk = dense_work();
-    const int64_t ar = transA ? K : M, ac = transA ? M : K;
-    const int64_t br = transB ? N : K, bc = transB ? K : N;
-    wk.gah.alloc((size_t)ar * ac, st);
-    wk.gal.alloc((size_t)ar * ac, st);
-    wk.gbh.alloc((size_t)br * bc, st);
-    wk.gbl.alloc((size_t)br * bc, st);
-    split_kernel<<<(unsigned)cdiv(ar * ac, 256), 256, 0, st>>>(ar, ac, A, lda, wk.gah.p, wk.gal.p);
-    APL_LAUNCH_CHECK();
-    split_kernel<<<(unsigned)cdiv(br * bc, 256), 256, 0, st>>>(br, bc, B, ldb, wk.gbh.p, wk.gbl.p);
-    APL_LAUNCH_CHECK();
-    Ah = wk.gah.p; Al = wk.gal.p; Bh = wk.gbh.p; Bl = wk.gbl.p;
-    lda2 = ar;
-    ldb2 = br;
-  }
-  if (splits > 1) {
-    const int64_t kchunk = cdiv(cdiv(K, splits), GBK) * GBK;
-    splits = cdiv(K, kchunk);
-    dense_work().splitk.alloc((size_t)splits * M * N, st);
-    grid.z = (unsigned)splits;
-    if (fp64)
-      dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
-                                         ldc, kchunk, dense_work().splitk.p);
-    else
-      df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, Ah, Al, lda2, Bh, Bl,
-                                            ldb2, 0.0, C, ldc, kchunk, dense_work().splitk.p);
-    APL_LAUNCH_CHECK();
-    splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
-                                                                     dense_work().splitk.p, alpha, beta, C,
-                                                                     ldc);
-  } else if (fp64) {
-    dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
-                                       ldc, K, nullptr);
-  } else {
-    df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, Ah, Al, lda2, Bh, Bl,
-                                          ldb2, beta, C, ldc, K, nullptr);
-  }
-  APL_LAUNCH_CHECK();
-  prof_end(st, tok, PROF_GEMM, 2.0 * (double)M * (double)N * (double)K);
-}
-
-// ------------------------------------------------------------------------------------
 // Triangular solve.  Diagonal blocks (<= 64) are solved by one thread per right-hand
 // vector; the rest is GEMM updates.
 // ------------------------------------------------------------------------------------
