@@ -81,3 +81,12 @@ def test_struct_layouts_match_c(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_build_compiles_every_cuda_source():
+    """Every .cu file under csrc is a translation unit of the library (a kernel file left
+    out of the build would leave its entry points undefined only at load time)."""
+    from paper_2604_05065_gb300 import build as B
+    csrc = os.path.join(ROOT, "paper_2604_05065_gb300", "csrc")
+    on_disk = sorted(f for f in os.listdir(csrc) if f.endswith(".cu"))
+    assert sorted(B.SOURCES) == on_disk
