@@ -315,6 +315,63 @@ def identity_preconditioner(n: int) -> Preconditioner:
 
 
 # --------------------------------------------------------------------------------------
+# SVD-free variant (Section "SVD-free variant", Eq. preconditioner_svdfree, Algorithm
+# SVD-free CURPreconditioner; unregularised problems, mu = 0)
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SvdFreePreconditioner:
+    """Ptilde^{-1} = sighat Q_R M^{-1} Q_R^T + (I - Q_R Q_R^T) with the core
+    M = T_C A(I,J)^{-1} T_R^T never formed or decomposed: M^{-1} = T_R^{-T} A(I,J) T_C^{-1}
+    is applied as two triangular solves around a product with the cross A(I,J).
+    Ptilde is not symmetric, so LSQR on A Ptilde^{-1} needs apply_inv_T as well."""
+    Q_R: np.ndarray           # n x ell, orthonormal columns
+    T_R: np.ndarray           # ell x ell upper triangular, R^T = Q_R T_R
+    T_C: np.ndarray           # ell x ell upper triangular, C^T C = T_C^T T_C
+    A_IJ: np.ndarray          # ell x ell cross A(I, J)
+    sighat: float             # target level: the CUR error estimate
+
+    @property
+    def ell(self) -> int:
+        return self.Q_R.shape[1]
+
+    def minv(self, t):
+        """M^{-1} t = T_R^{-T} (A(I,J) (T_C^{-1} t))."""
+        y = sla.solve_triangular(self.T_C, t, lower=False, check_finite=False)
+        return sla.solve_triangular(self.T_R, self.A_IJ @ y, trans="T", lower=False,
+                                    check_finite=False)
+
+    def minv_T(self, t):
+        """M^{-T} t = T_C^{-T} (A(I,J)^T (T_R^{-1} t))."""
+        y = sla.solve_triangular(self.T_R, t, lower=False, check_finite=False)
+        return sla.solve_triangular(self.T_C, self.A_IJ.T @ y, trans="T", lower=False,
+                                    check_finite=False)
+
+    def apply_inv(self, w):
+        t = self.Q_R.T @ w
+        return w + self.Q_R @ (self.sighat * self.minv(t) - t)
+
+    def apply_inv_T(self, w):
+        t = self.Q_R.T @ w
+        return w + self.Q_R @ (self.sighat * self.minv_T(t) - t)
+
+    def apply(self, w):
+        """Ptilde w = sighat^{-1} Q_R M Q_R^T w + (I - Q_R Q_R^T) w, M = T_C A(I,J)^{-1} T_R^T."""
+        t = self.Q_R.T @ w
+        Mt = self.T_C @ np.linalg.solve(self.A_IJ, self.T_R.T @ t)
+        return w + self.Q_R @ (Mt / self.sighat - t)
+
+
+def build_svdfree_preconditioner(C: np.ndarray, A_IJ: np.ndarray, Q_R: np.ndarray,
+                                 T_R: np.ndarray, sighat: float) -> SvdFreePreconditioner:
+    """Algorithm SVD-free CURPreconditioner: T_C = chol(C^T C); the operator is kept as
+    its factors (Q_R, T_R, T_C, A(I,J)) and the target level sighat (the estimate rho of
+    Eq. 2normestimate)."""
+    return SvdFreePreconditioner(Q_R, T_R, chol_upper(C.T @ C), np.array(A_IJ, copy=True),
+                                 float(sighat))
+
+
+# --------------------------------------------------------------------------------------
 # Preconditioned LSQR phase (Section 2.2; warm start of Section 3.2; stopping rules of
 # Section 5.3.2).  Golub-Kahan bidiagonalisation of Abar = [A; delta I] P^{-1} with an
 # explicit (m+n)-vector u, right-hand side rbar = b_aug - A_delta x0.

@@ -261,6 +261,72 @@ def test_optimal_preconditioner_condition_number():
                                   rel=1e-9)
 
 
+# ---------------------------------------------------------------- SVD-free variant ----
+
+def _svdfree_pair(A, b, steps, sighat):
+    """The SVD-free operator and the SVD-based one (mu = 0, same target level sighat)
+    from the same CUR factors."""
+    Y, I, J, core, E = _cur_state(A, b, steps)
+    Q, T = None, None
+    for k in range(steps):
+        Q, T = O.augment_qr(Q, T, A[I[k * b:(k + 1) * b], :].T)
+    Pt = O.build_svdfree_preconditioner(A[:, J], A[np.ix_(I, J)], Q, T, sighat)
+    P0 = O.build_preconditioner(A[:, J], core, Q, T, 0.0)
+    P = O.Preconditioner(P0.Vhat, P0.sig, P0.Lam, sighat, sighat / P0.Lam - 1.0)
+    return Pt, P, I, J
+
+
+def _dense_op(f, n):
+    return np.column_stack([f(e) for e in np.eye(n)])
+
+
+def test_svdfree_exact_low_rank_flattens_to_the_target_level():
+    """For A = C U R exactly (rank ell), A Q_R = Q_C M, so A Ptilde^{-1} = sighat Q_C Q_R^T:
+    ell singular values equal to sighat and the rest zero (a transposed factor or a missing
+    T_C in M^{-1} breaks this)."""
+    rng = np.random.default_rng(790)
+    m, n, r = 90, 36, 12
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    sighat = 0.37
+    Pt, _, I, J = _svdfree_pair(A, 4, 3, sighat)
+    assert Pt.ell == r
+    sv = np.linalg.svd(A @ _dense_op(Pt.apply_inv, n), compute_uv=False)
+    assert np.allclose(sv[:r], sighat, rtol=1e-9)
+    assert np.all(sv[r:] <= 1e-9 * sighat)
+
+
+def test_svdfree_lemma_same_spectrum_as_svd_based():
+    """Lemma (SVD-free preconditioner): Ptilde^{-1} = P^{-1} W with W orthogonal, so at
+    mu = 0 the preconditioned matrices have the same singular values."""
+    p = wl.small_dense(120, 40, 791, decay=4.0)
+    A = p.dense
+    Pt, P, I, J = _svdfree_pair(A, 5, 3, 2.5e-3)
+    n = A.shape[1]
+    Ptinv = _dense_op(Pt.apply_inv, n)
+    Pinv = _dense_op(P.apply_inv, n)
+    s1 = np.linalg.svd(A @ Ptinv, compute_uv=False)
+    s2 = np.linalg.svd(A @ Pinv, compute_uv=False)
+    assert np.allclose(s1, s2, rtol=1e-9, atol=1e-12 * s2[0])
+    W = np.linalg.solve(Pinv, Ptinv)
+    assert np.allclose(W.T @ W, np.eye(n), atol=1e-8)
+
+
+def test_svdfree_transpose_inverse_and_complement():
+    """apply_inv_T is the adjoint of apply_inv, apply inverts apply_inv, and both act as
+    the identity on the orthogonal complement of range(Q_R)."""
+    p = wl.small_dense(100, 30, 792, decay=3.0)
+    A = p.dense
+    Pt, _, I, J = _svdfree_pair(A, 4, 2, 0.9)
+    n = A.shape[1]
+    rng = np.random.default_rng(793)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    assert float(Pt.apply_inv(x) @ y) == pytest.approx(float(x @ Pt.apply_inv_T(y)), rel=1e-12)
+    assert np.allclose(Pt.apply(Pt.apply_inv(x)), x, atol=1e-10 * np.linalg.norm(x))
+    w = x - Pt.Q_R @ (Pt.Q_R.T @ x)
+    assert np.allclose(Pt.apply_inv(w), w, atol=1e-13 * np.linalg.norm(x))
+    assert np.allclose(Pt.apply_inv_T(w), w, atol=1e-13 * np.linalg.norm(x))
+
+
 # ---------------------------------------------------------------- LSQR ----------------
 
 @pytest.mark.parametrize("k", [1, 2, 5, 12])
