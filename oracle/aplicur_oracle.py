@@ -371,6 +371,21 @@ def build_svdfree_preconditioner(C: np.ndarray, A_IJ: np.ndarray, Q_R: np.ndarra
                                  float(sighat))
 
 
+def svdfree_smallest_sigma(P: SvdFreePreconditioner, iters: int = 50, seed: int = 1) -> float:
+    """sigma_min(M) = 1 / ||M^{-1}||_2 by power iteration on M^{-T} M^{-1} from a seeded
+    Gaussian start, using only the variant's triangular solves and A(I,J) products.
+    (Not in the paper: a target level near sigma_ell without the SVD, see the measured
+    sensitivity of sighat = rho.)  Converges from above."""
+    v = np.random.Generator(np.random.PCG64(seed)).standard_normal(P.ell)
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        y = P.minv_T(P.minv(v))
+        lam = float(np.linalg.norm(y))
+        v = y / lam
+    return 1.0 / math.sqrt(lam)
+
+
 # --------------------------------------------------------------------------------------
 # Preconditioned LSQR phase (Section 2.2; warm start of Section 3.2; stopping rules of
 # Section 5.3.2).  Golub-Kahan bidiagonalisation of Abar = [A; delta I] P^{-1} with an

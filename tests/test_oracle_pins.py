@@ -327,6 +327,24 @@ def test_svdfree_transpose_inverse_and_complement():
     assert np.allclose(Pt.apply_inv_T(w), w, atol=1e-13 * np.linalg.norm(x))
 
 
+def test_svdfree_power_iteration_finds_the_smallest_cur_singular_value():
+    """sigma_min(M) from M^{-1} alone equals the smallest singular value of the CUR
+    approximation (the SVD-based form's sigma_ell), so the SVD-free operator with that
+    target level conditions A like the SVD-based one (the Lemma)."""
+    p = wl.small_dense(300, 40, 905, decay=3.0)
+    A = p.dense
+    Pt, P, I, J = _svdfree_pair(A, 4, 6, 1.0)
+    est = O.svdfree_smallest_sigma(Pt, iters=80)
+    assert est == pytest.approx(float(P.sig[-1]), rel=1e-6)
+    Pt.sighat = est
+    n = A.shape[1]
+    P2 = O.Preconditioner(P.Vhat, P.sig, P.Lam, est, est / P.Lam - 1.0)
+    s1 = np.linalg.svd(A @ _dense_op(Pt.apply_inv, n), compute_uv=False)
+    s2 = np.linalg.svd(A @ _dense_op(P2.apply_inv, n), compute_uv=False)
+    assert np.allclose(s1, s2, rtol=1e-9)
+    assert s1[0] / s1[-1] < 0.1 * np.linalg.cond(A)
+
+
 # ---------------------------------------------------------------- LSQR ----------------
 
 @pytest.mark.parametrize("k", [1, 2, 5, 12])
