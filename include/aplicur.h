@@ -116,7 +116,20 @@ typedef struct {
    * exact hi products, TwoSum accumulation; about 2^-46 relative), several times faster
    * on GB300, whose FP64 rate is 1/64 of its FP32 rate. */
   int32_t fp64_dense;
+  /* APLICUR_VARIANT_SVD (0, default): the SVD-based preconditioner (Algorithm
+   * CURPreconditioner).  APLICUR_VARIANT_SVDFREE (1): the SVD-free preconditioner of the
+   * paper's "SVD-free variant" (Eq. preconditioner_svdfree), defined there for unregularised
+   * problems: requires mu = 0.  Its inverse sighat Q_R M^{-1} Q_R^T + (I - Q_R Q_R^T) uses
+   * M^{-1} = T_R^{-T} A(I,J) T_C^{-1}, formed once per build by two triangular solves.  The
+   * target level sighat is sigma_min(M) = 1 / ||M^{-1}||_2 from 50 power-iteration steps
+   * on M^{-T} M^{-1} (the smallest CUR singular value, which the SVD-based form uses; the
+   * paper's choice, the estimate rho, overstates it by up to the estimate's safety factor
+   * and can leave A P^{-1} worse conditioned than A); the dynamic stopping rule uses it as
+   * the smallest CUR singular value.  Not available for batched solves. */
+  int32_t variant;
 } aplicur_options;
+
+enum { APLICUR_VARIANT_SVD = 0, APLICUR_VARIANT_SVDFREE = 1 };
 
 /* Device time by kernel family, accumulated over the solves since creation or the
  * last aplicur_reset_profile (requires options.profile).  Families:

@@ -39,7 +39,8 @@ class Options(C.Structure):
                 ("sketch_signs", C.c_void_p), ("normest_w", C.c_void_p),
                 ("replay_nphases", C.c_int32), ("replay_phases", C.c_void_p),
                 ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
-                ("profile", C.c_int32), ("max_rank", C.c_int32), ("fp64_dense", C.c_int32)]
+                ("profile", C.c_int32), ("max_rank", C.c_int32), ("fp64_dense", C.c_int32),
+                ("variant", C.c_int32)]
 
 
 class Profile(C.Structure):

@@ -450,7 +450,51 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
 
 // CURPreconditioner Part 2: M = T_C U T_R^T, SVD of M, coefficients.  Vhat = Q_R V_M is
 // kept implicit (applied as two matrix-vector products per use).
+// SVD-free variant (Eq. preconditioner_svdfree, Algorithm SVD-free CURPreconditioner,
+// mu = 0): the core is kept as M^{-1} = T_R^{-T} A(I,J) T_C^{-1}, formed once here by two
+// triangular solves (no SVD); the passes apply P^{-T} and P^{-1} P^{-T} from it.  The
+// target level is sigma_min(M) from power iteration on M^{-T} M^{-1}.
+void build_svdfree_preconditioner(aplicur_ctx* h) {
+  DenseWorkScope dws(&h->dw);
+  cudaStream_t st = h->st;
+  const int L = h->ell, cap = h->cap;
+  h->VM.alloc((size_t)L * L, st);
+  h->sigma.alloc(L, st);
+  h->work.alloc((size_t)3 * L + 16, st);
+  double* Minv = h->VM.p;
+  // A(I, J): rows I of C = A(:, J) (dense), or gathered from the CSR matrix
+  if (h->A.fmt == 0) gather_rows_cm(st, h->Cbuf.p, h->m, L, h->I_d.p, L, Minv, L);
+  else gather_cross(st, h->A, h->I_d.p, L, h->J_d.p, L, h->colpos.p, Minv, L);
+  dtrsm(st, false, 'U', false, false, L, L, h->TC.p, cap, Minv, L);  // A(I,J) T_C^{-1}
+  dtrsm(st, true, 'U', true, false, L, L, h->TR.p, cap, Minv, L);   // T_R^{-T} (...)
+  const double smin = power_sigma_min(st, L, Minv, L, h->work.p, 50);
+  const double sighat = smin > 0.0 ? smin : 1.0;
+  h->sighat = sighat;
+  h->sig_host.assign(L, 0.0);  // this variant computes no singular values
+  APL_CUDA(cudaMemsetAsync(h->sigma.p, 0, L * sizeof(double), st));
+  std::vector<double> c1(L, sighat);
+  h->coef.alloc(L, st);
+  APL_CUDA(cudaMemcpyAsync(h->coef.p, c1.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  PrecondDev P;
+  P.ell = L;
+  P.Q = h->QR.p;
+  P.ldq = h->n;
+  P.VM = Minv;
+  P.coef = h->coef.p;
+  P.coef2 = nullptr;
+  P.svdfree = 1;
+  P.sighat = sighat;
+  P.normP = 1.0;
+  P.sig_ell = sighat;
+  h->P = P;
+  APL_CUDA(cudaStreamSynchronize(st));
+}
+
 void build_preconditioner(aplicur_ctx* h) {
+  if (h->opt.variant == APLICUR_VARIANT_SVDFREE) {
+    build_svdfree_preconditioner(h);
+    return;
+  }
   DenseWorkScope dws(&h->dw);
   cudaStream_t st = h->st;
   const int L = h->ell, cap = h->cap;
@@ -624,6 +668,10 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   APL_REQUIRE(h->opt.graph_iters >= 0 && h->opt.graph_iters <= 4096, "bad graph_iters");
   APL_REQUIRE(h->opt.precision >= APLICUR_PREC_FP64 && h->opt.precision <= APLICUR_PREC_DF32,
               "bad precision");
+  APL_REQUIRE(h->opt.variant == APLICUR_VARIANT_SVD || h->opt.variant == APLICUR_VARIANT_SVDFREE,
+              "bad variant");
+  APL_REQUIRE(h->opt.variant == APLICUR_VARIANT_SVD || mu == 0.0,
+              "the SVD-free preconditioner is defined for mu = 0");
   if (stream) h->st = (cudaStream_t)stream;
   else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
   cudaStream_t st = h->st;
@@ -1345,6 +1393,8 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     auto t0 = std::chrono::steady_clock::now();
     APL_REQUIRE(nrhs >= 1 && nrhs <= BATCH_MAX_RHS, "nrhs must be 1..16");
     APL_REQUIRE(mu > 0.0 && std::isfinite(mu), "batched solves need mu > 0");
+    APL_REQUIRE(!opt || opt->variant == APLICUR_VARIANT_SVD,
+                "batched solves use the SVD-based preconditioner");
     for (int p = 0; p < nprob; ++p) {
       APL_REQUIRE(A[p].dtype == APLICUR_F32, "batched solves take FP32 matrices");
       APL_REQUIRE(b[p] != nullptr, "b[p] NULL");

@@ -33,6 +33,12 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
 int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
                 double* sigma, int* flag_dev);
 
+// sigma_min(M) = 1 / ||M^{-1}||_2 for M^{-1} (L x L, column-major, ld ldm) by `iters` steps
+// of power iteration on M^{-T} M^{-1} from a fixed start vector; work holds 3 L + 1
+// doubles.  Converges from above.
+double power_sigma_min(cudaStream_t st, int64_t L, const double* Minv, int64_t ldm, double* work,
+                       int iters);
+
 // Elementwise helpers.
 void dcopy2d(cudaStream_t st, int64_t rows, int64_t cols, const double* src, int64_t lds,
              double* dst, int64_t ldd, bool transpose);

@@ -482,11 +482,16 @@ __global__ void __launch_bounds__(NT) pre_vt(int ell, const double* __restrict__
 // q3 = V_M ct, q3b = V_M c2t: a block takes 32 rows (lanes, coalesced column reads of the
 // column-major V_M) and its 8 warps split the k range; the partial sums meet in shared
 // memory in warp order.
+// SVD-free variant (sf = 1, 2; VM holds M^{-1}, sighat scales, q1 = Q_R^T w):
+//  sf = 1: ct = sighat M^{-T} q1 (from pre_vt); q3 = ct - q1 and q3b = sighat M^{-1} ct - q1,
+//          so the expansion gives P^{-T} w and P^{-1} P^{-T} w;
+//  sf = 2: ct = q1; q3 = sighat M^{-1} q1 - q1, so the expansion gives P^{-1} w.
 __global__ void __launch_bounds__(NT) pre_v(int ell, const double* __restrict__ VM,
                                             const double* __restrict__ ct,
                                             const double* __restrict__ c2t,
                                             double* __restrict__ q3, double* __restrict__ q3b,
-                                            const LsqrCtl* ctl) {
+                                            const double* __restrict__ q1, double sighat,
+                                            int sf, const LsqrCtl* ctl) {
   __shared__ double r1[NT / 32][32], r2[NT / 32][32];
   if (ctl && ctl->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(NT) pre_v(int ell, const double* __restrict__ 
     for (int k = warp; k < ell; k += NT / 32) {
       const double v = VM[i + (int64_t)k * ell];
       s1 = fma(v, ct[k], s1);
-      if (q3b) s2 = fma(v, c2t[k], s2);
+      if (q3b && c2t) s2 = fma(v, c2t[k], s2);
     }
   }
   r1[warp][lane] = s1;
@@ -505,8 +510,15 @@ __global__ void __launch_bounds__(NT) pre_v(int ell, const double* __restrict__ 
   if (warp != 0 || i >= ell) return;
   double t1 = 0.0, t2 = 0.0;
   for (int w = 0; w < NT / 32; ++w) { t1 += r1[w][lane]; t2 += r2[w][lane]; }
-  q3[i] = t1;
-  if (q3b) q3b[i] = t2;
+  if (sf == 1) {
+    q3[i] = ct[i] - q1[i];
+    q3b[i] = sighat * t1 - q1[i];
+  } else if (sf == 2) {
+    q3[i] = sighat * t1 - q1[i];
+  } else {
+    q3[i] = t1;
+    if (q3b) q3b[i] = t2;
+  }
 }
 
 // out1 = w + Q q3, out2 = w + Q q3b.  A block takes 32 rows per pass (lanes: coalesced
@@ -826,10 +838,23 @@ void LsqrEngine::launch_pre(const PrecondDev& P, const double* w, double* o1, do
   APL_LAUNCH_CHECK();
   pre_qsum<<<(unsigned)cdiv(ell, NT), NT, 0, st_>>>(ell, nch, qpart_.p, q1_.p, c);
   APL_LAUNCH_CHECK();
-  pre_vt<<<wb, NT, 0, st_>>>(ell, P.VM, q1_.p, P.coef, P.coef2, ct_.p, o2 ? c2t_.p : nullptr, c);
-  APL_LAUNCH_CHECK();
-  pre_v<<<(unsigned)cdiv(ell, 32), NT, 0, st_>>>(ell, P.VM, ct_.p, c2t_.p, q3_.p,
-                                                 o2 ? q3b_.p : nullptr, c);
+  if (P.svdfree && o2) {
+    // ct = sighat M^{-T} q1 (coef holds sighat), then q3, q3b for P^{-T} w, P^{-1} P^{-T} w
+    pre_vt<<<wb, NT, 0, st_>>>(ell, P.VM, q1_.p, P.coef, nullptr, ct_.p, nullptr, c);
+    APL_LAUNCH_CHECK();
+    pre_v<<<(unsigned)cdiv(ell, 32), NT, 0, st_>>>(ell, P.VM, ct_.p, nullptr, q3_.p, q3b_.p,
+                                                   q1_.p, P.sighat, 1, c);
+  } else if (P.svdfree) {
+    // P^{-1} w alone: q3 = sighat M^{-1} q1 - q1
+    pre_v<<<(unsigned)cdiv(ell, 32), NT, 0, st_>>>(ell, P.VM, q1_.p, nullptr, q3_.p, nullptr,
+                                                   q1_.p, P.sighat, 2, c);
+  } else {
+    pre_vt<<<wb, NT, 0, st_>>>(ell, P.VM, q1_.p, P.coef, P.coef2, ct_.p,
+                               o2 ? c2t_.p : nullptr, c);
+    APL_LAUNCH_CHECK();
+    pre_v<<<(unsigned)cdiv(ell, 32), NT, 0, st_>>>(ell, P.VM, ct_.p, c2t_.p, q3_.p,
+                                                   o2 ? q3b_.p : nullptr, nullptr, 0.0, 0, c);
+  }
   APL_LAUNCH_CHECK();
   const int blocks = (int)std::min<int64_t>(cdiv(n_, 32), sm_blocks());
   LsqrCtl* cw = in_phase ? ctl_.p : nullptr;

@@ -48,6 +48,10 @@ struct PrecondDev {
   const double* coef2 = nullptr;
   double normP = 1.0;    // ||P||_2
   double sig_ell = 0.0;  // smallest CUR singular value
+  // SVD-free variant: VM holds M^{-1} (ell x ell), coef the constant sighat; the passes
+  // form P^{-T} w and P^{-1} P^{-T} w (P is not symmetric)
+  int svdfree = 0;
+  double sighat = 0.0;
 };
 
 struct PhaseArgs {
