@@ -127,9 +127,18 @@ typedef struct {
    * and can leave A P^{-1} worse conditioned than A); the dynamic stopping rule uses it as
    * the smallest CUR singular value.  Not available for batched solves. */
   int32_t variant;
+  /* APLICUR_SCHEDULE_ADAPTIVE (0, default): fully adaptive (rank growth interleaved with
+   * preconditioner builds and warm-started LSQR phases).  APLICUR_SCHEDULE_SINGLE_SHOT (1):
+   * the paper's rank-adaptive single-shot variant (Section "Levels of adaptivity"): the rank
+   * grows as usual, but the preconditioner is built once, when growth ends, and a single
+   * LSQR phase (with its warm restarts) follows.  With max_rank = sketch_dim the one rank
+   * step selects all indices at once, which is the fixed-rank single-shot variant
+   * (Algorithm "Sketched CUR with cross approximation using LUPP"). */
+  int32_t schedule;
 } aplicur_options;
 
 enum { APLICUR_VARIANT_SVD = 0, APLICUR_VARIANT_SVDFREE = 1 };
+enum { APLICUR_SCHEDULE_ADAPTIVE = 0, APLICUR_SCHEDULE_SINGLE_SHOT = 1 };
 
 /* Device time by kernel family, accumulated over the solves since creation or the
  * last aplicur_reset_profile (requires options.profile).  Families:

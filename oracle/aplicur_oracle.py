@@ -522,6 +522,15 @@ class Options:
     check_gap: int = 10
     max_extra_phases: int = 8
     replay: dict | None = None       # {"phases": [...], "rebuild": [...]}
+    # Section "Levels of adaptivity": rank-adaptive single-shot preconditioning builds the
+    # preconditioner once, when rank growth ends, and runs a single phase (plus its warm
+    # restarts); the default is fully adaptive
+    single_shot: bool = False
+    # > 0 caps the CUR rank: reaching it ends rank growth like reaching min(m, n) (the last
+    # block is truncated to fit); with bsize = max_rank and single_shot the one rank step
+    # is the fixed-rank single-shot variant (Algorithm "Sketched CUR with cross
+    # approximation using LUPP", on the driver's sketch)
+    max_rank: int = 0
 
 
 @dataclasses.dataclass
@@ -594,20 +603,19 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
     def done(ne):
         return Result(x, I, J, ne <= tol, total, ne, steps, phases, Y, P)
 
+    kmax = min(m, n) if opts.max_rank <= 0 else min(m, n, opts.max_rank)
     while True:
         # Part 1: update CUR
-        Ip, Jp, margin = augment_cur(A, I, J, E_row, core, bsize)
-        exhausted = Ip.size < min(bsize, min(m, n) - len(J))
+        kb = min(bsize, kmax - len(J))
+        Ip, Jp, margin = augment_cur(A, I, J, E_row, core, kb)
+        exhausted = Ip.size < kb
         I = np.concatenate([I, Ip])
         J = np.concatenate([J, Jp])
         core = Core(A, I, J)
         E_row = sketched_residual(A, Y, I, J, core)
         rho = norm_estimate(E_row, W)
-        if exhausted or len(I) >= min(m, n):
-            rho_eff = 0.0 if exhausted else rho
-        else:
-            rho_eff = rho
-        last = rho_eff <= eps_cur or len(I) >= min(m, n) or exhausted
+        rho_eff = 0.0 if exhausted else rho
+        last = rho_eff <= eps_cur or len(I) >= kmax or exhausted
         # Part 2: update factorisations of R^T
         if Ip.size:
             Q_R, T_R = augment_qr(Q_R, T_R, rows(A, Ip).T)
@@ -616,7 +624,7 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
             rebuild = bool(rb_list.pop(0)) if rb_list else last
         else:
             gap = rho_eff - eps_cur
-            rebuild = last or (gap > 0.0 and d_cur / gap >= opts.nu_prec)
+            rebuild = last or (not opts.single_shot and gap > 0.0 and d_cur / gap >= opts.nu_prec)
         steps.append(dict(ell=len(I), rho=rho, rebuild=rebuild, margin=margin))
         if rebuild:
             C = cols(A, J)

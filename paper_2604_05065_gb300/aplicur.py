@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("replay_nphases", C.c_int32), ("replay_phases", C.c_void_p),
                 ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
                 ("profile", C.c_int32), ("max_rank", C.c_int32), ("fp64_dense", C.c_int32),
-                ("variant", C.c_int32)]
+                ("variant", C.c_int32), ("schedule", C.c_int32)]
 
 
 class Profile(C.Structure):

@@ -605,8 +605,10 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
     if (h->replay) {
       rebuild = rp_rb < h->rp_rebuild.size() ? h->rp_rebuild[rp_rb++] != 0 : last;
     } else {
+      // single-shot schedule: one build, when rank growth ends
       const double gap = rho_eff - h->eps_cur;
-      rebuild = last || (gap > 0.0 && d_cur / gap >= h->opt.nu_prec);
+      rebuild = last || (h->opt.schedule == APLICUR_SCHEDULE_ADAPTIVE && gap > 0.0 &&
+                         d_cur / gap >= h->opt.nu_prec);
     }
     h->steps.push_back(StepRec{h->ell, rho, rebuild ? 1 : 0, margin});
     if (rebuild && h->ell > 0) {
@@ -672,6 +674,9 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
               "bad variant");
   APL_REQUIRE(h->opt.variant == APLICUR_VARIANT_SVD || mu == 0.0,
               "the SVD-free preconditioner is defined for mu = 0");
+  APL_REQUIRE(h->opt.schedule == APLICUR_SCHEDULE_ADAPTIVE ||
+                  h->opt.schedule == APLICUR_SCHEDULE_SINGLE_SHOT,
+              "bad schedule");
   if (stream) h->st = (cudaStream_t)stream;
   else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
   cudaStream_t st = h->st;
@@ -1395,6 +1400,8 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     APL_REQUIRE(mu > 0.0 && std::isfinite(mu), "batched solves need mu > 0");
     APL_REQUIRE(!opt || opt->variant == APLICUR_VARIANT_SVD,
                 "batched solves use the SVD-based preconditioner");
+    APL_REQUIRE(!opt || opt->schedule == APLICUR_SCHEDULE_ADAPTIVE,
+                "batched solves use the fully adaptive schedule");
     for (int p = 0; p < nprob; ++p) {
       APL_REQUIRE(A[p].dtype == APLICUR_F32, "batched solves take FP32 matrices");
       APL_REQUIRE(b[p] != nullptr, "b[p] NULL");

@@ -345,6 +345,44 @@ def test_svdfree_power_iteration_finds_the_smallest_cur_singular_value():
     assert s1[0] / s1[-1] < 0.1 * np.linalg.cond(A)
 
 
+# ---------------------------------------------------------------- single-shot ---------
+
+def test_fixed_rank_single_shot_selects_like_lupp_on_the_sketch():
+    """Fixed-rank single-shot (bsize = max_rank = ell): the columns are LAPACK's first ell
+    row pivots of (S A)^T and the rows its first ell row pivots of C = A(:, J)
+    (Algorithm "Sketched CUR with cross approximation using LUPP"), on the same sketch."""
+    p = wl.small_dense(160, 40, 794, decay=3.0, mu=1e-6, sketch_dim=12)
+    A = p.dense
+    ell = 12
+    s = O.sketch_rows(ell)
+    rows, signs = orng.sparse_sign(9, s, p.m, O.sketch_xi(s))
+    W = orng.gaussian_w(9, p.n, 10)
+    res = O.aplicur(A, p.b, p.mu, ell, O.Options(seed=9, single_shot=True, max_rank=ell),
+                    tol=1e-10, srows=rows, signs=signs, W=W)
+    Y = O.apply_sketch(A, rows, signs, s)
+    J = _lapack_perm(Y.T)[:ell]
+    I = _lapack_perm(A[:, J])[:ell]
+    assert np.array_equal(res.J, J) and np.array_equal(res.I, I)
+    assert len(res.rank_steps) == 1 and res.rank_steps[0]["rebuild"]
+
+
+def test_rank_adaptive_single_shot_builds_once_and_solves():
+    """Rank-adaptive single-shot: the rank grows as in the adaptive driver, the
+    preconditioner is built once (at the last rank step), every phase runs with it, and the
+    solve reaches the ridge solution."""
+    p = wl.config1(scale=4)
+    A = p.dense
+    ada = O.aplicur(A, p.b, p.mu, p.sketch_dim, O.Options(seed=3), tol=1e-10)
+    res = O.aplicur(A, p.b, p.mu, p.sketch_dim, O.Options(seed=3, single_shot=True), tol=1e-10)
+    flags = [st["rebuild"] for st in res.rank_steps]
+    assert flags[-1] and not any(flags[:-1])
+    assert np.array_equal(res.I, ada.I) and np.array_equal(res.J, ada.J)
+    assert {ph["ell"] for ph in res.phases} == {len(res.I)}
+    assert res.converged
+    xd = O.ridge_direct(A, p.b, p.mu)
+    assert np.linalg.norm(res.x - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
 # ---------------------------------------------------------------- LSQR ----------------
 
 @pytest.mark.parametrize("k", [1, 2, 5, 12])
