@@ -59,3 +59,27 @@ def test_bench_defines_every_leg():
     for name in ("gpu_arm", "spmv_measure", "batched_measure", "roofline", "traffic_for",
                  "oracle_sample", "reference_arm", "make_config", "aggregate"):
         assert callable(getattr(mod, name)), name
+
+
+def test_roofline_names_the_dominant_family_and_its_rate():
+    """The roofline object of the bench line: the family with the largest device time,
+    achieved = work per launch / average launch time, frac = achieved / peak."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    nf = len(mod.NAMES)
+    prof = {"ms": [0.0] * nf, "launches": [0] * nf, "work": [0.0] * nf}
+    # family 0 (an A pass, bytes): 100 launches of 1 GB in 200 ms -> 500 GB/s
+    prof["ms"][0], prof["launches"][0], prof["work"][0] = 200.0, 100, 100 * 1e9
+    # family 3 (GEMM, flops): 10 launches of 1 TFLOP in 1000 ms -> 10 TFLOP/s, dominant
+    prof["ms"][3], prof["launches"][3], prof["work"][3] = 1000.0, 10, 10 * 1e12
+    r = mod.roofline(prof)
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"):
+        assert key in r, key
+    assert r["kernel"] == mod.NAMES[3] and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(10.0)
+    assert r["frac"] == pytest.approx(10.0 / r["peak"], rel=1e-3)
+    assert r["families"][mod.NAMES[0]]["GBps"] == pytest.approx(500.0)
