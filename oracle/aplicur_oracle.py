@@ -533,6 +533,27 @@ class Options:
     max_rank: int = 0
 
 
+class RebuildRule:
+    """Part 3 of Algorithm "APLICUR: detailed implementation" (re-preconditioning
+    criterion of Section "Adaptivity criteria"): rebuild the preconditioner when
+    d_cur / (rho - eps_cur) >= nu_prec or rho <= eps_cur, where d_cur is the gap
+    rho - eps_cur recorded at the previous rebuild (infinite before the first one).
+    The gap is only updated when a rebuild happens."""
+
+    def __init__(self, eps_cur: float, nu_prec: float):
+        self.eps_cur = eps_cur
+        self.nu_prec = nu_prec
+        self.d_cur = math.inf
+
+    def wants_rebuild(self, rho: float) -> bool:
+        if rho <= self.eps_cur:
+            return True
+        return self.d_cur / (rho - self.eps_cur) >= self.nu_prec
+
+    def rebuilt(self, rho: float) -> None:
+        self.d_cur = rho - self.eps_cur
+
+
 @dataclasses.dataclass
 class Result:
     x: np.ndarray
@@ -576,7 +597,7 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
     core = None
     E_row = Y.copy()
     Q_R = T_R = None
-    d_cur = math.inf
+    rule = RebuildRule(eps_cur, opts.nu_prec)
     x = np.zeros(n)
     steps, phases = [], []
     total = 0
@@ -623,8 +644,7 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
         if rb_list is not None:
             rebuild = bool(rb_list.pop(0)) if rb_list else last
         else:
-            gap = rho_eff - eps_cur
-            rebuild = last or (not opts.single_shot and gap > 0.0 and d_cur / gap >= opts.nu_prec)
+            rebuild = last or (not opts.single_shot and rule.wants_rebuild(rho_eff))
         steps.append(dict(ell=len(I), rho=rho, rebuild=rebuild, margin=margin))
         if rebuild:
             C = cols(A, J)
@@ -633,7 +653,7 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
             ne = run_phase(P, nu, last)
             if not replay and ne <= tol:
                 return done(ne)
-            d_cur = rho_eff - eps_cur
+            rule.rebuilt(rho_eff)
         if last:
             break
         if total >= maxit:

@@ -511,3 +511,147 @@ def test_ridge_gradients_match_central_differences():
         E[i, j] = 1.0
         fd = (loss(A + h * E, b, mu) - loss(A - h * E, b, mu)) / (2 * h)
         assert fd == pytest.approx(gA[i, j], rel=1e-5, abs=1e-9)
+
+
+# ---------------------------------------------------------------- pins of three steps --
+# Row selection at ell > 0, the re-preconditioning decision, and the constant of rho.
+# Each pin has a companion test that plants a plausible mistake in the oracle (on the
+# CPU, through monkeypatch) and checks that the pin then fails.
+
+def _independent_row_pivots(A, Y_S, I, J, Jp):
+    """I_+ from first principles (Algorithm augmentCUR, row step): the residual
+    A - A(:,J) pinv(A(I,J)) A(I,:) formed with the SVD-based pseudo-inverse, restricted
+    to the new columns J_+, rows I zeroed, and LAPACK getrf's first |J_+| row pivots."""
+    Res = A - A[:, J] @ np.linalg.pinv(A[np.ix_(I, J)]) @ A[I, :]
+    Ecol = Res[:, Jp].copy()
+    Ecol[I, :] = 0.0
+    return _lapack_perm(Ecol)[:len(Jp)]
+
+
+def _independent_col_pivots(A, S, I, J, b):
+    """J_+ from first principles (column step): S (A - CUR) with a dense S and the
+    pseudo-inverse core, columns J zeroed, LAPACK's first b pivots of its transpose."""
+    Res = A - A[:, J] @ np.linalg.pinv(A[np.ix_(I, J)]) @ A[I, :]
+    Er = S @ Res
+    Er[:, J] = 0.0
+    return _lapack_perm(Er.T)[:b]
+
+
+def _row_selection_case():
+    p = wl.small_dense(150, 45, 4242, decay=3.0)
+    A = p.dense
+    b = 5
+    Y, I, J, core, E = _cur_state(A, b, 3, seed=6)       # ell = 15
+    s = O.sketch_rows(b)
+    rows_, signs = orng.sparse_sign(6, s, A.shape[0], O.sketch_xi(s))
+    S = O.dense_S(rows_, signs, s)
+    return A, S, I, J, core, E, b
+
+
+def _row_selection_matches(A, S, I, J, core, E, b):
+    Ip, Jp, margin = O.augment_cur(A, I, J, E, core, b)
+    Jx = _independent_col_pivots(A, S, I, J, b)
+    Ix = _independent_row_pivots(A, None, I, J, Jp)
+    return np.array_equal(Jp, Jx) and np.array_equal(Ip, Ix), margin
+
+
+def test_row_selection_at_positive_rank_matches_lapack_on_independent_residual():
+    A, S, I, J, core, E, b = _row_selection_case()
+    assert len(I) == 15
+    ok, margin = _row_selection_matches(A, S, I, J, core, E, b)
+    assert margin > 1e-6          # no near-tie: the pivots are well defined
+    assert ok
+
+
+@pytest.mark.parametrize("plant", ["drop_cur_term", "transposed_core_solve"])
+def test_row_selection_pin_catches_planted_mistakes(monkeypatch, plant):
+    A, S, I, J, core, E, b = _row_selection_case()
+    if plant == "drop_cur_term":
+        # E_col = A(:, J+) without the C U A(I, J+) correction
+        monkeypatch.setattr(O.Core, "solve", lambda self, B: np.zeros((self.ell, B.shape[1])))
+    else:
+        # A(I,J)^{-T} B in place of A(I,J)^{-1} B
+        monkeypatch.setattr(O.Core, "solve",
+                            lambda self, B: sla.lu_solve(self.lu, B, trans=1, check_finite=False))
+    ok, _ = _row_selection_matches(A, S, I, J, core, E, b)
+    assert not ok
+
+
+# hand-worked rho sequence: eps_cur = 0.5, nu_prec = 10; every quotient is exact in binary
+#   rho     gap    d_cur before   d_cur / gap      rebuild   d_cur after
+#   1000.5  1000   inf            inf              yes       1000
+#   500.5   500    1000           2                no        1000
+#   100.5   100    1000           10 (>= 10)       yes       100
+#   20.5    20     100            5                no        100
+#   12.5    12     100            8.33             no        100
+#   10.5    10     100            10               yes       10
+#   40.5    40     10             0.25             no        10
+#   0.5     0      10             (rho <= eps)     yes       0
+_RHO_SEQ = [1000.5, 500.5, 100.5, 20.5, 12.5, 10.5, 40.5, 0.5]
+_REBUILD = [True, False, True, False, False, True, False, True]
+
+
+def _run_rule(rule_cls):
+    rule = rule_cls(0.5, 10.0)
+    flags = []
+    for rho in _RHO_SEQ:
+        f = rule.wants_rebuild(rho)
+        flags.append(f)
+        if f:
+            rule.rebuilt(rho)
+    return flags
+
+
+def test_rebuild_decision_on_hand_worked_rho_sequence():
+    assert _run_rule(O.RebuildRule) == _REBUILD
+
+
+@pytest.mark.parametrize("plant", ["strict_compare", "gap_every_step"])
+def test_rebuild_decision_pin_catches_planted_mistakes(monkeypatch, plant):
+    if plant == "strict_compare":
+        def wants(self, rho):
+            return rho <= self.eps_cur or self.d_cur / (rho - self.eps_cur) > self.nu_prec
+        monkeypatch.setattr(O.RebuildRule, "wants_rebuild", wants)
+    else:
+        orig = O.RebuildRule.wants_rebuild
+
+        def wants(self, rho):
+            f = orig(self, rho)
+            self.d_cur = rho - self.eps_cur      # gap recorded at every step
+            return f
+        monkeypatch.setattr(O.RebuildRule, "wants_rebuild", wants)
+    assert _run_rule(O.RebuildRule) != _REBUILD
+
+
+def test_driver_uses_the_rebuild_rule(monkeypatch):
+    """The driver's rebuild flags follow RebuildRule (a planted always-rebuild rule
+    changes them), so the hand-worked pin covers the free-running schedule."""
+    p = wl.config1(scale=4)
+    base = O.aplicur(p.dense, p.b, p.mu, p.sketch_dim, O.Options(seed=2), tol=1e-11)
+    monkeypatch.setattr(O.RebuildRule, "wants_rebuild", lambda self, rho: True)
+    planted = O.aplicur(p.dense, p.b, p.mu, p.sketch_dim, O.Options(seed=2), tol=1e-11)
+    fb = [s["rebuild"] for s in base.rank_steps]
+    fp = [s["rebuild"] for s in planted.rank_steps]
+    assert not all(fb) and all(fp)
+
+
+def test_norm_estimate_closed_form_on_rank_one():
+    """E = u v^T: ||E w_i|| = ||u|| |v^T w_i|, so Eq. 2normestimate gives
+    rho = 10 sqrt(2/pi) ||u|| max_i |v^T w_i| (the paper's constant, typed here)."""
+    g = np.random.default_rng(77)
+    u = g.standard_normal(40)
+    v = g.standard_normal(300)
+    W = orng.gaussian_w(5, 300, 10)
+    closed = 10.0 * math.sqrt(2.0 / math.pi) * np.linalg.norm(u) * np.abs(v @ W).max()
+    assert O.norm_estimate(np.outer(u, v), W) == pytest.approx(closed, rel=1e-13)
+
+
+@pytest.mark.parametrize("factor", [10.0, 10.0 * math.sqrt(2.0), math.sqrt(2.0 / math.pi)])
+def test_norm_estimate_pin_catches_a_wrong_constant(monkeypatch, factor):
+    monkeypatch.setattr(O, "NORMEST_FACTOR", factor)
+    g = np.random.default_rng(77)
+    u = g.standard_normal(40)
+    v = g.standard_normal(300)
+    W = orng.gaussian_w(5, 300, 10)
+    closed = 10.0 * math.sqrt(2.0 / math.pi) * np.linalg.norm(u) * np.abs(v @ W).max()
+    assert O.norm_estimate(np.outer(u, v), W) != pytest.approx(closed, rel=1e-6)
