@@ -49,9 +49,13 @@ enum { APLICUR_F64 = 0, APLICUR_F32 = 1 };
 /* Arithmetic of the products with an FP32-stored A (FP64-stored A always uses FP64):
  *  FP64  products and sums in FP64 (values promoted exactly);
  *  MIXED FP32 products with FP32 sums per thread, FP64 across threads; each LSQR phase
- *        is an inner solve of an FP64 iterative refinement: every phase starts from
- *        a residual formed in FP64 and ends once its estimate of ||Abar^T rbar|| fell
- *        by 1e-4, or when an FP64 check shows the residual no longer falling;
+ *        is an inner solve of an FP64 iterative refinement in correction form: it
+ *        starts from g = A^T (b - A x) - mu x formed with FP64 products, solves
+ *        [A; delta I] dx ~ [0; g / delta] (the normal equations of the paper's warm
+ *        start) and adds dx to x in FP64; it ends once its estimate of ||Abar^T rbar||
+ *        fell by 1e-4, or when an FP64 check shows the residual no longer falling.
+ *        The stopping tests use the paper's residual estimate.  (mu = 0: the phase
+ *        starts from the FP64 residual [b - A x; 0] instead.)
  *  DF32  compensated FP32: operand vectors split into FP32 hi + lo parts, exact
  *        products by FMA residuals and two-term sums, i.e. FP64-level accuracy from
  *        FP32 instructions only.
@@ -279,7 +283,10 @@ int64_t aplicur_launch_count(void);
  *  A   host struct: format APLICUR_DENSE_ROWMAJOR, dtype F64 or F32, values on the
  *      device, m, n >= 1, ld >= n, n <= 524288.
  *  x   device, m doubles; y device, n doubles (overwritten).
- *  stream  cudaStream_t as void*.
+ *  stream  cudaStream_t as void*, a stream of the current device.
+ * A, x and y must live on the current device: the scratch address is that device's
+ * copy of the array, so a call made with another device current would hand the
+ * kernels the wrong device's scratch.
  * The only scratch, 4 MiB of row-chunk partial sums, is a static device array that
  * every GPU loading the library keeps until the process exits.  All calls share it:
  * calls that may overlap on the GPU (different streams, threads) race and must be

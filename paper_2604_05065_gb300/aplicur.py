@@ -370,13 +370,42 @@ class Solver:
         return y
 
 
+def _check_noalloc_args(torch, A, x, y):
+    """Argument checks of dense_atx_noalloc, all taken before any launch: dtypes first,
+    then sizes, then devices (so that a mistake is reported by its real cause)."""
+    if A.dim() != 2 or A.layout != torch.strided:
+        raise ValueError("A must be a dense 2-D tensor")
+    if A.dtype not in (torch.float64, torch.float32):
+        raise TypeError("A must be float64 or float32")
+    if A.shape[0] < 1 or A.shape[1] < 1:
+        raise ValueError("A must have at least one row and one column")
+    if A.stride(1) != 1:
+        raise ValueError("A must be row-major (unit column stride)")
+    m, n = int(A.shape[0]), int(A.shape[1])
+    if x.dim() != 1 or x.numel() != m:
+        raise ValueError(f"x must be a vector of m = {m} values")
+    if y is not None:
+        if y.dtype != torch.float64:
+            raise TypeError("y must be float64")
+        if y.dim() != 1 or y.numel() < n or not y.is_contiguous():
+            raise ValueError(f"y must be a contiguous vector of at least n = {n} values")
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if x.device != A.device:
+        raise ValueError("x must be on A's device")
+    if y is not None and y.device != A.device:
+        raise ValueError("y must be on A's device")
+
+
 def dense_atx_noalloc(A, x, y=None):
     """y = A^T x for a dense CUDA tensor A through the allocation-free entry point (the
-    library allocates nothing; y, if not given, is allocated here by PyTorch)."""
+    library allocates nothing; y, if not given, is allocated here by PyTorch, and x is
+    converted to a contiguous float64 copy when it is not one already).  The call runs on
+    A's device and that device's current stream."""
+    import torch
+    _check_noalloc_args(torch, A, x, y)
     torch = _torch()
     lib = load()
-    if A.stride(1) != 1:
-        raise ValueError("A must be row-major")
     mat = Matrix()
     mat.format = 0
     mat.dtype = 0 if A.dtype == torch.float64 else 1
@@ -384,12 +413,13 @@ def dense_atx_noalloc(A, x, y=None):
     mat.ld = A.stride(0)
     mat.nnz = mat.m * mat.n
     mat.values = A.data_ptr()
-    x = x.to(torch.float64).contiguous()
-    if y is None:
-        y = torch.empty(mat.n, dtype=torch.float64, device=A.device)
-    stream = torch.cuda.current_stream(A.device).cuda_stream
-    st = lib.aplicur_dense_atx_noalloc(C.byref(mat), x.data_ptr(), y.data_ptr(),
-                                       C.c_void_p(stream))
+    with torch.cuda.device(A.device):
+        x = x.to(torch.float64).contiguous()
+        if y is None:
+            y = torch.empty(mat.n, dtype=torch.float64, device=A.device)
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+        st = lib.aplicur_dense_atx_noalloc(C.byref(mat), x.data_ptr(), y.data_ptr(),
+                                           C.c_void_p(stream))
     if st != 0:
         raise AplicurError(st, lib.aplicur_last_error(None).decode())
     return y

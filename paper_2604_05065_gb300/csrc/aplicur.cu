@@ -79,6 +79,11 @@ __global__ void add2d_kernel(int64_t rows, int64_t cols, const double* src, int6
   const int64_t r = e % rows, c = e / rows;
   dst[r + c * ldd] += src[r + c * lds];
 }
+__global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
 __global__ void scale_kernel(int64_t n, const double* s, double a, double* d) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = a * s[i];
@@ -141,6 +146,7 @@ struct aplicur_ctx {
   // solve
   LsqrEngine eng;
   DBuf<double> x, tmp_m, tmp_n, tmp_n2, lam;
+  DBuf<double> dx, rbot, zm;  // correction-form phases (FP32 products): dx, g / delta, 0
   double norm_Atb = 0;
   bool solved = false;
   std::vector<StepRec> steps;
@@ -555,7 +561,34 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
   a.fixed_len = fixed;
   a.maxit = maxit;
   a.check_gap = h->opt.check_gap;
+  // FP32 products (MIXED): the phase is one step of an FP64 iterative refinement in
+  // correction form.  With g = A^T (b - A x) - mu x formed with FP64 products, LSQR on
+  // [A; delta I] P^{-1} with right-hand side [0; g / delta] has the normal equations
+  // (A^T A + mu I) dx = g of the paper's warm start (Section 3.2), but all its vectors
+  // shrink with g, so FP32 products keep their relative accuracy and the refinement is
+  // not held at the FP32 floor u32 ||A|| ||b - A x|| of the warm-start form.
+  const bool corr = h->opt.precision == APLICUR_PREC_MIXED && h->A.dtype == APLICUR_F32 &&
+                    h->mu > 0.0;
+  if (corr) {
+    cudaStream_t st = h->st;
+    h->dx.alloc(h->n, st);
+    h->rbot.alloc(h->n, st);
+    h->zm.alloc(h->m, st);
+    h->dx.zero(st);
+    h->zm.zero(st);
+    h->eng.correction_rhs(h->b, h->x.p, h->delta, h->rbot.p, &a.kconst, &a.beta1p);
+    a.corr = 1;
+    a.rhs_top = h->zm.p;
+    a.rhs_bot = h->rbot.p;
+    a.x = h->dx.p;
+    // the Paige-Saunders tests must not end a phase short of tol
+    if (a.tol > 0.0) a.eps = std::min(a.eps, a.tol / 100.0);
+  }
   PhaseResult r = h->eng.run_phase(h->P, a);
+  if (corr) {
+    axpy_kernel<<<(unsigned)cdiv(h->n, 256), 256, 0, h->st>>>(h->n, 1.0, h->dx.p, h->x.p);
+    APL_LAUNCH_CHECK();
+  }
   const double ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
   h->phases.push_back(PhaseRec{h->P.ell, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
   *it = r.iters;

@@ -46,6 +46,27 @@ __device__ __forceinline__ bool dyn_stop(double phibar_prev, double phibar, doub
   return rate1 / rate > nu;
 }
 
+// Residual estimates of the paper's warm-start form in a correction phase:
+// pp = sqrt(phibar^2 + k).  The drop pp_prev - pp is formed from the squares so that it
+// keeps its accuracy when k dominates.
+__device__ __forceinline__ double paper_drop(double phibar_prev, double phibar, double k) {
+  const double pp_prev = sqrt(phibar_prev * phibar_prev + k), pp = sqrt(phibar * phibar + k);
+  return (phibar_prev - phibar) * (phibar_prev + phibar) / (pp_prev + pp);
+}
+__device__ __forceinline__ double paper_rate(double phibar_prev, double phibar, double k) {
+  const double pp = sqrt(phibar * phibar + k);
+  return pp > 0.0 ? log1p(paper_drop(phibar_prev, phibar, k) / pp) : INFINITY;
+}
+__device__ __forceinline__ bool dyn_stop_paper(double phibar_prev, double phibar, double k,
+                                               double rate1, double nu, double sig_ell) {
+  if (!isfinite(nu)) return false;
+  if (paper_drop(phibar_prev, phibar, k) < sig_ell) return true;
+  if (sqrt(phibar * phibar + k) <= 0.0) return false;
+  const double rate = paper_rate(phibar_prev, phibar, k);
+  if (rate <= 0.0) return true;
+  return rate1 / rate > nu;
+}
+
 __device__ void finalize_beta(LsqrCtl* c, double sumsq, int init) {
   const double beta = sqrt(sumsq);
   c->beta = beta;
@@ -90,8 +111,35 @@ __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
   c->zs = alpha > 0.0 ? 1.0 / alpha : 0.0;
   c->cabs = fabs(cc);
   const int it = ++c->it;
-  if (it == 1) c->rate1 = phibar > 0.0 ? log(phibar_prev / phibar) : INFINITY;
   int reason = R_NONE;
+  if (c->corr) {
+    // correction phase: tests on the paper's residual estimate pp (Section 5.3.2 rules,
+    // Paige-Saunders tests 1 and 2); ||Abar^T rbar|| is the same in both forms
+    const double k = c->kconst;
+    if (it == 1) c->rate1 = paper_rate(phibar_prev, phibar, k);
+    const double pp = sqrt(phibar * phibar + k);
+    const double arn = phibar * alpha * fabs(cc);
+    if (c->fixed_len >= 0) {
+      if (it >= c->fixed_len) reason = R_REPLAY;
+    } else if (beta == 0.0 || alpha == 0.0) {
+      reason = R_EXACT;
+    } else if (arn <= c->eps * sqrt(c->anorm2) * pp) {
+      reason = R_PS2;
+    } else if (pp <= c->eps * c->beta1p) {
+      reason = R_PS1;
+    } else if (c->inner > 0.0 && arn <= c->inner * c->arnorm0) {
+      reason = R_INNER;
+    } else if (dyn_stop_paper(phibar_prev, phibar, k, c->rate1, c->nu, c->sig_ell)) {
+      reason = R_DYNAMIC;
+    } else if (c->tol > 0.0 && it >= c->next_check && c->normP * arn / c->norm_ref <= c->tol) {
+      reason = R_CHECK;
+    } else if ((long long)it >= c->maxit) {
+      reason = R_MAXIT;
+    }
+    if (reason != R_NONE) { c->done = 1; c->reason = reason; }
+    return;
+  }
+  if (it == 1) c->rate1 = phibar > 0.0 ? log(phibar_prev / phibar) : INFINITY;
   if (c->fixed_len >= 0) {
     if (it >= c->fixed_len) reason = R_REPLAY;
   } else if (beta == 0.0 || alpha == 0.0) {
@@ -662,6 +710,11 @@ __global__ void ne_tail_kernel(int64_t n, double* q, const double* rb, const dou
   q[j] += delta * r;
 }
 
+__global__ void scale_to_kernel(int64_t n, const double* v, double a, double* out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = a * v[j];
+}
+
 __global__ void norm2_kernel(int64_t n, const double* v, double* red, double* out,
                              unsigned int* counter) {
   __shared__ double sh[NT / 32];
@@ -961,6 +1014,9 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   h.next_check = 0;
   h.use_p = pre ? 1 : 0;
   h.inner = (mode_ == 1 && a.fixed_len < 0) ? 1e-4 : 0.0;
+  h.corr = a.corr;
+  h.kconst = a.kconst;
+  h.beta1p = a.beta1p;
   APL_CUDA(cudaMemcpyAsync(ctl_.p, &h, sizeof(LsqrCtl), cudaMemcpyHostToDevice, st_));
   launch_iteration(P, true);
   APL_CUDA(cudaMemcpyAsync(&h, ctl_.p, sizeof(LsqrCtl), cudaMemcpyDeviceToHost, st_));
@@ -1175,6 +1231,21 @@ double LsqrEngine::ne_residual(const double* rhs_top, const double* rhs_bot, con
   ne_tail_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, q_.p, rhs_bot, x, delta);
   APL_LAUNCH_CHECK();
   return norm2(q_.p, n_) / norm_ref;
+}
+
+void LsqrEngine::correction_rhs(const double* b, const double* x, double delta, double* rhs_bot,
+                                double* kconst, double* beta1p) {
+  APL_CUDA(cudaMemcpyAsync(r_.p, b, m_ * sizeof(double), cudaMemcpyDeviceToDevice, st_));
+  matvec(0, x, r_.p, -1.0, 1.0, true);
+  matvec(1, r_.p, q_.p, 1.0, 0.0, true);
+  ne_tail_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, q_.p, nullptr, x, delta);
+  APL_LAUNCH_CHECK();
+  scale_to_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, q_.p, 1.0 / delta, rhs_bot);
+  APL_LAUNCH_CHECK();
+  const double nr = norm2(r_.p, m_), nx = norm2(x, n_), ng = norm2(q_.p, n_);
+  const double w2 = nr * nr + delta * delta * nx * nx;
+  *beta1p = std::sqrt(w2);
+  *kconst = std::max(0.0, w2 - (ng / delta) * (ng / delta));
 }
 
 void LsqrEngine::apply_precond(const PrecondDev& P, const double* w, double* out, double* out2) {

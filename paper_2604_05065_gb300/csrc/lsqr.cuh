@@ -32,6 +32,11 @@ struct LsqrCtl {
   double delta, eps, nu, sig_ell, tol, normP, norm_ref;
   double inner;     // > 0: stop when ||Abar^T rbar|| estimate <= inner * its phase-start value
   double arnorm0;   // alpha_1 beta_1 = ||Abar^T rbar_0||
+  // correction form (corr = 1): the phase solves for a correction with right-hand side
+  // [0; g / delta]; the stopping tests use the residual estimate of the paper's warm-start
+  // form, sqrt(phibar^2 + kconst), whose initial value is beta1p
+  double kconst, beta1p;
+  int corr, pad2;
   long long maxit;
   unsigned int counter[8];
 };
@@ -62,6 +67,10 @@ struct PhaseArgs {
   int fixed_len = -1;
   long long maxit = 1000000;
   int check_gap = 10;
+  // correction form (see LsqrCtl): kconst = ||[b - A x; -delta x]||^2 - ||g||^2 / delta^2 and
+  // beta1p = ||[b - A x; -delta x]|| of the outer iterate x
+  int corr = 0;
+  double kconst = 0.0, beta1p = 0.0;
 };
 
 struct PhaseResult {
@@ -84,6 +93,11 @@ class LsqrEngine {
   // y = alpha A x + beta y (trans 0) or y = A^T x (trans 1), FP64 or mixed products.
   void matvec(int trans, const double* x, double* y, double alpha, double beta, bool fp64);
   double norm2(const double* v, int64_t n);
+  // Right-hand side of the correction form at x: rhs_bot = g / delta with
+  // g = A^T (b - A x) - mu x formed with FP64 products, *kconst = ||[b - A x; -delta x]||^2
+  // - ||g||^2 / delta^2 (clamped at 0) and *beta1p = ||[b - A x; -delta x]||.
+  void correction_rhs(const double* b, const double* x, double delta, double* rhs_bot,
+                      double* kconst, double* beta1p);
   // out = P^{-1} w (and P^{-2} w in out2 when not NULL)
   void apply_precond(const PrecondDev& P, const double* w, double* out, double* out2);
   cudaStream_t stream() const { return st_; }

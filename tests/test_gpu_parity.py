@@ -224,8 +224,9 @@ def test_df32_matches_oracle_on_same_rounded_problem(name):
 @pytest.mark.parametrize("name", ["dense32", "sparse32"])
 def test_mixed_fp32_refinement_against_same_rounded_problem(name):
     """Plain FP32 products: error against the FP64 oracle of the same rounded matrix
-    within 1e-5.  Refinement restarts lower the FP64 residual until FP32 products of A^T
-    with the (large) residual stop resolving it, about u32 ||A|| ||r|| / ||A^T b||."""
+    within 1e-5, and the FP64 normal-equation residual at 1e-10.  Each phase solves for a
+    correction with right-hand side [0; g / delta], g the FP64 normal-equation residual,
+    so FP32 products resolve it to their relative accuracy at every refinement step."""
     import paper_2604_05065_gb300 as pkg
     p = PROBS[name]
     rows, signs, W = draws(p)
@@ -236,7 +237,7 @@ def test_mixed_fp32_refinement_against_same_rounded_problem(name):
     err = rel(x, xd)
     print(f"{name}: mixed FP32 error vs FP64 oracle {err:.3e}, phases {s.phases()}")
     assert err <= 1e-5
-    assert s.stats()["ne_res"] <= 1e-6
+    assert s.stats()["ne_res"] <= 1e-10
 
 
 def test_invalid_arguments_are_rejected():
