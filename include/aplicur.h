@@ -139,7 +139,33 @@ typedef struct {
    * step selects all indices at once, which is the fixed-rank single-shot variant
    * (Algorithm "Sketched CUR with cross approximation using LUPP"). */
   int32_t schedule;
+  /* Dense FP32 A with FP32 or compensated products (precision MIXED or DF32): how the
+   * LSQR iterations read A.  The fused pass reads A once per iteration: thread-block
+   * clusters stream row tiles through shared memory and form u' = A z - alpha u and the
+   * column partial sums of A^T u' from the same tile (it needs n and ld multiples of 4
+   * and a 16-byte aligned A; otherwise the two-pass form runs).  The two-pass form reads
+   * A twice (A z, then A^T u).  Both give the same result up to rounding.
+   *  APLICUR_DENSE_PASS_AUTO (0, default): fused with FP32 products (MIXED), where the
+   *    pass is bound by HBM; two-pass with compensated products (DF32), where about
+   *    eleven FP32 instructions per product make either form bound by instruction issue
+   *    and the two-pass form issues them faster;
+   *  APLICUR_DENSE_PASS_TWO (1): always two-pass;
+   *  APLICUR_DENSE_PASS_FUSED (2): fused wherever it applies. */
+  int32_t dense_pass;
+  /* Optional caller-supplied device allocator.  When alloc is set, every device buffer of
+   * the handle (workspace, factors, LSQR vectors) is allocated by
+   * alloc(bytes, stream, alloc_ctx) and released by free_(ptr, bytes, stream, alloc_ctx),
+   * with `stream` the stream the buffer is used on (stream-ordered semantics, as
+   * cudaMallocAsync / cudaFreeAsync); the library then allocates no device memory itself.
+   * alloc returning NULL fails the call with ENOMEM.  Set both or neither (EINVAL).  The
+   * callbacks may be called from worker threads of batched solves and from
+   * aplicur_destroy.  NULL (default): stream-ordered cudaMallocAsync / cudaFreeAsync. */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_ctx);
+  void (*free_)(void* ptr, size_t bytes, void* stream, void* alloc_ctx);
+  void* alloc_ctx;
 } aplicur_options;
+
+enum { APLICUR_DENSE_PASS_AUTO = 0, APLICUR_DENSE_PASS_TWO = 1, APLICUR_DENSE_PASS_FUSED = 2 };
 
 enum { APLICUR_VARIANT_SVD = 0, APLICUR_VARIANT_SVDFREE = 1 };
 enum { APLICUR_SCHEDULE_ADAPTIVE = 0, APLICUR_SCHEDULE_SINGLE_SHOT = 1 };
@@ -177,6 +203,8 @@ typedef struct {
   double time_rank_ms;  /* of which: CUR rank steps (Parts 1 and 2) */
   double time_build_ms; /*           preconditioner builds */
   double time_lsqr_ms;  /*           LSQR phases and residual checks */
+  int32_t fused_pass;   /* 1: LSQR iterations read dense A once (fused A pass) */
+  int32_t cluster_size; /* CTAs per thread-block cluster of the fused pass (0: not used) */
 } aplicur_stats;
 
 /* Fill `opt` with the defaults above. */
@@ -273,6 +301,10 @@ aplicur_status aplicur_reset_profile(aplicur_handle h);
 
 /* Kernels this process has launched through the library (every handle). */
 int64_t aplicur_launch_count(void);
+
+/* Device allocations this process made through the library's own stream-ordered
+ * allocator (cudaMallocAsync), i.e. without a caller allocator (every handle). */
+int64_t aplicur_internal_alloc_count(void);
 
 /* y = A^T x for a dense row-major A (FP64 or FP32 values, FP64 products and sums)
  * without allocating any device or host memory.  The paper has no counterpart; it

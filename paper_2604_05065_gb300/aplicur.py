@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("replay_nphases", C.c_int32), ("replay_phases", C.c_void_p),
                 ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
                 ("profile", C.c_int32), ("max_rank", C.c_int32), ("fp64_dense", C.c_int32),
-                ("variant", C.c_int32), ("schedule", C.c_int32)]
+                ("variant", C.c_int32), ("schedule", C.c_int32), ("dense_pass", C.c_int32),
+                ("alloc", C.c_void_p), ("free_", C.c_void_p), ("alloc_ctx", C.c_void_p)]
 
 
 class Profile(C.Structure):
@@ -60,7 +61,8 @@ class Stats(C.Structure):
                 ("nsteps", C.c_int32), ("converged", C.c_int32), ("ne_res", C.c_double),
                 ("rho", C.c_double), ("time_setup_ms", C.c_double),
                 ("time_solve_ms", C.c_double), ("time_rank_ms", C.c_double),
-                ("time_build_ms", C.c_double), ("time_lsqr_ms", C.c_double)]
+                ("time_build_ms", C.c_double), ("time_lsqr_ms", C.c_double),
+                ("fused_pass", C.c_int32), ("cluster_size", C.c_int32)]
 
 
 class BatchStats(C.Structure):
@@ -94,6 +96,7 @@ SIGNATURES = {
     "aplicur_get_profile": (C.c_int, [_VP, C.POINTER(Profile)]),
     "aplicur_reset_profile": (C.c_int, [_VP]),
     "aplicur_launch_count": (C.c_int64, []),
+    "aplicur_internal_alloc_count": (C.c_int64, []),
     "aplicur_dense_atx_noalloc": (C.c_int, [C.POINTER(Matrix), _VP, _VP, _VP]),
     "aplicur_batch_create": (C.c_int, [C.POINTER(_VP), _I32, C.POINTER(Matrix), _VP, _I32, _D,
                                        _I32, C.POINTER(Options), _VP]),

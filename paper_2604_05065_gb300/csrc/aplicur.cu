@@ -156,6 +156,8 @@ struct aplicur_ctx {
   float setup_ms = 0;
   ProfSink sink;
   DenseWork dw;  // scratch of the dense routines, used on st only
+  Allocator alloc_;       // caller's device allocator (empty: cudaMallocAsync)
+  bool poisoned = false;  // a bounded device wait gave up: buffers undefined
 };
 
 namespace {
@@ -561,14 +563,17 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
   a.fixed_len = fixed;
   a.maxit = maxit;
   a.check_gap = h->opt.check_gap;
-  // FP32 products (MIXED): the phase is one step of an FP64 iterative refinement in
-  // correction form.  With g = A^T (b - A x) - mu x formed with FP64 products, LSQR on
-  // [A; delta I] P^{-1} with right-hand side [0; g / delta] has the normal equations
-  // (A^T A + mu I) dx = g of the paper's warm start (Section 3.2), but all its vectors
-  // shrink with g, so FP32 products keep their relative accuracy and the refinement is
-  // not held at the FP32 floor u32 ||A|| ||b - A x|| of the warm-start form.
+  // FP32 products (MIXED): a final phase (no dynamic stop) is one step of an FP64
+  // iterative refinement in correction form.  With g = A^T (b - A x) - mu x formed with
+  // FP64 products, LSQR on [A; delta I] P^{-1} with right-hand side [0; g / delta] has the
+  // normal equations (A^T A + mu I) dx = g of the paper's warm start (Section 3.2), but
+  // all its vectors shrink with g, so FP32 products keep their relative accuracy and the
+  // refinement is not held at the FP32 floor u32 ||A|| ||b - A x|| of the warm-start form.
+  // Phases with the dynamic stop keep the warm-start form: the stopping rule reads the
+  // paper's residual estimate, which the correction form cannot recover accurately when
+  // ||g|| / delta is far above the residual.
   const bool corr = h->opt.precision == APLICUR_PREC_MIXED && h->A.dtype == APLICUR_F32 &&
-                    h->mu > 0.0;
+                    h->mu > 0.0 && !std::isfinite(nu);
   if (corr) {
     cudaStream_t st = h->st;
     h->dx.alloc(h->n, st);
@@ -576,8 +581,7 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
     h->zm.alloc(h->m, st);
     h->dx.zero(st);
     h->zm.zero(st);
-    h->eng.correction_rhs(h->b, h->x.p, h->delta, h->rbot.p, &a.kconst, &a.beta1p);
-    a.corr = 1;
+    h->eng.correction_rhs(h->b, h->x.p, h->delta, h->rbot.p);
     a.rhs_top = h->zm.p;
     a.rhs_bot = h->rbot.p;
     a.x = h->dx.p;
@@ -777,7 +781,12 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   cudaEventDestroy(e1);
   h->stats.time_setup_ms = h->setup_ms;
   if (!with_lsqr) return;
-  h->eng.setup(st, h->A, h->opt.precision, h->opt.graph_iters);
+  APL_REQUIRE(h->opt.dense_pass >= APLICUR_DENSE_PASS_AUTO &&
+                  h->opt.dense_pass <= APLICUR_DENSE_PASS_FUSED,
+              "bad dense_pass");
+  h->eng.setup(st, h->A, h->opt.precision, h->opt.graph_iters, h->opt.dense_pass);
+  h->stats.fused_pass = h->eng.fused_pass() ? 1 : 0;
+  h->stats.cluster_size = h->eng.fused_pass() ? h->eng.fused_plan().C : 0;
   h->eng.set_profile(h->opt.profile != 0);
   // ||A^T b|| in FP64
   h->eng.matvec(1, b, h->tmp_n.p, 1.0, 0.0, true);
@@ -791,9 +800,16 @@ aplicur_status fail(aplicur_ctx* h, const Error& e) {
 
 template <typename F>
 aplicur_status guarded(aplicur_ctx* h, F&& f) {
+  if (h && h->poisoned) {
+    h->err = "an earlier call of this handle returned ETIMEOUT: a bounded device wait gave up, "
+             "so the handle's device buffers are undefined; destroy the handle";
+    return APLICUR_ETIMEOUT;
+  }
+  AllocScope as(h && h->alloc_.alloc ? &h->alloc_ : nullptr);
   try {
     return (aplicur_status)f();
   } catch (const Error& e) {
+    if (h && e.code == ST_ETIMEOUT) h->poisoned = true;
     return fail(h, e);
   } catch (const std::exception& e) {
     if (h) h->err = e.what();
@@ -842,8 +858,13 @@ aplicur_status aplicur_create(aplicur_handle* out, const aplicur_matrix* A, cons
                               void* stream) {
   if (!out || !A || !b) { g_create_err = "null argument"; return APLICUR_EINVAL; }
   *out = nullptr;
+  if (opt && ((opt->alloc != nullptr) != (opt->free_ != nullptr))) {
+    g_create_err = "options: set both alloc and free_, or neither";
+    return APLICUR_EINVAL;
+  }
   aplicur_ctx* h = new (std::nothrow) aplicur_ctx();
   if (!h) return APLICUR_ENOMEM;
+  if (opt) h->alloc_ = Allocator{opt->alloc, opt->free_, opt->alloc_ctx};
   aplicur_status stt = guarded(h, [&]() -> int {
     ctx_init(h, A, b, mu, sketch_dim, opt, stream, true);
     return ST_OK;
@@ -1106,6 +1127,8 @@ aplicur_status aplicur_get_profile(aplicur_handle h, aplicur_profile* out) {
 
 int64_t aplicur_launch_count(void) { return launch_count(); }
 
+int64_t aplicur_internal_alloc_count(void) { return internal_alloc_count(); }
+
 aplicur_status aplicur_reset_profile(aplicur_handle h) {
   if (!h) return APLICUR_EINVAL;
   for (int k = 0; k < 3; ++k) {
@@ -1170,6 +1193,7 @@ struct aplicur_batch_ctx {
   std::vector<double> ne;
   std::vector<char> conv;
   std::vector<char> broke;       // per problem: a rank step or build broke down
+  Allocator alloc_;              // caller's device allocator (empty: cudaMallocAsync)
   aplicur_batch_stats stats{};
   std::string err;
   int nthreads = 1;
@@ -1187,8 +1211,10 @@ void parallel_for(int n, int nthreads, int device, F&& f) {
   std::atomic<int> next{0};
   std::exception_ptr first;
   std::mutex mtx;
+  const Allocator* alloc = current_allocator();
   auto work = [&]() {
     cudaSetDevice(device);
+    AllocScope as(alloc);
     while (true) {
       const int i = next.fetch_add(1);
       if (i >= n) break;
@@ -1210,6 +1236,7 @@ void parallel_for(int n, int nthreads, int device, F&& f) {
 
 template <typename F>
 aplicur_status bguarded(aplicur_batch_ctx* h, F&& f) {
+  AllocScope as(h->alloc_.alloc ? &h->alloc_ : nullptr);
   try {
     return (aplicur_status)f();
   } catch (const Error& e) {
@@ -1425,8 +1452,13 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
                                     const aplicur_options* opt, void* stream) {
   if (!out || !A || !b || nprob < 1) { g_batch_err = "null argument or nprob < 1"; return APLICUR_EINVAL; }
   *out = nullptr;
+  if (opt && ((opt->alloc != nullptr) != (opt->free_ != nullptr))) {
+    g_batch_err = "options: set both alloc and free_, or neither";
+    return APLICUR_EINVAL;
+  }
   aplicur_batch_ctx* h = new (std::nothrow) aplicur_batch_ctx();
   if (!h) return APLICUR_ENOMEM;
+  if (opt) h->alloc_ = Allocator{opt->alloc, opt->free_, opt->alloc_ctx};
   aplicur_status stt = bguarded(h, [&]() -> int {
     auto t0 = std::chrono::steady_clock::now();
     APL_REQUIRE(nrhs >= 1 && nrhs <= BATCH_MAX_RHS, "nrhs must be 1..16");

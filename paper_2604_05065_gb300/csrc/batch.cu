@@ -346,15 +346,11 @@ __global__ void beta_kernel(int npairs, int NR, const BProb* __restrict__ probs,
   const BProb& P = probs[p];
   double s = 0.0;
   if (init) {
-    // beta_1 = ||[0; g / delta]||; the paper's warm-start residual norm
-    // ||[b - A x; -delta x]|| differs from it by a component orthogonal to the range of
-    // [A; delta I] P^-1, so phibar of the paper's form is sqrt(phibar^2 + kconst)
-    double g2 = 0.0, w2 = 0.0;
+    // beta_1 = ||[0; g / delta]||: the stopping tests of a phase (Paige-Saunders and the
+    // dynamic rule) read the residual estimate of this correction system
+    double g2 = 0.0;
     for (int k = P.g0; k < P.g1; ++k) g2 += gpart[(int64_t)k * NR + r];
-    for (int k = P.q0; k < P.q1; ++k) w2 += part[(int64_t)k * NR + r];
     s = g2 / (P.delta * P.delta);
-    c.beta1p = sqrt(w2);
-    c.kconst = fmax(w2 - s, 0.0);
   } else {
     for (int k = P.b0; k < P.b1; ++k) s += part[(int64_t)k * NR + r];
   }
@@ -378,25 +374,15 @@ __global__ void beta_kernel(int npairs, int NR, const BProb* __restrict__ probs,
   }
 }
 
-// Dynamic stopping test of Section 5.3.2 on the paper's residual estimates
-// pp_prev = sqrt(phibar_prev^2 + k), pp = sqrt(phibar^2 + k): stop when the drop
-// pp_prev - pp is below sigma_ell or the rate log(pp_prev / pp) fell by more than nu
-// against the first one (a non-positive rate counts as an infinite ratio).  The drop is
-// formed from the squares so that it stays accurate when k dominates.
-__device__ __forceinline__ double paper_drop(double phibar_prev, double phibar, double k) {
-  const double pp_prev = sqrt(phibar_prev * phibar_prev + k), pp = sqrt(phibar * phibar + k);
-  return (phibar_prev - phibar) * (phibar_prev + phibar) / (pp_prev + pp);
-}
-__device__ __forceinline__ double paper_rate(double phibar_prev, double phibar, double k) {
-  const double pp = sqrt(phibar * phibar + k);
-  return pp > 0.0 ? log1p(paper_drop(phibar_prev, phibar, k) / pp) : INFINITY;
-}
-__device__ __forceinline__ bool bdyn_stop(double phibar_prev, double phibar, double k,
-                                          double rate1, double nu, double sig_ell) {
+// Dynamic stopping test of Section 5.3.2: stop when cvgdiff = phibar_prev - phibar is
+// below sigma_ell or cvgrate_1 / cvgrate_j > nu (a non-positive rate counts as an infinite
+// ratio).
+__device__ __forceinline__ bool bdyn_stop(double phibar_prev, double phibar, double rate1,
+                                          double nu, double sig_ell) {
   if (!isfinite(nu)) return false;
-  if (paper_drop(phibar_prev, phibar, k) < sig_ell) return true;
-  if (sqrt(phibar * phibar + k) <= 0.0) return false;
-  const double rate = paper_rate(phibar_prev, phibar, k);
+  if (phibar_prev - phibar < sig_ell) return true;
+  if (phibar <= 0.0) return false;
+  const double rate = log(phibar_prev / phibar);
   if (rate <= 0.0) return true;
   return rate1 / rate > nu;
 }
@@ -440,16 +426,15 @@ __global__ void alpha_kernel(int npairs, int NR, const BProb* __restrict__ probs
     c.alpha = alpha;
     c.sv = alpha > 0.0 ? 1.0 / alpha : 0.0;
     const long long it = ++c.it;
-    if (it == 1) c.rate1 = paper_rate(phibar_prev, phibar, c.kconst);
+    if (it == 1) c.rate1 = phibar > 0.0 ? log(phibar_prev / phibar) : INFINITY;
     int reason = BR_NONE;
     const double ca = fabs(cc);
-    const double pp = sqrt(phibar * phibar + c.kconst);  // the paper's ||rbar||
-    const double arn = phibar * alpha * ca;              // ||Abar^T rbar||, either form
+    const double arn = phibar * alpha * ca;  // ||Abar^T rbar||
     if (beta == 0.0 || alpha == 0.0) reason = BR_EXACT;
-    else if (arn <= c.eps * sqrt(c.anorm2) * pp) reason = BR_PS2;
-    else if (pp <= c.eps * c.beta1p) reason = BR_PS1;
+    else if (alpha * ca <= c.eps * sqrt(c.anorm2)) reason = BR_PS2;
+    else if (phibar <= c.eps * c.beta1) reason = BR_PS1;
     else if (c.inner > 0.0 && arn <= c.inner * c.arnorm0) reason = BR_INNER;
-    else if (bdyn_stop(phibar_prev, phibar, c.kconst, c.rate1, c.nu, c.sig_ell)) reason = BR_DYNAMIC;
+    else if (bdyn_stop(phibar_prev, phibar, c.rate1, c.nu, c.sig_ell)) reason = BR_DYNAMIC;
     else if (c.tol > 0.0 && c.normP * phibar * alpha * ca / c.norm_ref <= c.tol) reason = BR_CHECK;
     else if (it >= c.maxit) reason = BR_MAXIT;
     if (reason != BR_NONE) { c.live = 0; c.reason = reason; }

@@ -71,8 +71,6 @@ struct BPair {
   double cprev;       // expansion: V <- g + Q s1 - cprev V (likewise Z)
   double xc, dc;      // x += xc D ; D <- sv Z - dc D
   double nu, sig_ell, eps, inner, tol, normP, norm_ref;
-  double beta1p;      // ||[b - A x; -delta x]|| at the phase start (the paper's beta_1)
-  double kconst;      // beta1p^2 - beta_1^2: the paper's phibar^2 = phibar^2 + kconst
   long long it, maxit;
   int live;           // takes part in the running phase and has not stopped
   int upd;            // 0 none, 1 D = sv Z (phase start), 2 x and D update

@@ -79,28 +79,60 @@ void prof_set_work(int token_rec, double work);  // adjust the last record's wor
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Device buffer owned by the library (stream-ordered allocation).
+// Caller-supplied device allocator (aplicur_options alloc / free_ / alloc_ctx).  Empty:
+// the library's own stream-ordered cudaMallocAsync / cudaFreeAsync.
+struct Allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx) = nullptr;
+  void (*free_)(void* p, size_t bytes, void* stream, void* ctx) = nullptr;
+  void* ctx = nullptr;
+};
+// The allocator installed on the calling thread for the duration of a C ABI call (NULL:
+// the library's own).  Worker threads of batched solves inherit the caller's.
+const Allocator* current_allocator();
+struct AllocScope {
+  const Allocator* prev;
+  explicit AllocScope(const Allocator* a);
+  ~AllocScope();
+};
+void note_internal_alloc();
+long long internal_alloc_count();
+
+// Device buffer owned by the library (stream-ordered allocation, through the caller's
+// allocator when one is installed; freed by the allocator that made it).
 template <typename T>
 struct DBuf {
   T* p = nullptr;
   size_t n = 0;
   cudaStream_t st = nullptr;
+  Allocator al;
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, st);
+    if (p) {
+      if (al.free_) al.free_(p, n * sizeof(T), st, al.ctx);
+      else cudaFreeAsync(p, st);
+    }
     p = nullptr;
     n = 0;
   }
   // (Re)allocate to hold `count` elements; contents are not kept.
   void alloc(size_t count, cudaStream_t s) {
-    st = s;
-    if (count <= n && p) return;
+    if (count <= n && p) { st = s; return; }
     release();
+    st = s;
     if (count == 0) return;
-    APL_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), s));
+    const Allocator* a = current_allocator();
+    if (a && a->alloc) {
+      p = static_cast<T*>(a->alloc(count * sizeof(T), s, a->ctx));
+      if (!p) throw Error(ST_ENOMEM, "the caller's allocator returned NULL");
+      al = *a;
+    } else {
+      APL_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), s));
+      al = Allocator();
+      note_internal_alloc();
+    }
     n = count;
   }
   void zero(cudaStream_t s) {
@@ -111,6 +143,7 @@ struct DBuf {
     std::swap(p, o.p);
     std::swap(n, o.n);
     std::swap(st, o.st);
+    std::swap(al, o.al);
   }
 };
 

@@ -24,6 +24,16 @@ CaptureScope::CaptureScope() { ++g_capture_depth; }
 CaptureScope::~CaptureScope() { --g_capture_depth; }
 
 namespace {
+thread_local const Allocator* g_alloc = nullptr;
+std::atomic<long long> g_internal_allocs{0};
+}  // namespace
+const Allocator* current_allocator() { return g_alloc; }
+AllocScope::AllocScope(const Allocator* a) : prev(g_alloc) { g_alloc = a; }
+AllocScope::~AllocScope() { g_alloc = prev; }
+void note_internal_alloc() { g_internal_allocs.fetch_add(1, std::memory_order_relaxed); }
+long long internal_alloc_count() { return g_internal_allocs.load(); }
+
+namespace {
 thread_local ProfSink* g_sink = nullptr;
 thread_local DenseWork* g_work = nullptr;
 }

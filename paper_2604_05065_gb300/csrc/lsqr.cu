@@ -22,6 +22,7 @@
 
 #include "../../include/aplicur.h"
 #include "lsqr.cuh"
+#include "apass.cuh"
 #include "df32.cuh"
 
 namespace apl {
@@ -44,40 +45,6 @@ __device__ __forceinline__ bool dyn_stop(double phibar_prev, double phibar, doub
   const double rate = log(phibar_prev / phibar);
   if (rate <= 0.0) return true;
   return rate1 / rate > nu;
-}
-
-// Residual estimates of the paper's warm-start form in a correction phase:
-// pp = sqrt(phibar^2 + k).  The drop pp_prev - pp is formed from the squares so that it
-// keeps its accuracy when k dominates.
-__device__ __forceinline__ double paper_drop(double phibar_prev, double phibar, double k) {
-  const double pp_prev = sqrt(phibar_prev * phibar_prev + k), pp = sqrt(phibar * phibar + k);
-  return (phibar_prev - phibar) * (phibar_prev + phibar) / (pp_prev + pp);
-}
-__device__ __forceinline__ double paper_rate(double phibar_prev, double phibar, double k) {
-  const double pp = sqrt(phibar * phibar + k);
-  return pp > 0.0 ? log1p(paper_drop(phibar_prev, phibar, k) / pp) : INFINITY;
-}
-__device__ __forceinline__ bool dyn_stop_paper(double phibar_prev, double phibar, double k,
-                                               double rate1, double nu, double sig_ell) {
-  if (!isfinite(nu)) return false;
-  if (paper_drop(phibar_prev, phibar, k) < sig_ell) return true;
-  if (sqrt(phibar * phibar + k) <= 0.0) return false;
-  const double rate = paper_rate(phibar_prev, phibar, k);
-  if (rate <= 0.0) return true;
-  return rate1 / rate > nu;
-}
-
-__device__ void finalize_beta(LsqrCtl* c, double sumsq, int init) {
-  const double beta = sqrt(sumsq);
-  c->beta = beta;
-  c->us = beta > 0.0 ? 1.0 / beta : 0.0;
-  if (init) {
-    c->beta1 = beta;
-    c->phibar = beta;
-    if (beta == 0.0) { c->done = 1; c->reason = R_EXACT; }
-  } else {
-    c->anorm2 += c->alpha * c->alpha + beta * beta;
-  }
 }
 
 __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
@@ -111,35 +78,8 @@ __device__ void finalize_alpha(LsqrCtl* c, double sumsq, int init) {
   c->zs = alpha > 0.0 ? 1.0 / alpha : 0.0;
   c->cabs = fabs(cc);
   const int it = ++c->it;
-  int reason = R_NONE;
-  if (c->corr) {
-    // correction phase: tests on the paper's residual estimate pp (Section 5.3.2 rules,
-    // Paige-Saunders tests 1 and 2); ||Abar^T rbar|| is the same in both forms
-    const double k = c->kconst;
-    if (it == 1) c->rate1 = paper_rate(phibar_prev, phibar, k);
-    const double pp = sqrt(phibar * phibar + k);
-    const double arn = phibar * alpha * fabs(cc);
-    if (c->fixed_len >= 0) {
-      if (it >= c->fixed_len) reason = R_REPLAY;
-    } else if (beta == 0.0 || alpha == 0.0) {
-      reason = R_EXACT;
-    } else if (arn <= c->eps * sqrt(c->anorm2) * pp) {
-      reason = R_PS2;
-    } else if (pp <= c->eps * c->beta1p) {
-      reason = R_PS1;
-    } else if (c->inner > 0.0 && arn <= c->inner * c->arnorm0) {
-      reason = R_INNER;
-    } else if (dyn_stop_paper(phibar_prev, phibar, k, c->rate1, c->nu, c->sig_ell)) {
-      reason = R_DYNAMIC;
-    } else if (c->tol > 0.0 && it >= c->next_check && c->normP * arn / c->norm_ref <= c->tol) {
-      reason = R_CHECK;
-    } else if ((long long)it >= c->maxit) {
-      reason = R_MAXIT;
-    }
-    if (reason != R_NONE) { c->done = 1; c->reason = reason; }
-    return;
-  }
   if (it == 1) c->rate1 = phibar > 0.0 ? log(phibar_prev / phibar) : INFINITY;
+  int reason = R_NONE;
   if (c->fixed_len >= 0) {
     if (it >= c->fixed_len) reason = R_REPLAY;
   } else if (beta == 0.0 || alpha == 0.0) {
@@ -797,7 +737,8 @@ void launch_k2_mode(cudaStream_t st, const MatView& A, bool vec, int blocks, int
 
 // ======================================================================================
 
-void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_iters) {
+void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_iters,
+                       int dense_pass) {
   st_ = st;
   A_ = A;
   mode_ = A.dtype == 1 ? mode : 0;  // FP64-stored A always uses FP64 products
@@ -838,6 +779,23 @@ void LsqrEngine::setup(cudaStream_t st, const MatView& A, int mode, int graph_it
   }
   red_cap_ = sm_blocks() + 64;
   red_.alloc(red_cap_, st);
+  fused_ = FusedPlan();
+  const bool want = dense_pass == 2 ? mode_ != 0 : (dense_pass == 0 && mode_ == 1);
+  if (A.fmt == 0 && A.dtype == 1 && want) {
+    fused_ = plan_fused_apass(m_, n_, A.ld, A.vals, mode_);
+    if (fused_.ok && fused_.nclusters * fused_.C > red_cap_) fused_.ok = false;
+  }
+  if (fused_.ok) {
+    part_.alloc((size_t)std::max<int64_t>(k2_rchunks_, fused_.nclusters) * n_, st);
+    ferr_.alloc(1, st);
+    ferr_.zero(st);
+  }
+}
+
+void LsqrEngine::launch_fused(const double* z, bool fused_v) {
+  launch_fused_apass(st_, fused_, mode_, A_, z, zh_.p, zl_.p, u_.p, ctl_.p, red_.p, part_.p,
+                     ferr_.p);
+  APL_CUDA(cudaGetLastError());
 }
 
 void LsqrEngine::launch_k1(bool init, const double* z) {
@@ -1014,9 +972,6 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   h.next_check = 0;
   h.use_p = pre ? 1 : 0;
   h.inner = (mode_ == 1 && a.fixed_len < 0) ? 1e-4 : 0.0;
-  h.corr = a.corr;
-  h.kconst = a.kconst;
-  h.beta1p = a.beta1p;
   APL_CUDA(cudaMemcpyAsync(ctl_.p, &h, sizeof(LsqrCtl), cudaMemcpyHostToDevice, st_));
   launch_iteration(P, true);
   APL_CUDA(cudaMemcpyAsync(&h, ctl_.p, sizeof(LsqrCtl), cudaMemcpyDeviceToHost, st_));
@@ -1036,7 +991,13 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     // algorithmic bytes of one launch of each hot-loop kernel
     const double va = A_.dtype == 0 ? 8.0 : 4.0;
     const double sv = mode_ == 1 ? 4.0 : 8.0;  // operand vector bytes per element
-    if (A_.fmt == 0) {
+    if (fused_.ok) {
+      // the fused pass reads A once: A, z split and z (bottom rows), u read and written,
+      // the column partials written; the column sums read them back
+      const double pb = 8.0 * fused_.nclusters * n_;
+      prof.bytes[0] = (double)m_ * n_ * va + sv * n_ + 8.0 * n_ + 16.0 * (m_ + n_) + pb;
+      prof.bytes[1] = pb + 8.0 * n_ + 48.0 * n_;
+    } else if (A_.fmt == 0) {
       prof.bytes[0] = (double)m_ * n_ * va + sv * n_ + 16.0 * (m_ + n_) + (mode_ ? 8.0 * m_ : 0);
       prof.bytes[1] = (double)m_ * n_ * va + sv * m_ + 8.0 * n_ + 48.0 * n_;
     } else {
@@ -1045,13 +1006,25 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     }
     prof.bytes[2] = 2.0 * n_ * ell * 8.0 + 2.0 * ell * ell * 8.0 + 56.0 * n_;
   }
-  kernels_per_iter_ = (A_.fmt == 0 ? 3 : 2) + (ell > 0 ? 5 : 0);
+  kernels_per_iter_ = (A_.fmt == 0 ? (fused_.ok ? 2 : 3) : 2) + (ell > 0 ? 5 : 0);
   if (profile_) ensure_events(4 * std::max(G, 1));
   auto iteration = [&](int i) {
     if (profile_) record(4 * i);
-    launch_k1(false, ell > 0 ? z_.p : v_.p);
-    if (profile_) record(4 * i + 1);
-    launch_k2(false, ell == 0);
+    if (fused_.ok) {
+      launch_fused(ell > 0 ? z_.p : v_.p, ell == 0);
+      if (profile_) record(4 * i + 1);
+      double* zbuf = ell == 0 ? v_.p : z_.p;
+      float* zh = ell == 0 ? zh_.p : nullptr;
+      float* zl = ell == 0 ? zl_.p : nullptr;
+      k2b_dense<<<k2_blocks_, NT, 0, st_>>>(m_, n_, fused_.nclusters, part_.p, u_.p, g_.p, v_.p,
+                                            zbuf, d_.p, x_, zh, zl, ctl_.p, red_.p, 0,
+                                            ell == 0 ? 1 : 0);
+      APL_LAUNCH_CHECK();
+    } else {
+      launch_k1(false, ell > 0 ? z_.p : v_.p);
+      if (profile_) record(4 * i + 1);
+      launch_k2(false, ell == 0);
+    }
     if (profile_) record(4 * i + 2);
     if (ell > 0) launch_pre(P, g_.p, v_.p, z_.p, true, false);
     if (profile_) record(4 * i + 3);
@@ -1130,6 +1103,11 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   if (h.pending == 2) flush_x();
   res.iters = h.it;
   APL_CUDA(cudaStreamSynchronize(st_));
+  if (fused_.ok) {
+    int fe = 0;
+    APL_CUDA(cudaMemcpy(&fe, ferr_.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fe) throw Error(ST_ETIMEOUT, "fused A pass: a bounded wait ran past its bound");
+  }
   return res;
 }
 
@@ -1233,8 +1211,8 @@ double LsqrEngine::ne_residual(const double* rhs_top, const double* rhs_bot, con
   return norm2(q_.p, n_) / norm_ref;
 }
 
-void LsqrEngine::correction_rhs(const double* b, const double* x, double delta, double* rhs_bot,
-                                double* kconst, double* beta1p) {
+void LsqrEngine::correction_rhs(const double* b, const double* x, double delta,
+                                double* rhs_bot) {
   APL_CUDA(cudaMemcpyAsync(r_.p, b, m_ * sizeof(double), cudaMemcpyDeviceToDevice, st_));
   matvec(0, x, r_.p, -1.0, 1.0, true);
   matvec(1, r_.p, q_.p, 1.0, 0.0, true);
@@ -1242,10 +1220,6 @@ void LsqrEngine::correction_rhs(const double* b, const double* x, double delta, 
   APL_LAUNCH_CHECK();
   scale_to_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, q_.p, 1.0 / delta, rhs_bot);
   APL_LAUNCH_CHECK();
-  const double nr = norm2(r_.p, m_), nx = norm2(x, n_), ng = norm2(q_.p, n_);
-  const double w2 = nr * nr + delta * delta * nx * nx;
-  *beta1p = std::sqrt(w2);
-  *kconst = std::max(0.0, w2 - (ng / delta) * (ng / delta));
 }
 
 void LsqrEngine::apply_precond(const PrecondDev& P, const double* w, double* out, double* out2) {

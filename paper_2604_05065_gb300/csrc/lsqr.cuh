@@ -6,6 +6,20 @@
 
 namespace apl {
 
+// Plan of the fused dense A pass (apass.cu).
+struct FusedPlan {
+  bool ok = false;      // the fused pass applies to this matrix
+  int C = 1;            // CTAs per thread-block cluster (column panels of A)
+  int W = 0;            // panel width in columns (multiple of 4)
+  int R = 1;            // rows of A per pipeline stage
+  int S = 2;            // pipeline stages
+  int KQ = 1;           // float4 columns per consumer thread and row
+  int nclusters = 0;    // clusters of the persistent grid
+  int64_t rows_per_cluster = 0;
+  int ucap = 0;         // rows of u held in shared memory (>= rows_per_cluster)
+  size_t smem = 0;      // dynamic shared memory per CTA
+};
+
 enum StopReason { R_NONE = 0, R_EXACT = 1, R_REPLAY = 2, R_PS2 = 3, R_PS1 = 4, R_DYNAMIC = 5,
                   R_TOL = 6, R_MAXIT = 7, R_CHECK = 8, R_DRIFT = 9, R_INNER = 10 };
 
@@ -32,14 +46,24 @@ struct LsqrCtl {
   double delta, eps, nu, sig_ell, tol, normP, norm_ref;
   double inner;     // > 0: stop when ||Abar^T rbar|| estimate <= inner * its phase-start value
   double arnorm0;   // alpha_1 beta_1 = ||Abar^T rbar_0||
-  // correction form (corr = 1): the phase solves for a correction with right-hand side
-  // [0; g / delta]; the stopping tests use the residual estimate of the paper's warm-start
-  // form, sqrt(phibar^2 + kconst), whose initial value is beta1p
-  double kconst, beta1p;
-  int corr, pad2;
   long long maxit;
   unsigned int counter[8];
 };
+
+// beta = ||u'|| from its squared norm: the scale of the stored u' and, after the first
+// step of a phase, the running ||Abar||_F^2 estimate of the Paige-Saunders test 2.
+__device__ __forceinline__ void finalize_beta(LsqrCtl* c, double sumsq, int init) {
+  const double beta = sqrt(sumsq);
+  c->beta = beta;
+  c->us = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (init) {
+    c->beta1 = beta;
+    c->phibar = beta;
+    if (beta == 0.0) { c->done = 1; c->reason = R_EXACT; }
+  } else {
+    c->anorm2 += c->alpha * c->alpha + beta * beta;
+  }
+}
 
 // The preconditioner P^{-1} = I + Vhat diag(coef) Vhat^T (Eq. preconditioner2) with Vhat
 // kept implicit as Q_R V_M: Q (n x ell, column-major, ld ldq) and VM (ell x ell,
@@ -67,10 +91,6 @@ struct PhaseArgs {
   int fixed_len = -1;
   long long maxit = 1000000;
   int check_gap = 10;
-  // correction form (see LsqrCtl): kconst = ||[b - A x; -delta x]||^2 - ||g||^2 / delta^2 and
-  // beta1p = ||[b - A x; -delta x]|| of the outer iterate x
-  int corr = 0;
-  double kconst = 0.0, beta1p = 0.0;
 };
 
 struct PhaseResult {
@@ -83,7 +103,11 @@ struct PhaseResult {
 class LsqrEngine {
  public:
   // mode: 0 FP64 products, 1 FP32 products and sums, 2 compensated FP32 (see lsqr.cu)
-  void setup(cudaStream_t st, const MatView& A, int mode, int graph_iters);
+  // dense_pass: 0 the fused single-read A pass where it applies with FP32 products
+  // (mode 1), 1 always the two-pass form, 2 the fused pass where it applies (modes 1, 2)
+  void setup(cudaStream_t st, const MatView& A, int mode, int graph_iters, int dense_pass = 0);
+  bool fused_pass() const { return fused_.ok; }
+  const FusedPlan& fused_plan() const { return fused_; }
   void set_profile(bool on) { profile_ = on; }
   KernelProfile prof;
   PhaseResult run_phase(const PrecondDev& P, const PhaseArgs& a);
@@ -94,10 +118,8 @@ class LsqrEngine {
   void matvec(int trans, const double* x, double* y, double alpha, double beta, bool fp64);
   double norm2(const double* v, int64_t n);
   // Right-hand side of the correction form at x: rhs_bot = g / delta with
-  // g = A^T (b - A x) - mu x formed with FP64 products, *kconst = ||[b - A x; -delta x]||^2
-  // - ||g||^2 / delta^2 (clamped at 0) and *beta1p = ||[b - A x; -delta x]||.
-  void correction_rhs(const double* b, const double* x, double delta, double* rhs_bot,
-                      double* kconst, double* beta1p);
+  // g = A^T (b - A x) - mu x formed with FP64 products.
+  void correction_rhs(const double* b, const double* x, double delta, double* rhs_bot);
   // out = P^{-1} w (and P^{-2} w in out2 when not NULL)
   void apply_precond(const PrecondDev& P, const double* w, double* out, double* out2);
   cudaStream_t stream() const { return st_; }
@@ -106,6 +128,8 @@ class LsqrEngine {
   void launch_iteration(const PrecondDev& P, bool init);
   void launch_k1(bool init, const double* z);
   void launch_k2(bool init, bool fused_v);
+  // fused dense A pass (one read of A) followed by the column sums; non-init steps only
+  void launch_fused(const double* z, bool fused_v);
   void launch_pre(const PrecondDev& P, const double* w, double* o1, double* o2, bool in_phase,
                   bool init);
   void flush_x();
@@ -121,6 +145,8 @@ class LsqrEngine {
   DBuf<float> zh_, zl_, uh_, ul_;  // FP32 hi/lo splits of z' and u' (modes 1, 2)
   DBuf<double> scal_;
   DBuf<unsigned int> cnt_;
+  FusedPlan fused_;
+  DBuf<int> ferr_;  // set by the fused pass when a bounded wait gave up
   double* x_ = nullptr;
   bool profile_ = false;
   std::vector<cudaEvent_t> ev_;
