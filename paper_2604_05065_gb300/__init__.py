@@ -4,6 +4,6 @@ min ||A x - b||^2 + mu ||x||^2 (Huh, Cartis, Nakatsukasa, arXiv 2604.05065).
 The solver lives in the CUDA library libaplicur.so (C ABI in include/aplicur.h);
 `aplicur` is its Python binding and `workloads` holds seeded synthetic inputs.
 """
-from .aplicur import (AplicurError, BatchSolver, Solver, aplicur_solve_fn, default_options, load,  # noqa
+from .aplicur import (AplicurError, BatchSolver, DeviceAllocator, Solver, aplicur_solve_fn, default_options, load,  # noqa
                       solve, launch_count, PREC_FP64, PREC_MIXED, PREC_DF32,
                       PROFILE_FAMILIES)

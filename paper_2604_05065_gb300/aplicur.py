@@ -138,6 +138,71 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     return lib
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class DeviceAllocator:
+    """The caller-side device allocator of aplicur_options (alloc / free_ / alloc_ctx):
+    by default PyTorch's caching allocator on `device`, allocating on the stream the
+    library names (stream-ordered reuse, as cudaMallocAsync).  It keeps a record of the
+    live blocks and of the bytes handed out (`live`, `allocs`, `bytes`), and must outlive
+    every handle it was given to."""
+
+    def __init__(self, device, alloc=None, free=None):
+        import torch
+        self.index = torch.device(device).index if torch.device(device).index is not None \
+            else torch.cuda.current_device()
+        self.live = {}
+        self.allocs = 0
+        self.bytes = 0
+        alloc = alloc or (lambda nbytes, stream: torch.cuda.caching_allocator_alloc(
+            nbytes, self.index, stream))
+        free = free or torch.cuda.caching_allocator_delete
+
+        def _alloc(nbytes, stream, _ctx):
+            try:
+                ptr = int(alloc(int(nbytes), int(stream or 0)))
+            except Exception:   # the library turns NULL into ENOMEM
+                return None
+            self.live[ptr] = int(nbytes)
+            self.allocs += 1
+            self.bytes += int(nbytes)
+            return ptr
+
+        def _free(ptr, _nbytes, _stream, _ctx):
+            if ptr is None:
+                return
+            self.live.pop(int(ptr), None)
+            free(int(ptr))
+
+        self._alloc = _ALLOC_FN(_alloc)
+        self._free = _FREE_FN(_free)
+
+    def install(self, opts: "Options") -> None:
+        opts.alloc = C.cast(self._alloc, C.c_void_p).value
+        opts.free_ = C.cast(self._free, C.c_void_p).value
+        opts.alloc_ctx = None
+
+
+# live handles (weakly held) are destroyed at exit, before the interpreter tears down the
+# Python objects their allocator's free callbacks call into
+import weakref as _weakref  # noqa: E402
+_LIVE_HANDLES = _weakref.WeakSet()
+
+
+def _destroy_live_handles():
+    for obj in list(_LIVE_HANDLES):
+        try:
+            obj.close()
+        except Exception:
+            pass
+
+
+import atexit as _atexit  # noqa: E402
+_atexit.register(_destroy_live_handles)
+
+
 def default_options() -> Options:
     o = Options()
     load().aplicur_options_default(C.byref(o))
@@ -201,7 +266,7 @@ class Solver:
     float64).  Options are fields of the C options struct."""
 
     def __init__(self, A, b, mu: float, sketch_dim: int, *, sketch_rows=None, sketch_signs=None,
-                 normest_w=None, replay=None, **opts):
+                 normest_w=None, replay=None, allocator="torch", **opts):
         torch = _torch()
         lib = load()
         self._lib = lib
@@ -234,6 +299,13 @@ class Solver:
             o.normest_r = w.shape[1]
         self.mu = float(mu)
         self.sketch_dim = int(sketch_dim)
+        # device workspace: PyTorch's caching allocator (default), a DeviceAllocator, or
+        # None for the library's own stream-ordered allocations
+        if allocator == "torch":
+            allocator = DeviceAllocator(self.device)
+        self.allocator = allocator
+        if allocator is not None:
+            allocator.install(o)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         h = C.c_void_p()
         st = lib.aplicur_create(C.byref(h), C.byref(mat), b.data_ptr(), self.mu, self.sketch_dim,
@@ -241,6 +313,7 @@ class Solver:
         if st != 0:
             raise AplicurError(st, lib.aplicur_last_error(None).decode())
         self._h = h
+        _LIVE_HANDLES.add(self)
         if replay is not None:
             self.set_replay(replay)
 
@@ -248,6 +321,7 @@ class Solver:
         if getattr(self, "_h", None) is not None:
             self._lib.aplicur_destroy(self._h)
             self._h = None
+        _LIVE_HANDLES.discard(self)
 
     def close(self):
         self.__del__()
@@ -493,7 +567,7 @@ class BatchSolver:
     rhs: list of CUDA tensors of shape (m_p, R) or (m_p,) (converted to float64).
     Problem p is seeded with options.seed + p."""
 
-    def __init__(self, mats, rhs, mu: float, sketch_dim: int, **opts):
+    def __init__(self, mats, rhs, mu: float, sketch_dim: int, allocator="torch", **opts):
         torch = _torch()
         lib = load()
         self._lib = lib
@@ -525,6 +599,11 @@ class BatchSolver:
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
+        if allocator == "torch":
+            allocator = DeviceAllocator(self.device)
+        self.allocator = allocator
+        if allocator is not None:
+            allocator.install(o)
         h = C.c_void_p()
         stream = torch.cuda.current_stream(self.device).cuda_stream
         st = lib.aplicur_batch_create(C.byref(h), len(mats), arr, bptr, R, float(mu),
@@ -532,11 +611,13 @@ class BatchSolver:
         if st != 0:
             raise AplicurError(st, lib.aplicur_batch_last_error(None).decode())
         self._h = h
+        _LIVE_HANDLES.add(self)
 
     def __del__(self):
         if getattr(self, "_h", None) is not None:
             self._lib.aplicur_batch_destroy(self._h)
             self._h = None
+        _LIVE_HANDLES.discard(self)
 
     def close(self):
         self.__del__()
