@@ -719,3 +719,86 @@ def ridge_gradients(A, b, mu: float, x: np.ndarray, g: np.ndarray):
     Al = Ad @ lam
     r = np.asarray(b, dtype=np.float64) - Ad @ x
     return lam, Al, -float(lam @ x), np.outer(r, lam) - np.outer(Al, x)
+
+
+class RidgeQR:
+    """Householder QR of [A; sqrt(mu) I] in FP64, kept for several right-hand sides:
+    solve(top, bot) = argmin ||[A; sqrt(mu) I] x - [top; bot]|| by the same definition as
+    ridge_direct, without refactoring for each right-hand side (finite differences in b
+    and the adjoint solve of ridge_gradients reuse one factorisation)."""
+
+    def __init__(self, A, mu: float):
+        Ad = A.toarray() if _is_sparse(A) else np.asarray(A, dtype=np.float64)
+        self.m, self.n = Ad.shape
+        self.delta = math.sqrt(mu)
+        Aug = np.vstack([Ad, self.delta * np.eye(self.n)])
+        self.Q, self.R = np.linalg.qr(Aug, mode="reduced")
+
+    def solve(self, top, bot=None):
+        rhs = self.Q[:self.m].T @ np.asarray(top, dtype=np.float64)
+        if bot is not None:
+            rhs = rhs + self.Q[self.m:].T @ np.asarray(bot, dtype=np.float64)
+        return sla.solve_triangular(self.R, rhs, lower=False)
+
+
+def grad_A_entries(A, b, x, lam, rows, cols):
+    """Entries (rows[k], cols[k]) of dL/dA = r lambda^T - (A lambda) x^T, r = b - A x,
+    without forming the m x n matrix."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    r = np.asarray(b, dtype=np.float64) - matvec(A, x)
+    Al = matvec(A, lam)
+    return r[rows] * lam[cols] - Al[rows] * x[cols]
+
+
+class RidgeReduced:
+    """The ridge problem of a tall dense A reduced by one Householder QR A = Q_A R_A:
+    ||A x - b||^2 + mu ||x||^2 = ||R_A x - Q_A^T b||^2 + mu ||x||^2 + ||(I - Q_A Q_A^T) b||^2,
+    so x_mu = argmin ||[R_A; sqrt(mu) I] x - [Q_A^T b; 0]|| is a 2n x n least-squares
+    problem per mu (Householder QR), for any number of mu values and right-hand sides.
+    A rank-1 change A + h u v^T stays exactly reduced with one more orthonormal column:
+    u = Q_A w + u_perp gives A + h u v^T = [Q_A, q] [R_A + h w v^T; h ||u_perp|| v^T] with
+    q = u_perp / ||u_perp||, and b enters through [Q_A^T b; q^T b] (finite differences in A
+    without refactoring A)."""
+
+    def __init__(self, A):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.Q, self.R = np.linalg.qr(self.A, mode="reduced")
+        self.n = self.A.shape[1]
+        self._fact = {}  # mu -> QR of [R_A; sqrt(mu) I] (the unchanged A)
+
+    def _factor(self, M, mu, key):
+        if key is not None and key in self._fact:
+            return self._fact[key]
+        f = np.linalg.qr(np.vstack([M, math.sqrt(mu) * np.eye(self.n)]), mode="reduced")
+        if key is not None:
+            self._fact = {key: f}
+        return f
+
+    def _reduced(self, b, du=None, dv=None, h=0.0):
+        cb = self.Q.T @ np.asarray(b, dtype=np.float64)
+        if du is None or h == 0.0:
+            return self.R, cb
+        w = self.Q.T @ du
+        up = du - self.Q @ w
+        nu = float(np.linalg.norm(up))
+        M = self.R + h * np.outer(w, dv)
+        if nu == 0.0:
+            return M, cb
+        M = np.vstack([M, h * nu * np.asarray(dv, dtype=np.float64)[None, :]])
+        return M, np.concatenate([cb, [float(up @ b) / nu]])
+
+    def solve(self, b, mu, du=None, dv=None, h=0.0):
+        """argmin ||(A + h du dv^T) x - b||^2 + mu ||x||^2."""
+        M, rhs = self._reduced(b, du, dv, h)
+        Qa, Ra = self._factor(M, mu, mu if (du is None or h == 0.0) else None)
+        return sla.solve_triangular(Ra, Qa.T @ np.concatenate([rhs, np.zeros(self.n)]),
+                                    lower=False)
+
+    def adjoint(self, mu, g):
+        """lambda = (A^T A + mu I)^{-1} g as argmin ||[R_A; sqrt(mu) I] l - [0; g / sqrt(mu)]||
+        (the Q_A^T part of the right-hand side [0; g / sqrt(mu)] is zero)."""
+        delta = math.sqrt(mu)
+        Qa, Ra = self._factor(self.R, mu, mu)
+        rhs = np.concatenate([np.zeros(self.n), np.asarray(g, dtype=np.float64) / delta])
+        return sla.solve_triangular(Ra, Qa.T @ rhs, lower=False)

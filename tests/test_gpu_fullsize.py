@@ -78,3 +78,51 @@ def test_full_size_products_and_early_iterates(name):
     xg = sol.plain_lsqr(0.0, k).cpu().numpy()
     assert rel(xg, ref.x) <= 1e-9
     sol.close()
+
+
+def test_rbf_full_size_replay_matches_oracle_run():
+    """The 20000 x 20000 RBF workload at full size, replaying the oracle's schedule
+    (tests/golden/schedule_rbf_fp32_20000x20000.json, written by make_schedules.py from the
+    oracle only, converged to 1e-12): every CUR index of all six rank steps bit-exact, rho
+    per step, and the solution at 256 seeded sample entries against the oracle's
+    (FP32-storage gate 1e-5; the measured error is printed).  The free-running schedule is reported as the same or
+    different from the oracle's (rounding can move a dynamic stop)."""
+    import json
+    import os
+
+    import paper_2604_05065_gb300 as pkg
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "schedule_rbf_fp32_20000x20000.json")))
+    p = _problem("rbf_20000x20000")
+    Ad, bd = to_device(p)
+    sched = {"phases": [ph["iters"] for ph in gold["phases"]],
+             "rebuild": [st["rebuild"] for st in gold["rank_steps"]]}
+    idx = np.array(gold["x_sample_index"])
+    # compensated products replay the oracle's schedule; FP32 products (refinement in
+    # correction form) need more final iterations than the FP64 oracle to reach the same
+    # tol, so that form runs freely (its rank steps and builds depend on rho only, which
+    # the LSQR phases do not change)
+    for prec, rp in ((pkg.PREC_DF32, sched), (pkg.PREC_MIXED, None)):
+        sol = pkg.Solver(Ad, bd, p.mu, p.sketch_dim, seed=gold["seed"], precision=prec,
+                         replay=rp)
+        x = sol.solve(gold["tol"]).cpu().numpy()
+        I, J = sol.indices()
+        assert np.array_equal(I, np.array(gold["I"])) and np.array_equal(J, np.array(gold["J"]))
+        for st, gs in zip(sol.steps(), gold["rank_steps"]):
+            assert st["ell"] == gs["ell"]
+            assert st["rho"] == pytest.approx(gs["rho"], rel=1e-6)
+        err = rel(x[idx], np.array(gold["x_sample"]))
+        print(f"precision {prec}: solution vs oracle at 256 entries {err:.3e}, "
+              f"ne_res {sol.stats()['ne_res']:.2e}, phases {[q['iters'] for q in sol.phases()]}")
+        assert err <= 1e-5
+        sol.close()
+    # free run at the bench's tolerance; the phases before the final one are the
+    # oracle's at any tolerance (the final phase differs by the extra refinement)
+    free = pkg.Solver(Ad, bd, p.mu, p.sketch_dim, seed=gold["seed"], precision=pkg.PREC_DF32)
+    free.solve(1e-8)
+    ours = [ph["iters"] for ph in free.phases()]
+    same = ours[:-1] == sched["phases"][:-1]
+    print(f"free-running schedule (1e-8) {'same as' if same else 'different from'} the "
+          f"oracle's: {ours} vs {sched['phases']}")
+    assert free.stats()["converged"]
+    free.close()

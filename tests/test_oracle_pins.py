@@ -655,3 +655,43 @@ def test_norm_estimate_pin_catches_a_wrong_constant(monkeypatch, factor):
     W = orng.gaussian_w(5, 300, 10)
     closed = 10.0 * math.sqrt(2.0 / math.pi) * np.linalg.norm(u) * np.abs(v @ W).max()
     assert O.norm_estimate(np.outer(u, v), W) != pytest.approx(closed, rel=1e-6)
+
+
+# ---------------------------------------------------------------- reused QR -----------
+
+def test_ridge_qr_reuse_matches_direct_solves_and_gradients():
+    """RidgeQR gives ridge_direct's solution and ridge_gradients' lambda from one
+    factorisation, and grad_A_entries the entries of the full gradient."""
+    p = wl.small_dense(150, 25, 4343, decay=2.0, mu=1e-3)
+    A, b, mu = p.dense, p.b, p.mu
+    qr = O.RidgeQR(A, mu)
+    x = qr.solve(b)
+    assert np.allclose(x, O.ridge_direct(A, b, mu), rtol=1e-12, atol=0)
+    g = np.random.default_rng(3).standard_normal(25)
+    lam_o, gb_o, gmu_o, gA_o = O.ridge_gradients(A, b, mu, x, g)
+    lam = qr.solve(np.zeros(150), g / math.sqrt(mu))
+    assert np.allclose(lam, lam_o, rtol=1e-12, atol=0)
+    rows = np.array([0, 7, 149, 33])
+    cols = np.array([0, 24, 5, 5])
+    assert np.allclose(O.grad_A_entries(A, b, x, lam, rows, cols), gA_o[rows, cols], rtol=1e-12)
+
+
+def test_ridge_reduced_matches_direct_solves_and_rank_one_changes():
+    """The QR-reduced ridge problem gives ridge_direct's solution for several mu, the
+    solution of A + h u v^T (u with components inside and outside range(A)), and
+    ridge_gradients' lambda."""
+    p = wl.small_dense(200, 30, 4545, decay=3.0, mu=1e-4)
+    A, b = p.dense, p.b
+    red = O.RidgeReduced(A)
+    g = np.random.default_rng(5)
+    u = g.standard_normal(200)
+    v = g.standard_normal(30)
+    for mu in (1e-8, 1e-4, 1e-1):
+        x = red.solve(b, mu)
+        assert np.allclose(x, O.ridge_direct(A, b, mu), rtol=1e-10, atol=0)
+        xp = red.solve(b, mu, u, v, 1e-3)
+        assert np.allclose(xp, O.ridge_direct(A + 1e-3 * np.outer(u, v), b, mu), rtol=1e-9,
+                           atol=0)
+        gg = g.standard_normal(30)
+        lam_o = O.ridge_gradients(A, b, mu, x, gg)[0]
+        assert np.allclose(red.adjoint(mu, gg), lam_o, rtol=1e-9, atol=0)
