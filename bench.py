@@ -30,7 +30,7 @@ METRIC = "time-to-1e-8 rel. residual; SpMV HBM GB/s %peak; batched solves/s vs p
 TOL = 1e-8
 WORKLOADS = {
     # name: (generator, precision)
-    "rbf_fp32_20000x20000": ("config3", "df32"),
+    "rbf_fp32_20000x20000": ("config3", "mixed"),
     "dense_fp64_2000x200": ("config1", "fp64"),
     "sparse_csr_200000x20000": ("config2", "fp64"),
 }
@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--maxit", type=int, default=200000)
     ap.add_argument("--no-spmv", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other configurations' time-to-tol legs")
     ap.add_argument("--batched-nprob", type=int, default=64,
                     help="problems of the batched workload (512 is the full configuration; a "
                          "full solve takes minutes, so the default line carries 64)")
@@ -255,12 +257,98 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel family of the step (largest device time)
     roof = roofline(prof_tot)
+    hot = hot_loop_roofline(prof_tot)
+    legs = None if (args.no_legs or world > 1) else legs_measure(args, dev)
     spmv = None if args.no_spmv else spmv_measure(args, dev)
     batched = None if (args.no_batched or world > 1) else batched_measure(args, dev)
     return dict(value=value, ms=ms_max / args.steps, p=p, prec=prec, clocks=clk, e2e=e2e,
-                batched=batched,
+                batched=batched, hot=hot, legs=legs,
                 plain=plain, roof=roof, launches=launches, sched=sched, ne=st["ne_res"],
                 spmv=spmv)
+
+
+def _timed(stream, fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0, out
+
+
+def legs_measure(args, dev):
+    """Time-to-1e-8 of the other configurations, APLICUR beside plain (unpreconditioned)
+    GPU LSQR with the same kernels, one warm-up and one timed solve each:
+      dense FP64 2000 x 200 (mu 1e-4, sketch 20): APLICUR and plain, FP64;
+      sparse CSR 200000 x 20000 (mu 1e-6, sketch 100): plain only, FP64 and FP32 products
+        (APLICUR's CUR rank must reach about 0.7 n there before rho <= eps_cur: thousands
+        of columns of dense FP64 factorisations per build, not run here);
+      adjoint FP32 100000 x 2000 (mu 1e-4, sketch 100): forward and backward of
+        0.5 ||x - x_target||^2, APLICUR and plain, compensated FP32 products."""
+    import numpy as np
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+    from paper_2604_05065_gb300 import workloads as wl
+    stream = torch.cuda.current_stream(dev)
+    legs = {}
+
+    def solve_pair(A, b, mu, sd, precision, backward=None):
+        out = {}
+        for kind in ("aplicur", "plain"):
+            for rep in range(2):
+                s = pkg.Solver(A, b, mu, sd, precision=precision, seed=1)
+                fn = (lambda s=s: s.solve(TOL, args.maxit)) if kind == "aplicur" else \
+                    (lambda s=s: s.plain_lsqr(TOL, args.maxit))
+                if backward is None:
+                    secs, _ = _timed(stream, fn)
+                else:
+                    def fb(s=s, fn=fn):
+                        x = fn()
+                        return s.backward(x - backward, TOL, args.maxit, want_A=True)
+                    secs, _ = _timed(stream, fb)
+                st = s.stats()
+                s.close()
+            out[kind] = {"time_to_tol_s": round(secs, 5), "iters": st["iters"],
+                         "ne_res": st["ne_res"], "converged": bool(st["converged"]),
+                         "ell": st["ell"], "nphases": st["nphases"]}
+        out["aplicur_over_plain_time"] = round(out["aplicur"]["time_to_tol_s"]
+                                               / out["plain"]["time_to_tol_s"], 3)
+        return out
+
+    p = wl.config1()
+    A = torch.from_numpy(p.dense).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    legs[p.name] = dict(precision="fp64", **solve_pair(A, b, p.mu, p.sketch_dim, pkg.PREC_FP64))
+    del A, b
+    p = wl.config2()
+    A = torch.sparse_csr_tensor(torch.from_numpy(p.indptr.astype(np.int64)),
+                                torch.from_numpy(p.indices.astype(np.int64)),
+                                torch.from_numpy(p.data), size=(p.m, p.n)).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    leg = {"aplicur": {"not_run": "CUR rank near 0.7 n = 14000 before rho <= eps_cur = 30 "
+                                  "sqrt(mu): minutes of dense FP64 factorisations per build"}}
+    for pname, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+        for rep in range(2):
+            s = pkg.Solver(A, b, p.mu, p.sketch_dim, precision=prec, seed=1)
+            secs, _ = _timed(stream, lambda s=s: s.plain_lsqr(TOL, args.maxit))
+            st = s.stats()
+            s.close()
+        leg[f"plain_{pname}"] = {"time_to_tol_s": round(secs, 4), "iters": st["iters"],
+                                 "ne_res": st["ne_res"], "converged": bool(st["converged"])}
+    legs[p.name] = leg
+    del A, b
+    A, b, xt, mu, sd = wl.config5_device(dev)
+    leg = solve_pair(A, b, mu, sd, pkg.PREC_DF32, backward=xt)
+    leg.update(precision="df32", mode="forward + backward (gradients in b, mu and A)",
+               note="inputs drawn on the GPU by the same recipe (workloads.config5_device)")
+    legs["adjoint_fp32_100000x2000"] = leg
+    del A, b
+    torch.cuda.empty_cache()
+    return legs
 
 
 def spmv_measure(args, dev):
@@ -309,7 +397,8 @@ FP32_PEAK_TFLOPS = 80.5  # GB300 nominal FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP
 # FP32 instructions each (a product needs a rounding-error FMA, two cross terms and a
 # TwoSum), so its ceiling is the FP32 instruction rate / 6.
 DF32_PEAK_TFLOPS = round(152 * 128 * 2.07e9 / 6 / 1e12, 2)
-NAMES = ["A z pass (k1_dense)", "A^T u pass (k2a_dense + k2b_dense)",
+NAMES = ["A pass (fused_apass_kernel; k1_dense in the two-pass form)",
+         "A^T u column sums (k2b_dense; k2a_dense + k2b_dense in the two-pass form)",
          "preconditioner passes (pre_qt, pre_qsum, pre_vt, pre_v, pre_expand)",
          "dense GEMM (df32gemm_kernel, compensated FP32)",
          "Jacobi stage 2 (jacobi_df_block_kernel, compensated FP32)",
@@ -419,6 +508,24 @@ def roofline(prof):
     return out
 
 
+def hot_loop_roofline(prof):
+    """The dense A pass of the LSQR iterations (family 0: the fused single-read pass with
+    FP32 products, or A z of the two-pass form) against the measured HBM copy bandwidth."""
+    if not prof["launches"][0]:
+        return None
+    peak_bw, src = peaks()
+    avg_ms = prof["ms"][0] / prof["launches"][0]
+    per = prof["work"][0] / prof["launches"][0]
+    achieved = per / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "A pass of the LSQR iteration (fused_apass_kernel)",
+            "achieved": round(achieved, 1), "peak": peak_bw, "unit": "GB/s",
+            "frac": round(achieved / peak_bw, 4), "bytes_per_launch": int(per),
+            "avg_launch_ms": round(avg_ms, 5), "launches_timed": prof["launches"][0],
+            "traffic": traffic_for(0, per),
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+            else "fallback 6800 GB/s"}
+
+
 def traffic_for(k, bpl):
     """DRAM bytes per launch from the committed ncu summary table (profiles/ncu_traffic.md),
     scaled to this launch size, or None when no capture of the current kernel source exists."""
@@ -440,45 +547,141 @@ def traffic_for(k, bpl):
 
 # ----------------------------------------------------------------------------- CPU arm --
 
-def oracle_sample(p, sched, iters_sample=6):
-    """Times the oracle on a bounded sample of the full workload and scales it to one
-    solve with the run's schedule (rank steps, preconditioner builds, LSQR iterations)."""
-    import numpy as np
+class OracleReplay:
+    """The oracle's solve of a workload cut into strata in the order the driver of
+    Algorithm "APLICUR: detailed implementation" runs them: the sketch, every rank step
+    (Parts 1 and 2), every preconditioner build and, per LSQR phase, a sample of
+    SAMPLE_ITERS iterations plus the residual check.  The schedule (rebuild flags, phase
+    lengths) is the oracle's own full run (tests/golden, written by make_schedules.py); the
+    strata call the oracle's functions as they stand, on the full workload.  A phase is
+    scaled by its length: the phase start and the residual check each cost about one
+    iteration (one product with A and one with A^T), so a phase of k iterations costs
+    (k + 2) / (SAMPLE_ITERS + 2) of its sample."""
 
-    from oracle import aplicur_oracle as O
-    from oracle import rng as orng
+    SAMPLE_ITERS = 3
 
-    A = p.to_scipy() if p.fmt == "csr" else np.asarray(p.dense, dtype=np.float64)
-    b = np.asarray(p.b, dtype=np.float64)
-    s = O.sketch_rows(p.sketch_dim)
-    xi = O.sketch_xi(s)
+    def __init__(self, p, gold):
+        import numpy as np
+        self.np = np
+        self.p = p
+        self.A = p.to_scipy() if p.fmt == "csr" else np.asarray(p.dense, dtype=np.float64)
+        self.b = np.asarray(p.b, dtype=np.float64)
+        self.mu = p.mu
+        self.delta = math.sqrt(p.mu)
+        self.rebuild = [bool(st["rebuild"]) for st in gold["rank_steps"]]
+        self.phase_iters = list(gold["bench_tol"]["phases"])
+        self.strata = []            # (name, fn, scale)
+        ph = 0
+        self.strata.append(("sketch", self._sketch, 1.0))
+        for k, rb in enumerate(self.rebuild):
+            self.strata.append((f"rank step {k + 1}", self._rank_step, 1.0))
+            if rb:
+                self.strata.append((f"build {ph + 1}", self._build, 1.0))
+                it = self.phase_iters[ph] if ph < len(self.phase_iters) else 0
+                self.strata.append((f"phase {ph + 1} ({it} iterations)", self._phase,
+                                    (it + 2) / (self.SAMPLE_ITERS + 2)))
+                ph += 1
+        self.times = {}
+        self.pos = 0
+
+    # ---- the driver's pieces, on the oracle's functions
+    def _sketch(self):
+        from oracle import aplicur_oracle as O
+        from oracle import rng as orng
+        s = O.sketch_rows(self.p.sketch_dim)
+        rows, signs = orng.sparse_sign(1, s, self.p.m, O.sketch_xi(s))
+        self.W = orng.gaussian_w(1, self.p.n, 10)
+        self.Y = O.apply_sketch(self.A, rows, signs, s)
+        e = self.np.zeros(0, self.np.int64)
+        self.I, self.J, self.core, self.E = e, e, None, self.Y.copy()
+        self.Q = self.T = None
+        self.x = self.np.zeros(self.p.n)
+        self.norm_Atb = float(self.np.linalg.norm(O.rmatvec(self.A, self.b)))
+
+    def _rank_step(self):
+        from oracle import aplicur_oracle as O
+        np = self.np
+        kb = min(self.p.sketch_dim, min(self.p.m, self.p.n) - len(self.J))
+        Ip, Jp, _ = O.augment_cur(self.A, self.I, self.J, self.E, self.core, kb)
+        self.I = np.concatenate([self.I, Ip])
+        self.J = np.concatenate([self.J, Jp])
+        self.core = O.Core(self.A, self.I, self.J)
+        self.E = O.sketched_residual(self.A, self.Y, self.I, self.J, self.core)
+        O.norm_estimate(self.E, self.W)
+        if Ip.size:
+            self.Q, self.T = O.augment_qr(self.Q, self.T, O.rows(self.A, Ip).T)
+
+    def _build(self):
+        from oracle import aplicur_oracle as O
+        self.P = O.build_preconditioner(O.cols(self.A, self.J), self.core, self.Q, self.T,
+                                        self.delta)
+
+    def _phase(self):
+        from oracle import aplicur_oracle as O
+        r = O.plsqr_phase(self.A, self.b, self.delta, self.x, self.P, eps_lsqr=0.0,
+                          fixed_len=self.SAMPLE_ITERS)
+        self.x = r.x
+        O.ne_residual(self.A, self.b, self.mu, self.x, self.norm_Atb)
+
+    def run_next(self):
+        """Run the next stratum (after the last one, a new solve starts with the sketch);
+        returns its wall time in seconds."""
+        name, fn, _ = self.strata[self.pos]
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        self.times.setdefault(name, []).append(dt)
+        self.pos = (self.pos + 1) % len(self.strata)
+        return dt
+
+    def covered(self):
+        return all(name in self.times for name, _, _ in self.strata)
+
+    def solve_seconds(self):
+        """One full solve, from the strata measured (their means)."""
+        return sum(statistics.mean(self.times[name]) * sc for name, _, sc in self.strata)
+
+    def describe(self):
+        parts = ", ".join(f"{name} {statistics.mean(self.times[name]) * sc:.2f} s"
+                          for name, _, sc in self.strata)
+        return (f"oracle solve of the full workload cut into {len(self.strata)} strata in "
+                f"driver order on the oracle's own schedule (rank steps and builds at every "
+                f"rank of the schedule, phases from {self.SAMPLE_ITERS}-iteration samples "
+                f"scaled by their lengths): {parts}")
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part"):
+                model = line.split(":", 1)[1].strip()
+                if low.startswith("model name"):
+                    break
+    except OSError:
+        pass
+    try:
+        import platform
+        model = model or platform.processor()
+        arch = platform.machine()
+    except Exception:
+        arch = ""
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    return {"cpu": model, "arch": arch, "cores": os.cpu_count(),
+            "blas_threads": int(threads) if threads else os.cpu_count()}
+
+
+def oracle_baseline(p, gold):
+    """The oracle timed once through every stratum of a solve (CPU baseline of the GPU
+    arm's line)."""
+    rep = OracleReplay(p, gold)
     t0 = time.perf_counter()
-    rows, signs = orng.sparse_sign(1, s, p.m, xi)
-    W = orng.gaussian_w(1, p.n, 10)
-    Y = O.apply_sketch(A, rows, signs, s)
-    t_sketch = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    I0 = np.zeros(0, np.int64)
-    Ip, Jp, _ = O.augment_cur(A, I0, I0, Y, None, p.sketch_dim)
-    core = O.Core(A, Ip, Jp)
-    E = O.sketched_residual(A, Y, Ip, Jp, core)
-    O.norm_estimate(E, W)
-    Q, T = O.augment_qr(None, None, O.rows(A, Ip).T)
-    t_step = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    P = O.build_preconditioner(O.cols(A, Jp), core, Q, T, math.sqrt(p.mu))
-    t_build = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.plsqr_phase(A, b, math.sqrt(p.mu), np.zeros(p.n), P, eps_lsqr=0.0, maxit=iters_sample)
-    t_iter = (time.perf_counter() - t0) / iters_sample
-    est = (t_sketch + sched.get("steps", 1) * t_step + sched.get("builds", 1) * t_build
-           + sched.get("iters", 1) * t_iter)
-    sample = (f"oracle on the full workload: sketch, 1 rank step, 1 preconditioner build and "
-              f"{iters_sample} LSQR iterations ({t_sketch:.2f}+{t_step:.2f}+{t_build:.2f}+"
-              f"{iters_sample}x{t_iter:.3f} s), scaled to one solve by the schedule "
-              f"{sched.get('steps')} rank steps / {sched.get('builds')} builds / "
-              f"{sched.get('iters')} iterations")
-    return 1.0 / est, sample, t_sketch + t_step + t_build + iters_sample * t_iter
+    while not rep.covered():
+        rep.run_next()
+    wall = time.perf_counter() - t0
+    secs = rep.solve_seconds()
+    return 1.0 / secs, rep.describe(), wall
 
 
 def make_config(p, prec, world):
@@ -502,24 +705,43 @@ def load_schedule(name):
 
 
 def reference_arm(args, rank, world):
+    """The oracle as the reference arm: the K timed steps run the strata of OracleReplay
+    in driver order (spread over the steps when K is smaller than the number of strata,
+    one per step and cycling otherwise); the value is one full solve assembled from the
+    strata.  Warm-up steps do no oracle work (nothing in it warms up)."""
     if rank != 0:
         return
     p, prec = make_workload(args.workload)
-    sched = load_schedule(args.workload) or {"steps": 1, "builds": 1, "iters": 1}
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, sample, _ = oracle_sample(p, sched)
-        if i >= args.warmup:
-            vals.append(v)
-    value = statistics.median(vals)
-    cores = os.cpu_count()
+    gold = load_schedule(args.workload)
+    if gold is None or "bench_tol" not in gold:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no oracle schedule for {args.workload} under tests/golden"}))
+        return
+    rep = OracleReplay(p, gold)
+    nstr = len(rep.strata)
+    if args.steps >= nstr:
+        per_step = [1] * args.steps
+    else:
+        per_step = [nstr // args.steps + (1 if k < nstr % args.steps else 0)
+                    for k in range(args.steps)]
+    step_s = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step[k]):
+            rep.run_next()
+        step_s.append(time.perf_counter() - t0)
+    value = 1.0 / rep.solve_seconds()
+    info = cpu_info()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1000.0 * statistics.mean(step_s), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": make_config(p, prec, world),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+            "time_to_tol_s": 1.0 / value,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": info["blas_threads"],
+                             "kind": "oracle", "cpu": info["cpu"], "arch": info["arch"],
+                             "sample": rep.describe()
+                             + f"; each timed step ran {per_step[0]} stratum(s)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -543,11 +765,14 @@ def main():
     if rank == 0:
         p = r["p"]
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            sched = load_schedule(args.workload) or r["sched"]
-            v, sample, secs = oracle_sample(p, sched)
-            cpu = {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": sample, "sample_seconds": round(secs, 2)}
+        gold = load_schedule(args.workload)
+        if world == 1 and not args.no_cpu_baseline and gold and "bench_tol" in gold:
+            v, sample, secs = oracle_baseline(p, gold)
+            info = cpu_info()
+            cpu = {"value": v, "unit": "solves/s", "cores": info["blas_threads"],
+                   "kind": "oracle", "cpu": info["cpu"], "arch": info["arch"],
+                   "sample": sample, "sample_seconds": round(secs, 2),
+                   "oracle_full_run_seconds_on_build_host": gold["bench_tol"]["oracle_seconds"]}
         line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -556,6 +781,7 @@ def main():
                 "time_to_tol_s": r["ms"] / 1000.0, "schedule": r["sched"],
                 "ne_res": r["ne"], "plain_lsqr": r["plain"], "clocks": r["clocks"],
                 "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roof"],
+                "roofline_hot_loop": r["hot"], "legs": r["legs"],
                 "spmv": r["spmv"], "batched": r["batched"],
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

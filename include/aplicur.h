@@ -18,8 +18,9 @@
  *  - Borrowed inputs (A, b) must stay alive and unmodified until
  *    aplicur_destroy.  The library never frees caller memory.
  *  - All work is issued on the stream given at creation (a cudaStream_t
- *    passed as void*; NULL means the legacy default stream).  Calls that
- *    return host results synchronise that stream.
+ *    passed as void*; NULL: a non-blocking stream the handle creates and owns, so
+ *    that graph captures on it never meet work on the legacy default stream of
+ *    other threads).  Calls that return host results synchronise that stream.
  *  - No C++ exception crosses this boundary.  Every call returns an
  *    aplicur_status; on failure aplicur_last_error(h) holds a message.
  *  - Calls on one handle are not thread-safe; distinct handles are.
@@ -239,7 +240,9 @@ aplicur_status aplicur_set_replay(aplicur_handle h, int32_t nphases, const int32
                                   int32_t nsteps, const int8_t* rebuild);
 
 /* Plain (unpreconditioned) LSQR on [A; delta I] with the same kernels and the
- * same stopping test: the comparison baseline.  x_out device n doubles. */
+ * same stopping test: the comparison baseline.  x_out device n doubles.  Clears the CUR
+ * state of the handle, so that a following aplicur_backward is the unpreconditioned
+ * adjoint solve of this baseline. */
 aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, double* x_out);
 
 /* Adjoint of the last solve (not in the paper).  With g = dL/dx (device, n),
@@ -249,7 +252,7 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
  *   grad_mu = -lambda^T x                 (host, 1 double, may be NULL)
  *   grad_A  = r lambda^T - (A lambda) x^T (device, m x n row-major in A's dtype,
  *             leading dim n; dense A only; may be NULL), r = b - A x.
- * Requires mu > 0 and a previous aplicur_solve. */
+ * Requires mu > 0 and a previous aplicur_solve (or aplicur_plain_lsqr: then P = I). */
 aplicur_status aplicur_backward(aplicur_handle h, const double* grad_x, double tol,
                                 int64_t maxit, double* grad_b, double* grad_mu, void* grad_A);
 

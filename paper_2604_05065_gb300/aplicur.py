@@ -19,7 +19,9 @@ PREC_FP64, PREC_MIXED, PREC_DF32 = 0, 1, 2
 
 
 class AplicurError(RuntimeError):
-    def __init__(self, status: int, msg: str):
+    def __init__(self, status: int, msg: str, allocator=None):
+        if status == 2 and allocator is not None and allocator.last_error:
+            msg = f"{msg} ({allocator.last_error})"
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
 
@@ -156,6 +158,7 @@ class DeviceAllocator:
         self.live = {}
         self.allocs = 0
         self.bytes = 0
+        self.last_error = None   # the exception of the last refused allocation
         alloc = alloc or (lambda nbytes, stream: torch.cuda.caching_allocator_alloc(
             nbytes, self.index, stream))
         free = free or torch.cuda.caching_allocator_delete
@@ -163,7 +166,8 @@ class DeviceAllocator:
         def _alloc(nbytes, stream, _ctx):
             try:
                 ptr = int(alloc(int(nbytes), int(stream or 0)))
-            except Exception:   # the library turns NULL into ENOMEM
+            except Exception as e:   # the library turns NULL into ENOMEM
+                self.last_error = f"{type(e).__name__}: {e}"
                 return None
             self.live[ptr] = int(nbytes)
             self.allocs += 1
@@ -209,10 +213,10 @@ def default_options() -> Options:
     return o
 
 
-def _check(lib, st, h=None):
+def _check(lib, st, h=None, allocator=None):
     if st != 0 and st != 4:
         msg = lib.aplicur_last_error(h).decode() if h is not None else ""
-        raise AplicurError(st, msg)
+        raise AplicurError(st, msg, allocator)
     return st
 
 
@@ -311,7 +315,7 @@ class Solver:
         st = lib.aplicur_create(C.byref(h), C.byref(mat), b.data_ptr(), self.mu, self.sketch_dim,
                                 C.byref(o), C.c_void_p(stream))
         if st != 0:
-            raise AplicurError(st, lib.aplicur_last_error(None).decode())
+            raise AplicurError(st, lib.aplicur_last_error(None).decode(), allocator)
         self._h = h
         _LIVE_HANDLES.add(self)
         if replay is not None:
@@ -331,7 +335,7 @@ class Solver:
         torch = _torch()
         x = torch.empty(self.n, dtype=torch.float64, device=self.device)
         st = self._lib.aplicur_solve(self._h, tol, maxit, x.data_ptr())
-        _check(self._lib, st, self._h)
+        _check(self._lib, st, self._h, self.allocator)
         self.last_status = st
         return x
 
@@ -339,7 +343,7 @@ class Solver:
         torch = _torch()
         x = torch.empty(self.n, dtype=torch.float64, device=self.device)
         st = self._lib.aplicur_plain_lsqr(self._h, tol, maxit, x.data_ptr())
-        _check(self._lib, st, self._h)
+        _check(self._lib, st, self._h, self.allocator)
         self.last_status = st
         return x
 
@@ -353,7 +357,7 @@ class Solver:
             gA = torch.empty(self.m, self.n, dtype=self.dtype, device=self.device)
         st = self._lib.aplicur_backward(self._h, g.data_ptr(), tol, maxit, gb.data_ptr(),
                                         C.byref(gmu), gA.data_ptr() if gA is not None else None)
-        _check(self._lib, st, self._h)
+        _check(self._lib, st, self._h, self.allocator)
         return gb, gmu.value, gA
 
     def set_replay(self, replay: dict):
@@ -362,7 +366,7 @@ class Solver:
         rb = np.ascontiguousarray(replay.get("rebuild", []), dtype=np.int8)
         st = self._lib.aplicur_set_replay(self._h, ph.size, ph.ctypes.data if ph.size else None,
                                           rb.size, rb.ctypes.data if rb.size else None)
-        _check(self._lib, st, self._h)
+        _check(self._lib, st, self._h, self.allocator)
 
     # ------------------------------------------------------------------ queries -----
     def indices(self):
@@ -609,7 +613,7 @@ class BatchSolver:
         st = lib.aplicur_batch_create(C.byref(h), len(mats), arr, bptr, R, float(mu),
                                       int(sketch_dim), C.byref(o), C.c_void_p(stream))
         if st != 0:
-            raise AplicurError(st, lib.aplicur_batch_last_error(None).decode())
+            raise AplicurError(st, lib.aplicur_batch_last_error(None).decode(), allocator)
         self._h = h
         _LIVE_HANDLES.add(self)
 
@@ -629,7 +633,8 @@ class BatchSolver:
         ptr = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
         st = fn(self._h, float(tol), int(maxit), ptr)
         if st != 0 and st != 4:
-            raise AplicurError(st, self._lib.aplicur_batch_last_error(self._h).decode())
+            raise AplicurError(st, self._lib.aplicur_batch_last_error(self._h).decode(),
+                               self.allocator)
         self.last_status = st
         return [x.t() for x in xs]
 

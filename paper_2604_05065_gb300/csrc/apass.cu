@@ -4,17 +4,17 @@
 // Layout.  A persistent grid of thread-block clusters; a cluster of C CTAs owns a
 // contiguous range of rows of A, and CTA c of the cluster owns the column panel
 // [c W, c W + W).  A producer warp streams row segments of its panel into a ring of S
-// shared-memory stages with bulk (TMA) copies completing on mbarriers; eight consumer
-// warps then, per tile of R rows,
-//   1. form the partial dot products of the R rows with z over the panel,
-//   2. send them to every CTA of the cluster (distributed shared memory, remote mbarrier
-//      arrive), and, one tile later,
-//   3. add the C partials in rank order (every CTA gets the same u'_i), and accumulate
-//      A(i, panel)^T u'_i from the tile still in shared memory.
-// Each CTA ends with the column partials of its panel over its cluster's rows; the
-// column-sum kernel adds them in cluster order.  Every wait is bounded in time; a wait
-// that gives up sets the error flag and the kernel finishes its protocol without data
-// (no barrier is skipped, no copy is left in flight at exit).
+// shared-memory stages with bulk (TMA) copies completing on mbarriers.  Per tile of R
+// rows, the compute warps form the partial dot products of the rows with z over the
+// panel; a sender warp adds them and stores them into every CTA of the cluster with
+// st.async (distributed shared memory, completing transaction bytes on the receiver's
+// mbarrier); one step later a u' warp adds the C partials in rank order (every CTA gets
+// the same u'_i), and one step after that the compute warps accumulate A(i, panel)^T u'_i
+// from the tile still in shared memory.  Each CTA ends with the column partials of its
+// panel over its cluster's rows; the column-sum kernel adds them in cluster order.  Every
+// wait is bounded in time; a wait that gives up sets the error flag and the kernel
+// finishes its protocol without data (no barrier is skipped, no copy is left in flight
+// at exit).
 #include <cuda_runtime.h>
 
 #include <algorithm>

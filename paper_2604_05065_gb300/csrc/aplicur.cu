@@ -715,7 +715,7 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
                   h->opt.schedule == APLICUR_SCHEDULE_SINGLE_SHOT,
               "bad schedule");
   if (stream) h->st = (cudaStream_t)stream;
-  else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
+  else { APL_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking)); h->own_stream = true; }
   cudaStream_t st = h->st;
   h->m = A->m; h->n = A->n; h->kmax = std::min(h->m, h->n);
   APL_REQUIRE(h->opt.max_rank >= 0, "max_rank must be >= 0");
@@ -919,6 +919,8 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
   return guarded(h, [&]() -> int {
     APL_REQUIRE(x_out != nullptr, "x_out NULL");
     auto t0 = std::chrono::steady_clock::now();
+    // no CUR state: a later aplicur_backward runs the adjoint solve unpreconditioned too
+    reset_cur(h);
     h->x.zero(h->st);
     h->phases.clear();
     PrecondDev I;
@@ -946,6 +948,9 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
     h->stats.ne_res = ne;
     h->stats.converged = ne <= tol;
     h->stats.nphases = (int)h->phases.size();
+    h->stats.ell = 0;
+    h->stats.nsteps = 0;
+    h->solved = true;
     APL_CUDA(cudaMemcpyAsync(x_out, h->x.p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     APL_CUDA(cudaStreamSynchronize(h->st));
     h->stats.time_solve_ms =
@@ -1473,7 +1478,7 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     }
     APL_CUDA(cudaGetDevice(&h->device));
     if (stream) h->st = (cudaStream_t)stream;
-    else { APL_CUDA(cudaStreamCreate(&h->st)); h->own_stream = true; }
+    else { APL_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking)); h->own_stream = true; }
     h->np = nprob;
     h->R = nrhs;
     h->mu = mu;

@@ -1105,7 +1105,8 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   APL_CUDA(cudaStreamSynchronize(st_));
   if (fused_.ok) {
     int fe = 0;
-    APL_CUDA(cudaMemcpy(&fe, ferr_.p, sizeof(int), cudaMemcpyDeviceToHost));
+    APL_CUDA(cudaMemcpyAsync(&fe, ferr_.p, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    APL_CUDA(cudaStreamSynchronize(st_));
     if (fe) throw Error(ST_ETIMEOUT, "fused A pass: a bounded wait ran past its bound");
   }
   return res;

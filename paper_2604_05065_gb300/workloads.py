@@ -277,3 +277,24 @@ def batched_device(device, nprob=512, m_range=(2000, 50000), n_range=(100, 2000)
         sizes.append((m, n, "dense" if p < half else "csr"))
     return mats, rhs, sizes
 
+
+
+def config5_device(device, mu: float = 1e-4, index=5):
+    """The adjoint workload generated on the GPU (torch, seeded): the recipe of ``config5``
+    (A = U diag(exp(-i/200)) V^T of 100000 x 2000 stored in FP32, U and V from QR of
+    Gaussians drawn on the device; b and x_target ~ N(0, 1)), for the benchmark, where
+    host generation would take a QR of a 100000 x 2000 matrix on the CPU.  Returns
+    (A, b, x_target, mu, sketch_dim) as device tensors."""
+    import torch
+
+    m, n = 100000, 2000
+    gen = torch.Generator(device=device)
+    gen.manual_seed(BASE_SEED + 50 + index)
+    U, _ = torch.linalg.qr(torch.randn(m, n, generator=gen, device=device, dtype=torch.float64))
+    V, _ = torch.linalg.qr(torch.randn(n, n, generator=gen, device=device, dtype=torch.float64))
+    s = torch.exp(-torch.arange(n, device=device, dtype=torch.float64) / 200.0)
+    A = ((U * s) @ V.T).to(torch.float32).contiguous()
+    del U, V
+    b = torch.randn(m, generator=gen, device=device, dtype=torch.float64)
+    xt = torch.randn(n, generator=gen, device=device, dtype=torch.float64)
+    return A, b, xt, mu, 100

@@ -43,6 +43,13 @@ def main(name):
                           for st in res.rank_steps],
            "I": [int(i) for i in res.I], "J": [int(j) for j in res.J],
            "oracle_seconds": round(time.time() - t0, 1)}
+    # the same solve to the bench's tolerance: its schedule and the oracle's time, which
+    # the CPU baseline's stratified sample should reproduce
+    t0 = time.time()
+    r8 = O.aplicur(A, p.b, p.mu, p.sketch_dim, O.Options(seed=1), tol=1e-8, maxit=20000)
+    out["bench_tol"] = {"tol": 1e-8, "iters": int(r8.iters), "ne_res": float(r8.ne_res),
+                        "phases": [int(ph["iters"]) for ph in r8.phases],
+                        "oracle_seconds": round(time.time() - t0, 1)}
     idx = np.sort(np.random.default_rng(SAMPLE_SEED).choice(p.n, size=min(256, p.n),
                                                             replace=False))
     out["x_sample_index"] = [int(i) for i in idx]

@@ -56,8 +56,9 @@ def test_bench_defines_every_leg():
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
-    for name in ("gpu_arm", "spmv_measure", "batched_measure", "roofline", "traffic_for",
-                 "oracle_sample", "reference_arm", "make_config", "aggregate"):
+    for name in ("gpu_arm", "spmv_measure", "batched_measure", "legs_measure", "roofline",
+                 "hot_loop_roofline", "traffic_for", "oracle_baseline", "OracleReplay",
+                 "reference_arm", "make_config", "aggregate", "cpu_info"):
         assert callable(getattr(mod, name)), name
 
 
@@ -83,3 +84,34 @@ def test_roofline_names_the_dominant_family_and_its_rate():
     assert r["achieved"] == pytest.approx(10.0)
     assert r["frac"] == pytest.approx(10.0 / r["peak"], rel=1e-3)
     assert r["families"][mod.NAMES[0]]["GBps"] == pytest.approx(500.0)
+
+
+def test_oracle_replay_strata_follow_the_schedule():
+    """The CPU baseline's strata: the sketch, every rank step, and per rebuild the build
+    and a phase sample scaled by the phase length, in driver order; running them all on a
+    small problem covers every stratum, and the assembled solve time is their scaled sum."""
+    import importlib.util
+    import os
+
+    from oracle import aplicur_oracle as O
+    from paper_2604_05065_gb300 import workloads as wl
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod3", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    p = wl.config1(scale=4)
+    res = O.aplicur(p.dense, p.b, p.mu, p.sketch_dim, O.Options(seed=1), tol=1e-8)
+    gold = {"rank_steps": res.rank_steps,
+            "bench_tol": {"phases": [ph["iters"] for ph in res.phases]}}
+    rep = mod.OracleReplay(p, gold)
+    names = [nm for nm, _, _ in rep.strata]
+    nb = sum(1 for st in res.rank_steps if st["rebuild"])
+    assert names[0] == "sketch" and len(names) == 1 + len(res.rank_steps) + 2 * nb
+    assert sum(1 for nm in names if nm.startswith("rank step")) == len(res.rank_steps)
+    while not rep.covered():
+        rep.run_next()
+    tot = sum(sum(v) / len(v) * sc for (nm, _, sc) in rep.strata for v in [rep.times[nm]])
+    assert rep.solve_seconds() == pytest.approx(tot)
+    ph = [sc for nm, _, sc in rep.strata if nm.startswith("phase")]
+    iters = gold["bench_tol"]["phases"]
+    assert ph == pytest.approx([(k + 2) / (rep.SAMPLE_ITERS + 2) for k in iters[:len(ph)]])
