@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the other configurations' time-to-tol legs")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline workload only (no e2e, plain LSQR, legs, SpMV, "
+                         "batched or CPU legs): the profiling runs under profiles/")
+    ap.add_argument("--npts", type=int, default=0,
+                    help="RBF points of a smaller RBF case (profiling; 0: the workload)")
+    ap.add_argument("--precision", default="", choices=["", "fp64", "mixed", "df32"],
+                    help="override the workload's arithmetic (profiling)")
     ap.add_argument("--batched-nprob", type=int, default=64,
                     help="problems of the batched workload (512 is the full configuration; a "
                          "full solve takes minutes, so the default line carries 64)")
@@ -79,10 +86,14 @@ def aggregate(ms_local, steps, world, device=None):
     return ms_max, world * steps / (ms_max / 1000.0)
 
 
-def make_workload(name):
+def make_workload(name, npts=0, precision=""):
     from paper_2604_05065_gb300 import workloads as wl
     gen, prec = WORKLOADS[name]
-    return getattr(wl, gen)(), prec
+    if npts and gen == "config3":
+        p = wl.rbf_kernel(npts=npts, sketch_dim=max(5, 250 * npts // 20000))
+    else:
+        p = getattr(wl, gen)()
+    return p, precision or prec
 
 
 # ----------------------------------------------------------------------------- clocks ---
@@ -149,7 +160,10 @@ def gpu_arm(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    p, prec = make_workload(args.workload)
+    if args.only_headline:
+        args.no_plain = args.no_legs = args.no_spmv = args.no_batched = True
+        args.no_cpu_baseline = True
+    p, prec = make_workload(args.workload, args.npts, args.precision)
     precision = {"mixed": pkg.PREC_MIXED, "df32": pkg.PREC_DF32}.get(prec, pkg.PREC_FP64)
     if p.fmt == "dense":
         A_host = torch.from_numpy(p.dense).pin_memory()
@@ -215,7 +229,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---- end to end from pinned host buffers
     e2e = None
-    if A_host is not None:
+    if A_host is not None and not args.only_headline:
         Ae = torch.empty_like(A)
         be = torch.empty_like(b)
         for _ in range(1):
