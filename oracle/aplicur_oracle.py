@@ -122,6 +122,14 @@ def apply_sketch(A, srows: np.ndarray, signs: np.ndarray, s: int) -> np.ndarray:
     return Y
 
 
+def dense_sketch(A, S: np.ndarray) -> np.ndarray:
+    """Y = S A for a dense sketching operator S (s x m): the Gaussian embedding or the
+    SRFT of the appendix "Sketch comparison", applied by its definition in FP64."""
+    if _is_sparse(A):
+        return np.asarray((A.T @ S.T).T, dtype=np.float64)
+    return S @ np.asarray(A, dtype=np.float64)
+
+
 # --------------------------------------------------------------------------------------
 # LU with partial pivoting, first k pivots (used by augmentCUR)
 # --------------------------------------------------------------------------------------
@@ -569,7 +577,7 @@ class Result:
 
 
 def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-10,
-            maxit=100000, srows=None, signs=None, W=None) -> Result:
+            maxit=100000, srows=None, signs=None, W=None, S=None) -> Result:
     """Adaptive CUR-preconditioned LSQR for min ||A x - b||^2 + mu ||x||^2."""
     opts = opts or Options()
     if _is_sparse(A):
@@ -591,7 +599,8 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
         return Result(np.zeros(n), np.zeros(0, np.int64), np.zeros(0, np.int64), True, 0, 0.0,
                       [], [], np.zeros((s, n)), None)
 
-    Y = apply_sketch(A, srows, signs, s)
+    # S: a dense sketching operator (s x m) in place of the sparse sign embedding
+    Y = apply_sketch(A, srows, signs, s) if S is None else dense_sketch(A, S)
     I = np.zeros(0, np.int64)
     J = np.zeros(0, np.int64)
     core = None

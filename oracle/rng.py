@@ -116,3 +116,76 @@ def gaussian_w(seed: int, n: int, r: int) -> np.ndarray:
     vals = np.fromiter((math.sqrt(-2.0 * math.log(a)) * math.cos(two_pi * c)
                         for a, c in zip(u1.tolist(), u2.tolist())), dtype=np.float64, count=total)
     return vals.reshape(r, n).T.copy()
+
+
+# ---- dense sketching operators (Appendix "Sketch comparison": Gaussian and SRFT) -------
+# Stream layout, continuing the one above:
+#   t = 4: entry (r, c) of the Gaussian sketch G (s x m), index c * s + r (column-major);
+#          value from two draws by Box-Muller as for W; S = G / sqrt(s).
+#   t = 5: sign d_c of column c of the subsampled randomized Hadamard transform (bit 63 of
+#          the first draw of stream (5, c): clear +1, set -1);
+#   t = 6: its s sampled rows of the m' x m' Hadamard matrix (m' = the power of two >= m),
+#          drawn one after another from stream (6, 0) as ((z >> 32) * m') >> 32, a row
+#          already taken drawn again; rows kept in draw order.
+
+
+def _gaussian_entries(seed: int, t: int, total: int) -> np.ndarray:
+    st = _stream_state_np(seed, t, np.arange(total, dtype=np.uint64))
+    st1 = st + np.uint64(GOLDEN)
+    st2 = st1 + np.uint64(GOLDEN)
+    z1 = _mix64_np(st1)
+    z2 = _mix64_np(st2)
+    u1 = ((z1 >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
+    u2 = (z2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    two_pi = 2.0 * math.pi
+    return np.fromiter((math.sqrt(-2.0 * math.log(a)) * math.cos(two_pi * c)
+                        for a, c in zip(u1.tolist(), u2.tolist())), dtype=np.float64, count=total)
+
+
+def gaussian_sketch(seed: int, s: int, m: int) -> np.ndarray:
+    """The s x m Gaussian embedding G / sqrt(s), G i.i.d. N(0, 1)."""
+    g = _gaussian_entries(seed, 4, s * m)
+    return g.reshape(m, s).T / math.sqrt(s)
+
+
+def srht_rows_signs(seed: int, s: int, m: int):
+    """(sampled Hadamard rows (s,), column signs (m,)) of the SRHT of m columns."""
+    mp = 1
+    while mp < m:
+        mp *= 2
+    if s > mp:
+        raise ValueError("need s <= the padded length")
+    st = stream_state(seed, 6, 0)
+    rows, taken = [], set()
+    while len(rows) < s:
+        st = (st + GOLDEN) & MASK
+        p = ((mix64(st) >> 32) * mp) >> 32
+        if p not in taken:
+            taken.add(p)
+            rows.append(p)
+    sst = _stream_state_np(seed, 5, np.arange(m, dtype=np.uint64)) + np.uint64(GOLDEN)
+    signs = np.where((_mix64_np(sst) >> np.uint64(63)) == 0, 1.0, -1.0)
+    return np.array(rows, dtype=np.int64), signs
+
+
+def srht_sketch(seed: int, s: int, m: int) -> np.ndarray:
+    """The s x m subsampled randomized Hadamard transform (1 / sqrt(s)) R H D: row r holds
+    (-1)^popcount(p_r & c) d_c / sqrt(s), p_r the sampled row of the unnormalised m' x m'
+    Walsh-Hadamard matrix (its columns beyond m meet the zero padding of A)."""
+    rows, d = srht_rows_signs(seed, s, m)
+    c = np.arange(m, dtype=np.int64)
+    par = np.zeros((s, m), dtype=np.int64)
+    x = rows[:, None] & c[None, :]
+    while np.any(x):
+        par ^= x & 1
+        x >>= 1
+    return np.where(par == 0, 1.0, -1.0) * d[None, :] / math.sqrt(s)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round to bfloat16 (round to nearest, ties to even) after rounding to FP32, returned as
+    float64: the rounding of the tensor-core sketch operands (FP64 values go to FP32 first)."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return (u.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)

@@ -695,3 +695,58 @@ def test_ridge_reduced_matches_direct_solves_and_rank_one_changes():
         gg = g.standard_normal(30)
         lam_o = O.ridge_gradients(A, b, mu, x, gg)[0]
         assert np.allclose(red.adjoint(mu, gg), lam_o, rtol=1e-9, atol=0)
+
+
+# ---------------------------------------------------------------- dense sketches ------
+
+def test_gaussian_sketch_moments_and_embedding():
+    """Entries of G / sqrt(s) have mean 0 and variance 1/s, and E ||S x||^2 = ||x||^2."""
+    s, m = 20, 5000
+    S = orng.gaussian_sketch(11, s, m)
+    assert S.shape == (s, m)
+    v = S.ravel() * math.sqrt(s)
+    assert abs(v.mean()) < 5.0 / math.sqrt(v.size)
+    assert abs(v.var() - 1.0) < 5.0 * math.sqrt(2.0 / v.size)
+    x = np.random.default_rng(2).standard_normal(300)
+    # seeds far apart: the stream of entry i is keyed by seed ^ i, so nearby small seeds
+    # would share entries
+    vals = [np.linalg.norm(orng.gaussian_sketch(k << 40, 10, 300) @ x) ** 2 for k in range(200)]
+    assert np.mean(vals) == pytest.approx(float(x @ x), rel=0.1)
+
+
+def test_srht_rows_are_sylvester_hadamard_rows():
+    """S sqrt(s) / d equals the sampled rows of scipy's Sylvester-Hadamard matrix (columns
+    past m cut), S S^T = (m/s) I when m is a power of two, and E ||S x||^2 = ||x||^2 with
+    padding."""
+    s, m = 12, 64
+    S = orng.srht_sketch(4, s, m)
+    rows, d = orng.srht_rows_signs(4, s, m)
+    assert len(set(rows.tolist())) == s
+    H = sla.hadamard(64)
+    assert np.array_equal(S * math.sqrt(s) / d[None, :], H[rows, :m])
+    assert np.allclose(S @ S.T, (m / s) * np.eye(s), atol=1e-12)
+    x = np.random.default_rng(3).standard_normal(50)   # padded to 64
+    vals = [np.linalg.norm(orng.srht_sketch(k << 40, 16, 50) @ x) ** 2 for k in range(300)]
+    assert np.mean(vals) == pytest.approx(float(x @ x), rel=0.1)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(9).standard_normal(10000) * 10.0 ** np.random.default_rng(10).integers(-20, 20, 10000)
+    ours = orng.round_bf16(x)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ours, ref)
+    assert orng.round_bf16([1.0 + 2.0 ** -8])[0] == 1.0             # tie to even
+    assert orng.round_bf16([1.0 + 3 * 2.0 ** -8])[0] == 1.0 + 2 ** -6  # tie to even, up
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "srht"])
+def test_aplicur_with_dense_sketch_reaches_ridge_solution(kind):
+    p = wl.small_dense(400, 50, 4646, decay=3.0, mu=1e-4, sketch_dim=5)
+    s = O.sketch_rows(5)
+    S = (orng.gaussian_sketch if kind == "gaussian" else orng.srht_sketch)(2, s, p.m)
+    res = O.aplicur(p.dense, p.b, p.mu, 5, O.Options(seed=2), tol=1e-11, S=S)
+    assert res.converged
+    assert np.allclose(res.Y, S @ p.dense, rtol=1e-13, atol=1e-13 * np.abs(res.Y).max())
+    x = O.ridge_direct(p.dense, p.b, p.mu)
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-7
