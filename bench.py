@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--maxit", type=int, default=200000)
     ap.add_argument("--no-spmv", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-sketch", action="store_true",
+                    help="skip the sketching-operator leg (dense workloads)")
+    ap.add_argument("--only-sketch", action="store_true",
+                    help="run the sketching-operator leg alone and print it (1 GPU)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the other configurations' time-to-tol legs")
     ap.add_argument("--only-headline", action="store_true",
@@ -161,7 +165,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     if args.only_headline:
-        args.no_plain = args.no_legs = args.no_spmv = args.no_batched = True
+        args.no_plain = args.no_legs = args.no_spmv = args.no_batched = args.no_sketch = True
         args.no_cpu_baseline = True
     p, prec = make_workload(args.workload, args.npts, args.precision)
     precision = {"mixed": pkg.PREC_MIXED, "df32": pkg.PREC_DF32}.get(prec, pkg.PREC_FP64)
@@ -178,6 +182,10 @@ def gpu_arm(args, rank, world, local_rank):
     b = b_host.to(dev, non_blocking=True)
     torch.cuda.synchronize()
     opts = dict(precision=precision, profile=1, seed=1)
+    if args.only_sketch:
+        print(json.dumps({"workload": p.name, "sketch": sketch_measure(args, dev, A, b, p,
+                                                                        precision)}))
+        return None
 
     nfam = len(pkg.PROFILE_FAMILIES)
     prof_tot = {"ms": [0.0] * nfam, "launches": [0] * nfam, "work": [0.0] * nfam}
@@ -272,11 +280,13 @@ def gpu_arm(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel family of the step (largest device time)
     roof = roofline(prof_tot)
     hot = hot_loop_roofline(prof_tot)
+    sketch = None if (args.no_sketch or p.fmt != "dense") else sketch_measure(
+        args, dev, A, b, p, precision)
     legs = None if (args.no_legs or world > 1) else legs_measure(args, dev)
     spmv = None if args.no_spmv else spmv_measure(args, dev)
     batched = None if (args.no_batched or world > 1) else batched_measure(args, dev)
     return dict(value=value, ms=ms_max / args.steps, p=p, prec=prec, clocks=clk, e2e=e2e,
-                batched=batched, hot=hot, legs=legs,
+                batched=batched, hot=hot, legs=legs, sketch=sketch,
                 plain=plain, roof=roof, launches=launches, sched=sched, ne=st["ne_res"],
                 spmv=spmv)
 
@@ -363,6 +373,60 @@ def legs_measure(args, dev):
     del A, b
     torch.cuda.empty_cache()
     return legs
+
+
+def sketch_measure(args, dev, A, b, p, precision):
+    """The one-time sketch Y = S A of the headline workload (dense FP32 A, s = 1.1 sketch
+    dim) with each operator: the sparse sign embedding (xi = 8, FP64 sums), the Gaussian
+    embedding as a compensated-FP32 product, and the Gaussian embedding on the tensor
+    cores with A in 1, 2 and 3 bfloat16 terms.  Device time of the product (the library's
+    events around it in aplicur_create; the host draw of S is outside), median of three
+    creations after one warm-up; the tensor-core forms also solve to the bench tolerance
+    (APLICUR from that sketch, the same precision as the headline)."""
+    import statistics
+
+    import paper_2604_05065_gb300 as pkg
+    m, n = p.m, p.n
+    sd = p.sketch_dim
+    srow = (11 * sd + 9) // 10
+    va = A.element_size()
+    out = {"s": srow}
+    forms = [("sparse_sign", dict(sketch_kind=pkg.SKETCH_SPARSE_SIGN)),
+             ("gaussian_compensated_fp32", dict(sketch_kind=pkg.SKETCH_GAUSSIAN)),
+             ("gaussian_tc_1term", dict(sketch_kind=pkg.SKETCH_GAUSSIAN, sketch_tc=1)),
+             ("gaussian_tc_2terms", dict(sketch_kind=pkg.SKETCH_GAUSSIAN, sketch_tc=2)),
+             ("gaussian_tc_3terms", dict(sketch_kind=pkg.SKETCH_GAUSSIAN, sketch_tc=3))]
+    for name, kw in forms:
+        times = []
+        for rep in range(4):
+            s = pkg.Solver(A, b, p.mu, sd, precision=precision, seed=1, **kw)
+            if rep:
+                times.append(s.stats()["time_setup_ms"])
+            if rep < 3:
+                s.close()
+        ms = statistics.median(times)
+        rec = {"ms": round(ms, 3)}
+        if kw.get("sketch_tc"):
+            k = kw["sketch_tc"]
+            # algorithmic bytes: A once, S~ once (bfloat16; re-read from L2 per column
+            # tile), Y written in FP64
+            byts = va * m * n + 2.0 * srow * m + 8.0 * srow * n
+            rec["achieved_gbs"] = round(byts / (ms * 1e-3) / 1e9, 1)
+            hbm, src = peaks()
+            rec[f"hbm_frac_of_{src}"] = round(byts / (ms * 1e-3) / 1e9 / hbm, 3)
+            rec["tensor_tflops"] = round(2.0 * k * srow * m * n / (ms * 1e-3) / 1e12, 1)
+            secs, _ = _timed(torch_stream(dev), lambda s=s: s.solve(TOL, args.maxit))
+            st = s.stats()
+            rec.update(solve_s=round(secs, 4), ell=st["ell"], iters=st["iters"],
+                       converged=bool(st["converged"]), rank_breakdown=st["rank_breakdown"])
+        s.close()
+        out[name] = rec
+    return out
+
+
+def torch_stream(dev):
+    import torch
+    return torch.cuda.current_stream(dev)
 
 
 def spmv_measure(args, dev):
@@ -776,6 +840,8 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     r = gpu_arm(args, rank, world, local_rank)
+    if r is None:
+        return
     if rank == 0:
         p = r["p"]
         cpu = None
@@ -795,7 +861,7 @@ def main():
                 "time_to_tol_s": r["ms"] / 1000.0, "schedule": r["sched"],
                 "ne_res": r["ne"], "plain_lsqr": r["plain"], "clocks": r["clocks"],
                 "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roof"],
-                "roofline_hot_loop": r["hot"], "legs": r["legs"],
+                "roofline_hot_loop": r["hot"], "legs": r["legs"], "sketch": r["sketch"],
                 "spmv": r["spmv"], "batched": r["batched"],
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

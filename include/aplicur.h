@@ -164,7 +164,29 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* alloc_ctx);
   void (*free_)(void* ptr, size_t bytes, void* stream, void* alloc_ctx);
   void* alloc_ctx;
+  /* The sketching operator S of Y = S A (appendix "Sketch comparison"):
+   *  APLICUR_SKETCH_SPARSE_SIGN (0, default): the sparse sign embedding of Section 5.1
+   *    (xi nonzeros per column, Y summed in a fixed FP64 order);
+   *  APLICUR_SKETCH_GAUSSIAN (1): G / sqrt(s) with G i.i.d. N(0, 1);
+   *  APLICUR_SKETCH_SRHT (2): the subsampled randomized Hadamard transform
+   *    (1 / sqrt(s)) R H D (random column signs D, s distinct sampled rows R of the
+   *    Walsh-Hadamard matrix of the padded length).
+   * The dense operators are drawn on the host from the project generator (seed) and
+   * applied as a product with A: FP64 products for CSR A, the dense routines' products
+   * (compensated FP32 by default) for dense A. */
+  int32_t sketch_kind;
+  /* 1, 2 or 3 (dense A and a dense operator only; 0 = off): Y on the tensor cores
+   * (tcgen05, FP32 accumulation), s <= 512.  S is rounded to bfloat16 (the rounded matrix
+   * is the sketching operator) and A, after rounding to FP32, is represented by the first
+   * sketch_tc terms of its bfloat16 expansion A_0 + A_1 + A_2 (A_0 = bf16(A), A_1 =
+   * bf16(A - A_0), ...; three terms hold an FP32 value exactly).  One term leaves a noise
+   * floor of about 2^-9 |A| entrywise in the sketch, which the adaptive rank cannot see
+   * through when delta is below it; two terms lower it to 2^-17; three leave the FP32
+   * accumulation only.  The CUR indices can differ from those of the FP64 sketch. */
+  int32_t sketch_tc;
 } aplicur_options;
+
+enum { APLICUR_SKETCH_SPARSE_SIGN = 0, APLICUR_SKETCH_GAUSSIAN = 1, APLICUR_SKETCH_SRHT = 2 };
 
 enum { APLICUR_DENSE_PASS_AUTO = 0, APLICUR_DENSE_PASS_TWO = 1, APLICUR_DENSE_PASS_FUSED = 2 };
 
@@ -206,6 +228,11 @@ typedef struct {
   double time_lsqr_ms;  /*           LSQR phases and residual checks */
   int32_t fused_pass;   /* 1: LSQR iterations read dense A once (fused A pass) */
   int32_t cluster_size; /* CTAs per thread-block cluster of the fused pass (0: not used) */
+  int32_t rank_breakdown; /* 1: a rank step met a non-positive Cholesky pivot (the new
+                           * columns or rows were numerically dependent on the selected
+                           * ones); rank growth ended there and the solve finished with
+                           * the last preconditioner built (the batched driver does the
+                           * same per problem) */
 } aplicur_stats;
 
 /* Fill `opt` with the defaults above. */

@@ -189,3 +189,18 @@ def round_bf16(x) -> np.ndarray:
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
     return (u.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def bf16_pieces(x, k: int) -> list:
+    """The k-term bfloat16 expansion of fp32(x): p_0 = bf16(f), p_j = bf16(f - p_0 - ... -
+    p_{j-1}) with every difference taken in FP32 (exact: each residual has at most 24 - 8 j
+    significant bits left).  Three terms represent an FP32 value exactly (barring underflow
+    below 2^-126); returned as float64 arrays.  The operand representation of A in the
+    tensor-core sketch."""
+    r = np.asarray(x, dtype=np.float32).copy()
+    out = []
+    for _ in range(k):
+        p = round_bf16(r)
+        out.append(p)
+        r = (r - p.astype(np.float32)).astype(np.float32)
+    return out

@@ -6,4 +6,4 @@ The solver lives in the CUDA library libaplicur.so (C ABI in include/aplicur.h);
 """
 from .aplicur import (AplicurError, BatchSolver, DeviceAllocator, Solver, aplicur_solve_fn, default_options, load,  # noqa
                       solve, launch_count, PREC_FP64, PREC_MIXED, PREC_DF32,
-                      PROFILE_FAMILIES)
+                      SKETCH_SPARSE_SIGN, SKETCH_GAUSSIAN, SKETCH_SRHT, PROFILE_FAMILIES)

@@ -16,6 +16,7 @@ REASONS = {0: "none", 1: "exact", 2: "replay", 3: "ps_test2", 4: "ps_test1", 5: 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
           6: "ETIMEOUT"}
 PREC_FP64, PREC_MIXED, PREC_DF32 = 0, 1, 2
+SKETCH_SPARSE_SIGN, SKETCH_GAUSSIAN, SKETCH_SRHT = 0, 1, 2
 
 
 class AplicurError(RuntimeError):
@@ -43,7 +44,8 @@ class Options(C.Structure):
                 ("replay_nsteps", C.c_int32), ("replay_rebuild", C.c_void_p),
                 ("profile", C.c_int32), ("max_rank", C.c_int32), ("fp64_dense", C.c_int32),
                 ("variant", C.c_int32), ("schedule", C.c_int32), ("dense_pass", C.c_int32),
-                ("alloc", C.c_void_p), ("free_", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+                ("alloc", C.c_void_p), ("free_", C.c_void_p), ("alloc_ctx", C.c_void_p),
+                ("sketch_kind", C.c_int32), ("sketch_tc", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -64,7 +66,8 @@ class Stats(C.Structure):
                 ("rho", C.c_double), ("time_setup_ms", C.c_double),
                 ("time_solve_ms", C.c_double), ("time_rank_ms", C.c_double),
                 ("time_build_ms", C.c_double), ("time_lsqr_ms", C.c_double),
-                ("fused_pass", C.c_int32), ("cluster_size", C.c_int32)]
+                ("fused_pass", C.c_int32), ("cluster_size", C.c_int32),
+                ("rank_breakdown", C.c_int32)]
 
 
 class BatchStats(C.Structure):

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaplicur.so")
-SOURCES = ["aplicur.cu", "lsqr.cu", "apass.cu", "cur.cu", "dense.cu", "gemm.cu", "batch.cu"]
+SOURCES = ["aplicur.cu", "lsqr.cu", "apass.cu", "cur.cu", "dense.cu", "gemm.cu", "batch.cu",
+           "tcsketch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -16,6 +16,7 @@
 #include "batch.cuh"
 #include "dense.cuh"
 #include "lsqr.cuh"
+#include "tcsketch.cuh"
 
 using namespace apl;
 
@@ -54,6 +55,45 @@ void draw_sketch(uint64_t seed, int s, int64_t m, int xi, std::vector<int>& rows
       ss += GOLDEN;
       signs[i * xi + k] = (mix64(ss) >> 63) == 0 ? 1 : -1;
     }
+  }
+}
+
+// Dense sketching operators of the appendix "Sketch comparison", s x m column-major.
+// Gaussian embedding: entry (r, c) from stream (4, c s + r) by Box-Muller, divided by
+// sqrt(s).  Subsampled randomized Hadamard transform: column signs d_c from the first draw
+// of stream (5, c) (bit 63 clear: +1), s distinct rows p_r of the m' x m' Walsh-Hadamard
+// matrix (m' the power of two >= m) drawn in turn from stream (6, 0) as
+// ((z >> 32) m') >> 32, entry (-1)^popcount(p_r & c) d_c / sqrt(s).
+void draw_gaussian_sketch(uint64_t seed, int s, int64_t m, std::vector<double>& S) {
+  S.resize((size_t)s * m);
+  const double two_pi = 2.0 * M_PI, sc = 1.0 / std::sqrt((double)s);
+  for (int64_t idx = 0; idx < (int64_t)s * m; ++idx) {
+    const uint64_t st = stream_state(seed, 4, (uint64_t)idx);
+    const uint64_t z1 = mix64(st + GOLDEN);
+    const uint64_t z2 = mix64(st + 2 * GOLDEN);
+    const double u1 = (double)((z1 >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+    S[idx] = std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2) * sc;
+  }
+}
+
+void draw_srht_sketch(uint64_t seed, int s, int64_t m, std::vector<double>& S) {
+  uint64_t mp = 1;
+  while ((int64_t)mp < m) mp <<= 1;
+  APL_REQUIRE((uint64_t)s <= mp, "SRHT: sketch rows exceed the padded length");
+  std::vector<uint64_t> rows;
+  uint64_t st = stream_state(seed, 6, 0);
+  while ((int)rows.size() < s) {
+    st += GOLDEN;
+    const uint64_t p = ((mix64(st) >> 32) * mp) >> 32;
+    if (std::find(rows.begin(), rows.end(), p) == rows.end()) rows.push_back(p);
+  }
+  S.resize((size_t)s * m);
+  const double sc = 1.0 / std::sqrt((double)s);
+  for (int64_t c = 0; c < m; ++c) {
+    const double d = (mix64(stream_state(seed, 5, (uint64_t)c) + GOLDEN) >> 63) == 0 ? 1.0 : -1.0;
+    for (int r = 0; r < s; ++r)
+      S[(size_t)c * s + r] = (__builtin_popcountll(rows[r] & (uint64_t)c) & 1) ? -d * sc : d * sc;
   }
 }
 
@@ -158,6 +198,7 @@ struct aplicur_ctx {
   DenseWork dw;  // scratch of the dense routines, used on st only
   Allocator alloc_;       // caller's device allocator (empty: cudaMallocAsync)
   bool poisoned = false;  // a bounded device wait gave up: buffers undefined
+  TcSketchWork tcw;       // tensor-core sketch (dense operators in bfloat16)
 };
 
 namespace {
@@ -628,11 +669,22 @@ int do_solve(aplicur_ctx* h, double tol, long long maxit) {
     return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
   };
   h->stats.time_rank_ms = h->stats.time_build_ms = h->stats.time_lsqr_ms = 0.0;
+  h->stats.rank_breakdown = 0;
   while (true) {
     double rho = 0, margin = INFINITY;
     bool exhausted = false;
     auto t0 = clk::now();
-    rank_step(h, &rho, &exhausted, &margin);
+    try {
+      rank_step(h, &rho, &exhausted, &margin);
+    } catch (const Error& e) {
+      // numerically dependent new indices: rank growth ends at the current rank (the
+      // step's partial writes lie beyond it), and the solve goes on with the last
+      // preconditioner built
+      if (e.code != ST_EBREAKDOWN) throw;
+      h->stats.rank_breakdown = 1;
+      h->stats.time_rank_ms += ms_since(t0);
+      break;
+    }
     h->stats.time_rank_ms += ms_since(t0);
     h->stats.rho = rho;
     const bool full = h->ell >= h->kmax;
@@ -714,6 +766,13 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   APL_REQUIRE(h->opt.schedule == APLICUR_SCHEDULE_ADAPTIVE ||
                   h->opt.schedule == APLICUR_SCHEDULE_SINGLE_SHOT,
               "bad schedule");
+  APL_REQUIRE(h->opt.sketch_kind >= APLICUR_SKETCH_SPARSE_SIGN &&
+                  h->opt.sketch_kind <= APLICUR_SKETCH_SRHT,
+              "bad sketch_kind");
+  APL_REQUIRE(h->opt.sketch_tc >= 0 && h->opt.sketch_tc <= 3, "sketch_tc: 0 to 3 terms");
+  APL_REQUIRE(!h->opt.sketch_tc || (h->opt.sketch_kind != APLICUR_SKETCH_SPARSE_SIGN &&
+                                    A->format == APLICUR_DENSE_ROWMAJOR),
+              "sketch_tc needs a dense operator (Gaussian or SRHT) and a dense A");
   if (stream) h->st = (cudaStream_t)stream;
   else { APL_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking)); h->own_stream = true; }
   cudaStream_t st = h->st;
@@ -730,6 +789,8 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   h->bsize = sketch_dim;
   h->s = (11 * sketch_dim + 9) / 10;
   h->xi = std::min(h->opt.xi, h->s);
+  APL_REQUIRE(!h->opt.sketch_tc || h->s <= TC_SKETCH_MAX_S,
+              "sketch_tc: the tensor-core sketch takes s = ceil(1.1 sketch_dim) <= 512");
   h->dw.fp64_gemm = h->opt.fp64_dense != 0;
   h->r = h->opt.normest_r;
   if (h->A.fmt == 1) build_csc(h);
@@ -772,8 +833,31 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   APL_CUDA(cudaEventCreate(&e0));
   APL_CUDA(cudaEventCreate(&e1));
   APL_CUDA(cudaEventRecord(e0, st));
-  sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
-         1.0 / std::sqrt((double)h->xi), h->Y.p);
+  if (h->opt.sketch_kind == APLICUR_SKETCH_SPARSE_SIGN) {
+    sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
+           1.0 / std::sqrt((double)h->xi), h->Y.p);
+  } else {
+    // a dense operator drawn on the host (the draw is not part of the timed product)
+    APL_CUDA(cudaEventRecord(e1, st));
+    APL_CUDA(cudaEventSynchronize(e1));
+    std::vector<double> S;
+    if (h->opt.sketch_kind == APLICUR_SKETCH_GAUSSIAN) draw_gaussian_sketch(h->opt.seed, h->s, h->m, S);
+    else draw_srht_sketch(h->opt.seed, h->s, h->m, S);
+    if (h->opt.sketch_tc) {
+      tc_sketch_upload(st, S.data(), h->s, h->m, h->n, h->tcw);
+      APL_CUDA(cudaEventRecord(e0, st));
+      tc_sketch_apply(st, h->A, h->tcw, h->Y.p, h->opt.sketch_tc);
+    } else {
+      DBuf<double> Sd, chunk;
+      Sd.alloc(S.size(), st);
+      APL_CUDA(cudaMemcpyAsync(Sd.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      APL_CUDA(cudaEventRecord(e0, st));
+      DenseWorkScope dws(&h->dw);
+      operator_sketch(st, h->A, h->s, Sd.p, h->Y.p, chunk);
+      APL_CUDA(cudaEventRecord(e1, st));
+      APL_CUDA(cudaEventSynchronize(e1));
+    }
+  }
   APL_CUDA(cudaEventRecord(e1, st));
   APL_CUDA(cudaEventSynchronize(e1));
   APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));

@@ -1,7 +1,9 @@
 // Sketch and CUR-refinement kernels.
+#include <algorithm>
 #include <climits>
 
 #include "cur.cuh"
+#include "dense.cuh"
 #include "df32.cuh"
 
 namespace apl {
@@ -850,6 +852,78 @@ void fill_int(cudaStream_t st, int* p, int64_t n, int v) {
   if (n <= 0) return;
   fill_int_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(p, n, v);
   APL_LAUNCH_CHECK();
+}
+
+}  // namespace apl
+
+// ---- dense sketching operators (Gaussian, SRHT) with FP64-level products -------------
+
+namespace apl {
+namespace {
+
+template <typename T>
+__global__ void widen_rows_kernel(int64_t rows, int64_t n, int64_t ld, const T* __restrict__ A,
+                                  double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * n) return;
+  const int64_t i = e / n, j = e - i * n;
+  out[e] = (double)A[i * ld + j];
+}
+
+// Y(:, j) = sum over the nonzeros a_ij of column j, in ascending i, of a_ij S(:, i); one
+// warp per column, lanes over the sketch rows.
+template <typename T>
+__global__ void opsketch_csc_kernel(int s, int64_t n, const int* __restrict__ colptr,
+                                    const int* __restrict__ rowidx, const T* __restrict__ cvals,
+                                    const double* __restrict__ S, double* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n) return;
+  const int e0 = colptr[j], e1 = colptr[j + 1];
+  for (int r0 = 0; r0 < s; r0 += 32) {
+    const int r = r0 + lane;
+    double acc = 0.0;
+    if (r < s)
+      for (int e = e0; e < e1; ++e) acc = fma((double)cvals[e], S[r + (int64_t)s * rowidx[e]], acc);
+    if (r < s) Y[r + (int64_t)s * j] = acc;
+  }
+}
+
+}  // namespace
+
+void operator_sketch(cudaStream_t st, const MatView& A, int s, const double* S, double* Y,
+                     DBuf<double>& chunk) {
+  if (A.fmt == 1) {
+    const unsigned blocks = (unsigned)cdiv(A.n * 32, 256);
+    if (A.dtype == 0)
+      opsketch_csc_kernel<double><<<blocks, 256, 0, st>>>(s, A.n, A.colptr, A.rowidx,
+                                                          (const double*)A.cvals, S, Y);
+    else
+      opsketch_csc_kernel<float><<<blocks, 256, 0, st>>>(s, A.n, A.colptr, A.rowidx,
+                                                         (const float*)A.cvals, S, Y);
+    APL_LAUNCH_CHECK();
+    return;
+  }
+  // dense: Y = sum over row chunks of S(:, chunk) A(chunk, :), the chunk viewed column-major
+  // as its n x rows transpose
+  const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(A.m, (int64_t)(1 << 25) / A.n));
+  for (int64_t i0 = 0; i0 < A.m; i0 += rows) {
+    const int64_t mc = std::min(rows, A.m - i0);
+    const double* blk;
+    int64_t ldb;
+    if (A.dtype == 0) {
+      blk = (const double*)A.vals + i0 * A.ld;
+      ldb = A.ld;
+    } else {
+      chunk.alloc((size_t)rows * A.n, st);
+      widen_rows_kernel<float><<<(unsigned)cdiv(mc * A.n, 256), 256, 0, st>>>(
+          mc, A.n, A.ld, (const float*)A.vals + i0 * A.ld, chunk.p);
+      APL_LAUNCH_CHECK();
+      blk = chunk.p;
+      ldb = A.n;
+    }
+    dgemm(st, 0, 1, s, A.n, mc, 1.0, S + (int64_t)s * i0, s, blk, ldb, i0 == 0 ? 0.0 : 1.0, Y, s);
+  }
 }
 
 }  // namespace apl

@@ -27,6 +27,13 @@ void sketch(cudaStream_t st, const MatView& A, int s, int xi, const int* tptr, c
             const signed char* tsgn, const int* srows, const signed char* ssign, double scale,
             double* Y);
 
+// Y = S A (s x n column-major FP64) for a dense sketching operator S (s x m column-major
+// FP64, device): CSR A by its CSC copy (FP64 products in ascending row order), dense A by
+// row chunks through dgemm (the dense routines' products: compensated FP32 by default).
+// Needs the calling context's dense workspace installed.
+void operator_sketch(cudaStream_t st, const MatView& A, int s, const double* S, double* Y,
+                     DBuf<double>& chunk);
+
 // Partial-pivoting selection on X (N x K) in place: X(i, c) = X[i * rs + c * cs].
 // Performs k elimination steps; piv_host receives the pivot rows (original indices),
 // the return value is the number of nonzero pivots taken, *margin the smallest

@@ -115,3 +115,15 @@ def test_oracle_replay_strata_follow_the_schedule():
     ph = [sc for nm, _, sc in rep.strata if nm.startswith("phase")]
     iters = gold["bench_tol"]["phases"]
     assert ph == pytest.approx([(k + 2) / (rep.SAMPLE_ITERS + 2) for k in iters[:len(ph)]])
+
+
+def test_bench_package_names_exist():
+    """Every package attribute bench.py uses is exported (a missing name would only show
+    on the GPU machine)."""
+    import inspect
+    import re
+
+    import bench
+    import paper_2604_05065_gb300 as pkg
+    names = set(re.findall(r"pkg\.([A-Za-z_][A-Za-z_0-9]*)", inspect.getsource(bench)))
+    assert names and all(hasattr(pkg, n) for n in names), [n for n in names if not hasattr(pkg, n)]

@@ -740,6 +740,26 @@ def test_bf16_rounding_matches_torch():
     assert orng.round_bf16([1.0 + 3 * 2.0 ** -8])[0] == 1.0 + 2 ** -6  # tie to even, up
 
 
+def test_bf16_expansion():
+    """Three bfloat16 terms hold an FP32 value exactly; each term is a bfloat16 number at
+    most 2^-8 of the one before (rounding to nearest leaves half an ulp of 8 bits); two
+    terms leave at most 2^-16 relative."""
+    g = np.random.default_rng(11)
+    x = g.standard_normal(20000) * 10.0 ** g.integers(-30, 30, 20000)
+    f = x.astype(np.float32).astype(np.float64)
+    p = orng.bf16_pieces(x, 3)
+    assert np.array_equal(p[0] + p[1] + p[2], f)
+    for q in p:
+        assert np.array_equal(orng.round_bf16(q), q)
+    assert np.all(np.abs(p[1]) <= 2.0 ** -8 * np.abs(p[0]))
+    assert np.all(np.abs(p[2]) <= 2.0 ** -8 * np.abs(p[1]))
+    assert np.all(np.abs(f - p[0] - p[1]) <= 2.0 ** -16 * np.abs(f))
+    assert np.array_equal(orng.bf16_pieces(x, 1)[0], orng.round_bf16(x))
+    # a value that needs all three terms: 1 + 2^-9 + 2^-20
+    v = orng.bf16_pieces([1.0 + 2.0 ** -9 + 2.0 ** -20], 3)
+    assert [float(q[0]) for q in v] == [1.0, 2.0 ** -9, 2.0 ** -20]
+
+
 @pytest.mark.parametrize("kind", ["gaussian", "srht"])
 def test_aplicur_with_dense_sketch_reaches_ridge_solution(kind):
     p = wl.small_dense(400, 50, 4646, decay=3.0, mu=1e-4, sketch_dim=5)
