@@ -845,8 +845,7 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
     else draw_srht_sketch(h->opt.seed, h->s, h->m, S);
     if (h->opt.sketch_tc) {
       tc_sketch_upload(st, S.data(), h->s, h->m, h->n, h->tcw);
-      APL_CUDA(cudaEventRecord(e0, st));
-      tc_sketch_apply(st, h->A, h->tcw, h->Y.p, h->opt.sketch_tc);
+      tc_sketch_apply(st, h->A, h->tcw, h->Y.p, h->opt.sketch_tc, e0, e1);
     } else {
       DBuf<double> Sd, chunk;
       Sd.alloc(S.size(), st);
@@ -858,7 +857,8 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
       APL_CUDA(cudaEventSynchronize(e1));
     }
   }
-  APL_CUDA(cudaEventRecord(e1, st));
+  if (!(h->opt.sketch_kind != APLICUR_SKETCH_SPARSE_SIGN && h->opt.sketch_tc))
+    APL_CUDA(cudaEventRecord(e1, st));
   APL_CUDA(cudaEventSynchronize(e1));
   APL_CUDA(cudaEventElapsedTime(&h->setup_ms, e0, e1));
   cudaEventDestroy(e0);

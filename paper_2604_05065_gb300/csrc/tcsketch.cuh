@@ -28,7 +28,9 @@ void tc_sketch_upload(cudaStream_t st, const double* S_host, int s, int64_t m, i
 // Y (s x n column-major FP64, device) = S~ A~ for a dense row-major A (FP32 or FP64
 // values, FP64 rounded to FP32 first): S~ the bfloat16 S, A~ the sum of the first `terms`
 // (1 to 3) terms of the bfloat16 expansion of A, FP32 accumulation.  Throws ST_ETIMEOUT
-// when a bounded wait gave up (the work buffers are then undefined).
-void tc_sketch_apply(cudaStream_t st, const MatView& A, TcSketchWork& w, double* Y, int terms);
+// when a bounded wait gave up (the work buffers are then undefined).  e0 / e1, when given,
+// are recorded on st just before the product's first kernel and after its last.
+void tc_sketch_apply(cudaStream_t st, const MatView& A, TcSketchWork& w, double* Y, int terms,
+                     cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 
 }  // namespace apl
