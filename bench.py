@@ -307,9 +307,9 @@ def legs_measure(args, dev):
     """Time-to-1e-8 of the other configurations, APLICUR beside plain (unpreconditioned)
     GPU LSQR with the same kernels, one warm-up and one timed solve each:
       dense FP64 2000 x 200 (mu 1e-4, sketch 20): APLICUR and plain, FP64;
-      sparse CSR 200000 x 20000 (mu 1e-6, sketch 100): plain only, FP64 and FP32 products
-        (APLICUR's CUR rank must reach about 0.7 n there before rho <= eps_cur: thousands
-        of columns of dense FP64 factorisations per build, not run here);
+      sparse CSR 200000 x 20000 (mu 1e-6, sketch 100): APLICUR with the SVD-free
+        preconditioner on a CUR of [A; sqrt(mu) I] (one solve), plain LSQR in FP64 and
+        FP32 products;
       adjoint FP32 100000 x 2000 (mu 1e-4, sketch 100): forward and backward of
         0.5 ||x - x_target||^2, APLICUR and plain, compensated FP32 products."""
     import numpy as np
@@ -353,8 +353,20 @@ def legs_measure(args, dev):
                                 torch.from_numpy(p.indices.astype(np.int64)),
                                 torch.from_numpy(p.data), size=(p.m, p.n)).to(dev)
     b = torch.from_numpy(p.b).to(dev)
-    leg = {"aplicur": {"not_run": "CUR rank near 0.7 n = 14000 before rho <= eps_cur = 30 "
-                                  "sqrt(mu): minutes of dense FP64 factorisations per build"}}
+    leg = {}
+    # APLICUR with the SVD-free preconditioner on a CUR of A_mu (one solve: the CUR rank
+    # grows to about n, tens of seconds of dense factor products)
+    s = pkg.Solver(A, b, p.mu, p.sketch_dim, precision=pkg.PREC_FP64, seed=1, variant=1)
+    secs, _ = _timed(stream, lambda s=s: s.solve(TOL, args.maxit))
+    st = s.stats()
+    s.close()
+    leg["aplicur_svdfree_fp64"] = {
+        "time_to_tol_s": round(secs, 3), "iters": st["iters"], "ne_res": st["ne_res"],
+        "converged": bool(st["converged"]), "ell": st["ell"], "nsteps": st["nsteps"],
+        "ms_rank": round(st["time_rank_ms"]), "ms_build": round(st["time_build_ms"]),
+        "ms_lsqr": round(st["time_lsqr_ms"]),
+        "note": "variant 1 with mu > 0: CUR of [A; sqrt(mu) I]; one solve, no warm-up"}
+    torch.cuda.empty_cache()
     for pname, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
         for rep in range(2):
             s = pkg.Solver(A, b, p.mu, p.sketch_dim, precision=prec, seed=1)
@@ -363,6 +375,8 @@ def legs_measure(args, dev):
             s.close()
         leg[f"plain_{pname}"] = {"time_to_tol_s": round(secs, 4), "iters": st["iters"],
                                  "ne_res": st["ne_res"], "converged": bool(st["converged"])}
+    leg["aplicur_over_plain_time"] = round(leg["aplicur_svdfree_fp64"]["time_to_tol_s"]
+                                           / leg["plain_fp64"]["time_to_tol_s"], 2)
     legs[p.name] = leg
     del A, b
     A, b, xt, mu, sd = wl.config5_device(dev)

@@ -123,8 +123,13 @@ typedef struct {
   int32_t fp64_dense;
   /* APLICUR_VARIANT_SVD (0, default): the SVD-based preconditioner (Algorithm
    * CURPreconditioner).  APLICUR_VARIANT_SVDFREE (1): the SVD-free preconditioner of the
-   * paper's "SVD-free variant" (Eq. preconditioner_svdfree), defined there for unregularised
-   * problems: requires mu = 0.  Its inverse sighat Q_R M^{-1} Q_R^T + (I - Q_R Q_R^T) uses
+   * paper's "SVD-free variant" (Eq. preconditioner_svdfree).  With mu = 0 the CUR is of A;
+   * with mu > 0 it is of the regularised matrix A_mu = [A; sqrt(mu) I] ((m + n) x n, the
+   * appended rows stored with sqrt(mu) rounded to A's value type), as the paper prescribes
+   * for regularised problems: the sketch then has m + n columns (user-supplied sketch
+   * draws hold (m + n) xi entries), row indices >= m (aplicur_get_indices) name the row
+   * m + j of A_mu, sqrt(mu) e_j^T, and C, R and the cross are those of A_mu.  Its inverse
+   * sighat Q_R M^{-1} Q_R^T + (I - Q_R Q_R^T) uses
    * M^{-1} = T_R^{-T} A(I,J) T_C^{-1}, formed once per build by two triangular solves.  The
    * target level sighat is sigma_min(M) = 1 / ||M^{-1}||_2 from 50 power-iteration steps
    * on M^{-T} M^{-1} (the smallest CUR singular value, which the SVD-based form uses; the

@@ -69,6 +69,17 @@ def rmatvec(A, y):
     return np.asarray(A.T @ y, dtype=np.float64)
 
 
+def regularized_matrix(A, delta: float):
+    """A_mu = [A; delta I] ((m + n) x n): the matrix whose CUR the SVD-free variant takes
+    for regularised problems (section "SVD-free variant", last paragraph).  Row m + j is
+    delta e_j^T."""
+    n = A.shape[1]
+    if _is_sparse(A):
+        return sp.vstack([A.tocsr().astype(np.float64), delta * sp.identity(n, format="csr")],
+                         format="csr")
+    return np.vstack([np.asarray(A, dtype=np.float64), delta * np.eye(n)])
+
+
 # --------------------------------------------------------------------------------------
 # Sketch (Definition "sparse sign embedding", Section 5.1; Algorithm APLICUR lines 3-4)
 # --------------------------------------------------------------------------------------
@@ -285,6 +296,10 @@ class Preconditioner:
         """P^{-1} w = sighat Vhat Lam^{-1} Vhat^T w + (I - Vhat Vhat^T) w."""
         return w + self.Vhat @ (self.coef * (self.Vhat.T @ w))
 
+    def apply_inv_T(self, w):
+        """P^{-T} w = P^{-1} w (P is symmetric)."""
+        return self.apply_inv(w)
+
     def apply(self, w):
         """P w = sighat^{-1} Vhat Lam Vhat^T w + (I - Vhat Vhat^T) w."""
         return w + self.Vhat @ ((self.Lam / self.sighat - 1.0) * (self.Vhat.T @ w))
@@ -305,10 +320,11 @@ def chol_upper(G: np.ndarray) -> np.ndarray:
 
 
 def build_preconditioner(C: np.ndarray, core: Core, Q_R: np.ndarray, T_R: np.ndarray,
-                         delta: float) -> Preconditioner:
-    """Algorithm CURPreconditioner: T_C = chol(C^T C); M = T_C U T_R^T; SVD of M;
-    Vhat = Q_R V_M; Lam = sqrt(sig^2 + delta^2); sighat = sqrt(sig_ell^2 + delta^2)."""
-    T_C = chol_upper(C.T @ C)
+                         delta: float, T_C: np.ndarray | None = None) -> Preconditioner:
+    """Algorithm CURPreconditioner: T_C = chol(C^T C) (or the given factor); M = T_C U T_R^T;
+    SVD of M; Vhat = Q_R V_M; Lam = sqrt(sig^2 + delta^2); sighat = sqrt(sig_ell^2 + delta^2)."""
+    if T_C is None:
+        T_C = chol_upper(C.T @ C)
     M = T_C @ core.solve(T_R.T)
     _, sig, VMt = np.linalg.svd(M)
     Vhat = Q_R @ VMt.T
@@ -363,6 +379,16 @@ class SvdFreePreconditioner:
         t = self.Q_R.T @ w
         return w + self.Q_R @ (self.sighat * self.minv_T(t) - t)
 
+    @property
+    def norm(self) -> float:
+        """Taken as 1 in the explicit-residual trigger (||Ptilde||_2 is not formed)."""
+        return 1.0
+
+    @property
+    def sig_ell(self) -> float:
+        """The dynamic stop's smallest CUR singular value: the target level."""
+        return self.sighat
+
     def apply(self, w):
         """Ptilde w = sighat^{-1} Q_R M Q_R^T w + (I - Q_R Q_R^T) w, M = T_C A(I,J)^{-1} T_R^T."""
         t = self.Q_R.T @ w
@@ -371,12 +397,13 @@ class SvdFreePreconditioner:
 
 
 def build_svdfree_preconditioner(C: np.ndarray, A_IJ: np.ndarray, Q_R: np.ndarray,
-                                 T_R: np.ndarray, sighat: float) -> SvdFreePreconditioner:
-    """Algorithm SVD-free CURPreconditioner: T_C = chol(C^T C); the operator is kept as
-    its factors (Q_R, T_R, T_C, A(I,J)) and the target level sighat (the estimate rho of
-    Eq. 2normestimate)."""
-    return SvdFreePreconditioner(Q_R, T_R, chol_upper(C.T @ C), np.array(A_IJ, copy=True),
-                                 float(sighat))
+                                 T_R: np.ndarray, sighat: float,
+                                 T_C: np.ndarray | None = None) -> SvdFreePreconditioner:
+    """Algorithm SVD-free CURPreconditioner: T_C = chol(C^T C) (or the given factor); the
+    operator is kept as its factors (Q_R, T_R, T_C, A(I,J)) and the target level sighat
+    (the estimate rho of Eq. 2normestimate)."""
+    return SvdFreePreconditioner(Q_R, T_R, chol_upper(C.T @ C) if T_C is None else T_C,
+                                 np.array(A_IJ, copy=True), float(sighat))
 
 
 def svdfree_smallest_sigma(P: SvdFreePreconditioner, iters: int = 50, seed: int = 1) -> float:
@@ -448,7 +475,8 @@ def plsqr_phase(A, b, delta, x0, P: Preconditioner, *, eps_lsqr=1e-10, nu=math.i
         return PhaseResult(x, 0, "exact", [0.0])
     u_top /= beta
     u_bot /= beta
-    v = P.apply_inv(rmatvec(A, u_top) + delta * u_bot)
+    # Abar^T u = P^{-T} (A^T u_top + delta u_bot); Abar z = [A; delta I] P^{-1} z
+    v = P.apply_inv_T(rmatvec(A, u_top) + delta * u_bot)
     alpha = math.sqrt(float(v @ v))
     if alpha == 0.0:
         return PhaseResult(x, 0, "exact", [beta])
@@ -474,7 +502,7 @@ def plsqr_phase(A, b, delta, x0, P: Preconditioner, *, eps_lsqr=1e-10, nu=math.i
             u_top /= beta
             u_bot /= beta
         anorm2 += alpha * alpha + beta * beta
-        v = P.apply_inv(rmatvec(A, u_top) + delta * u_bot) - beta * v
+        v = P.apply_inv_T(rmatvec(A, u_top) + delta * u_bot) - beta * v
         alpha = math.sqrt(float(v @ v))
         if alpha > 0.0:
             v /= alpha
@@ -539,6 +567,13 @@ class Options:
     # is the fixed-rank single-shot variant (Algorithm "Sketched CUR with cross
     # approximation using LUPP", on the driver's sketch)
     max_rank: int = 0
+    # "svd": Algorithm CURPreconditioner; "svdfree": the SVD-free preconditioner (Eq.
+    # preconditioner_svdfree) with the target level sigma_min(M); for mu > 0 of a CUR of
+    # A_mu = [A; delta I] (section "SVD-free variant", last paragraph)
+    variant: str = "svd"
+    # the delta stored in A_mu's appended rows (default sqrt(mu); an implementation that
+    # keeps A_mu in FP32 stores sqrt(mu) rounded to FP32)
+    cur_delta: float | None = None
 
 
 class RebuildRule:
@@ -574,6 +609,7 @@ class Result:
     phases: list              # per phase: dict(ell, iters, reason, ne_res)
     Y: np.ndarray
     last_P: Preconditioner | None
+    rank_breakdown: bool = False  # a rank step's new columns made C^T C singular
 
 
 def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-10,
@@ -590,8 +626,14 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
     eps_cur = opts.eps_cur_factor * delta
     s = sketch_rows(bsize)
     xi = sketch_xi(s, opts.xi)
+    # the matrix of the CUR: A, or A_mu for the SVD-free variant of a regularised problem
+    svdfree = opts.variant == "svdfree"
+    CA = A
+    if svdfree and mu > 0.0:
+        CA = regularized_matrix(A, delta if opts.cur_delta is None else opts.cur_delta)
+    cm = CA.shape[0]
     if srows is None:
-        srows, signs = orng.sparse_sign(opts.seed, s, m, xi)
+        srows, signs = orng.sparse_sign(opts.seed, s, cm, xi)
     if W is None:
         W = orng.gaussian_w(opts.seed, n, opts.normest_r)
     norm_Atb = float(np.linalg.norm(rmatvec(A, b)))
@@ -600,7 +642,7 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
                       [], [], np.zeros((s, n)), None)
 
     # S: a dense sketching operator (s x m) in place of the sparse sign embedding
-    Y = apply_sketch(A, srows, signs, s) if S is None else dense_sketch(A, S)
+    Y = apply_sketch(CA, srows, signs, s) if S is None else dense_sketch(CA, S)
     I = np.zeros(0, np.int64)
     J = np.zeros(0, np.int64)
     core = None
@@ -631,24 +673,36 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
         return ne
 
     def done(ne):
-        return Result(x, I, J, ne <= tol, total, ne, steps, phases, Y, P)
+        return Result(x, I, J, ne <= tol, total, ne, steps, phases, Y, P, rank_breakdown)
 
-    kmax = min(m, n) if opts.max_rank <= 0 else min(m, n, opts.max_rank)
+    kmax = min(cm, n) if opts.max_rank <= 0 else min(cm, n, opts.max_rank)
+    rank_breakdown = False
+    Cn, T_C = cols(CA, J), None  # C = A(:, J) and its Cholesky factor at the current rank
     while True:
         # Part 1: update CUR
         kb = min(bsize, kmax - len(J))
-        Ip, Jp, margin = augment_cur(A, I, J, E_row, core, kb)
+        Ip, Jp, margin = augment_cur(CA, I, J, E_row, core, kb)
+        if Ip.size:
+            # new columns numerically dependent on the chosen ones (C^T C not positive
+            # definite): rank growth ends at the current rank and the solve goes on with
+            # the last preconditioner built
+            Cn = cols(CA, np.concatenate([J, Jp]))
+            try:
+                T_C = chol_upper(Cn.T @ Cn)
+            except np.linalg.LinAlgError:
+                rank_breakdown = True
+                break
         exhausted = Ip.size < kb
         I = np.concatenate([I, Ip])
         J = np.concatenate([J, Jp])
-        core = Core(A, I, J)
-        E_row = sketched_residual(A, Y, I, J, core)
+        core = Core(CA, I, J)
+        E_row = sketched_residual(CA, Y, I, J, core)
         rho = norm_estimate(E_row, W)
         rho_eff = 0.0 if exhausted else rho
         last = rho_eff <= eps_cur or len(I) >= kmax or exhausted
         # Part 2: update factorisations of R^T
         if Ip.size:
-            Q_R, T_R = augment_qr(Q_R, T_R, rows(A, Ip).T)
+            Q_R, T_R = augment_qr(Q_R, T_R, rows(CA, Ip).T)
         # Part 3: re-precondition and run LSQR
         if rb_list is not None:
             rebuild = bool(rb_list.pop(0)) if rb_list else last
@@ -656,8 +710,12 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
             rebuild = last or (not opts.single_shot and rule.wants_rebuild(rho_eff))
         steps.append(dict(ell=len(I), rho=rho, rebuild=rebuild, margin=margin))
         if rebuild:
-            C = cols(A, J)
-            P = build_preconditioner(C, core, Q_R, T_R, delta)
+            C = Cn  # A(:, J) of this step, T_C its Cholesky factor
+            if svdfree:
+                P = build_svdfree_preconditioner(C, cross(CA, I, J), Q_R, T_R, 1.0, T_C)
+                P.sighat = svdfree_smallest_sigma(P)
+            else:
+                P = build_preconditioner(C, core, Q_R, T_R, delta, T_C)
             nu = math.inf if last else opts.nu_lsqr
             ne = run_phase(P, nu, last)
             if not replay and ne <= tol:
@@ -668,6 +726,8 @@ def aplicur(A, b, mu: float, bsize: int, opts: Options | None = None, *, tol=1e-
         if total >= maxit:
             return done(ne_residual(A, b, mu, x, norm_Atb))
     # final phase ended without reaching tol: warm-restart it with the same P
+    if P is None:
+        P = identity_preconditioner(n)
     ne = phases[-1]["ne_res"] if phases else ne_residual(A, b, mu, x, norm_Atb)
     extra = 0
     while (replay and ph_list) or (not replay and ne > tol and total < maxit
@@ -711,6 +771,25 @@ def ridge_direct(A, b, mu: float) -> np.ndarray:
     rhs = np.concatenate([np.asarray(b, dtype=np.float64), np.zeros(n)])
     Q, R = np.linalg.qr(Aug, mode="reduced")
     return sla.solve_triangular(R, Q.T @ rhs, lower=False)
+
+
+def ridge_sparse(A, b, mu: float, rtol: float = 1e-15):
+    """The ridge solution (A^T A + mu I) x = A^T b of a sparse A by conjugate gradients on
+    the normal equations with the Jacobi preconditioner diag(A^T A) + mu (scipy's cg),
+    run until the normal-equation residual is rtol of ||A^T b||.  Returns (x, relative
+    normal-equation residual); the relative error of x is at most that residual times
+    cond(A^T A + mu I)."""
+    import scipy.sparse.linalg as spla
+    A = sp.csr_matrix(A, dtype=np.float64)
+    n = A.shape[1]
+    b = np.asarray(b, dtype=np.float64)
+    d = np.asarray(A.multiply(A).sum(axis=0)).ravel() + mu
+    op = spla.LinearOperator((n, n), matvec=lambda v: A.T @ (A @ v) + mu * v, dtype=np.float64)
+    M = spla.LinearOperator((n, n), matvec=lambda v: v / d, dtype=np.float64)
+    rhs = A.T @ b
+    x, _ = spla.cg(op, rhs, M=M, rtol=rtol, atol=0.0, maxiter=100000)
+    res = float(np.linalg.norm(A.T @ (b - A @ x) - mu * x) / np.linalg.norm(rhs))
+    return np.asarray(x, dtype=np.float64), res
 
 
 def ridge_gradients(A, b, mu: float, x: np.ndarray, g: np.ndarray):

@@ -158,6 +158,13 @@ struct aplicur_ctx {
   DBuf<int> colptr, rowidx;
   DBuf<double> cv64;
   DBuf<float> cv32;
+  // The matrix the CUR is taken of: A itself, or A_mu = [A; delta I] ((m + n) x n, values
+  // in A's type) for the SVD-free variant with mu > 0.  cm is its row count.
+  MatView CA;
+  int64_t cm = 0;
+  DBuf<int> ca_rowptr, ca_colidx, ca_colptr, ca_rowidx;
+  DBuf<double> ca_v64, ca_cv64;
+  DBuf<float> ca_v32, ca_cv32;
   const double* b = nullptr;
   double mu = 0, delta = 0, eps_cur = 0;
   int bsize = 0, s = 0, xi = 0, r = 0;
@@ -231,8 +238,8 @@ void ctx_grow(aplicur_ctx* h, int need) {
   regrow_cols(h->QR, h->n);
   // the preconditioner reads the leading columns of Q_R in place
   if (h->P.Q == oldQ) h->P.Q = h->QR.p;
-  if (h->A.fmt == 0) {
-    regrow_cols(h->Cbuf, h->m);
+  if (h->CA.fmt == 0) {
+    regrow_cols(h->Cbuf, h->cm);
     DBuf<double> nb;
     nb.alloc((size_t)nc * h->n, st);
     if (oc > 0 && h->Rbuf.p) dcopy2d(st, oc, h->n, h->Rbuf.p, oc, nb.p, nc, false);
@@ -249,17 +256,18 @@ void ctx_grow(aplicur_ctx* h, int need) {
   APL_CUDA(cudaStreamSynchronize(st));
 }
 
-void build_csc(aplicur_ctx* h) {
-  const int64_t m = h->m, n = h->n, nnz = h->A.nnz;
-  cudaStream_t st = h->st;
+// CSC copy (colptr, rowidx, values) of the CSR matrix V (m rows), attached to V.
+void build_csc(cudaStream_t st, MatView& V, int64_t m, DBuf<int>& colptr_b, DBuf<int>& rowidx_b,
+               DBuf<double>& cv64_b, DBuf<float>& cv32_b) {
+  const int64_t n = V.n, nnz = V.nnz;
   std::vector<int> rp(m + 1), ci(nnz);
-  APL_CUDA(cudaMemcpyAsync(rp.data(), h->A.rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  APL_CUDA(cudaMemcpyAsync(rp.data(), V.rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   if (nnz)
-    APL_CUDA(cudaMemcpyAsync(ci.data(), h->A.colidx, nnz * sizeof(int), cudaMemcpyDeviceToHost, st));
-  const size_t vs = h->A.dtype == 0 ? 8 : 4;
+    APL_CUDA(cudaMemcpyAsync(ci.data(), V.colidx, nnz * sizeof(int), cudaMemcpyDeviceToHost, st));
+  const size_t vs = V.dtype == 0 ? 8 : 4;
   std::vector<char> vals(nnz * vs), cvals(nnz * vs);
   if (nnz)
-    APL_CUDA(cudaMemcpyAsync(vals.data(), h->A.vals, nnz * vs, cudaMemcpyDeviceToHost, st));
+    APL_CUDA(cudaMemcpyAsync(vals.data(), V.vals, nnz * vs, cudaMemcpyDeviceToHost, st));
   APL_CUDA(cudaStreamSynchronize(st));
   APL_REQUIRE(rp[0] == 0 && rp[m] == nnz, "CSR rowptr inconsistent with nnz");
   std::vector<int> cp(n + 1, 0), ri(nnz);
@@ -277,27 +285,97 @@ void build_csc(aplicur_ctx* h) {
       std::memcpy(&cvals[p * vs], &vals[e * vs], vs);
     }
   }
-  h->colptr.alloc(n + 1, st);
-  h->rowidx.alloc(std::max<int64_t>(nnz, 1), st);
-  APL_CUDA(cudaMemcpyAsync(h->colptr.p, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  colptr_b.alloc(n + 1, st);
+  rowidx_b.alloc(std::max<int64_t>(nnz, 1), st);
+  APL_CUDA(cudaMemcpyAsync(colptr_b.p, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   if (nnz)
-    APL_CUDA(cudaMemcpyAsync(h->rowidx.p, ri.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
-  if (h->A.dtype == 0) {
-    h->cv64.alloc(std::max<int64_t>(nnz, 1), st);
-    if (nnz) APL_CUDA(cudaMemcpyAsync(h->cv64.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
-    h->A.cvals = h->cv64.p;
+    APL_CUDA(cudaMemcpyAsync(rowidx_b.p, ri.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (V.dtype == 0) {
+    cv64_b.alloc(std::max<int64_t>(nnz, 1), st);
+    if (nnz) APL_CUDA(cudaMemcpyAsync(cv64_b.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
+    V.cvals = cv64_b.p;
   } else {
-    h->cv32.alloc(std::max<int64_t>(nnz, 1), st);
-    if (nnz) APL_CUDA(cudaMemcpyAsync(h->cv32.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
-    h->A.cvals = h->cv32.p;
+    cv32_b.alloc(std::max<int64_t>(nnz, 1), st);
+    if (nnz) APL_CUDA(cudaMemcpyAsync(cv32_b.p, cvals.data(), nnz * vs, cudaMemcpyHostToDevice, st));
+    V.cvals = cv32_b.p;
   }
-  h->A.colptr = h->colptr.p;
-  h->A.rowidx = h->rowidx.p;
+  V.colptr = colptr_b.p;
+  V.rowidx = rowidx_b.p;
   APL_CUDA(cudaStreamSynchronize(st));
 }
 
+void build_csc(aplicur_ctx* h) {
+  build_csc(h->st, h->A, h->m, h->colptr, h->rowidx, h->cv64, h->cv32);
+}
+
+template <typename T>
+__global__ void amu_diag_kernel(int64_t m, int64_t n, T delta, T* V) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) V[(m + j) * n + j] = delta;
+}
+
+// A_mu = [A; delta I] ((m + n) x n, delta rounded to A's value type) as the CUR matrix:
+// dense row-major with ld n, or CSR with one entry delta in each appended row (and its CSC).
+void build_amu(aplicur_ctx* h) {
+  cudaStream_t st = h->st;
+  const int64_t m = h->m, n = h->n;
+  const MatView& A = h->A;
+  MatView V = A;
+  V.m = m + n;
+  V.colptr = nullptr; V.rowidx = nullptr; V.cvals = nullptr;
+  const size_t es = A.dtype == 0 ? 8 : 4;
+  if (A.fmt == 0) {
+    void* buf;
+    if (A.dtype == 0) { h->ca_v64.alloc((size_t)(m + n) * n, st); buf = h->ca_v64.p; }
+    else { h->ca_v32.alloc((size_t)(m + n) * n, st); buf = h->ca_v32.p; }
+    APL_CUDA(cudaMemcpy2DAsync(buf, n * es, A.vals, A.ld * es, n * es, m, cudaMemcpyDeviceToDevice, st));
+    APL_CUDA(cudaMemsetAsync((char*)buf + (size_t)m * n * es, 0, (size_t)n * n * es, st));
+    const unsigned g = (unsigned)cdiv(n, 256);
+    if (A.dtype == 0) amu_diag_kernel<double><<<g, 256, 0, st>>>(m, n, h->delta, (double*)buf);
+    else amu_diag_kernel<float><<<g, 256, 0, st>>>(m, n, (float)h->delta, (float*)buf);
+    APL_LAUNCH_CHECK();
+    V.ld = n;
+    V.nnz = (m + n) * n;
+    V.vals = buf;
+  } else {
+    const int64_t nnz = A.nnz;
+    APL_REQUIRE(nnz + n < (1LL << 31), "A_mu: nnz + n exceeds int32 indexing");
+    std::vector<int> rp(m + n + 1), ci(nnz + n);
+    std::vector<char> vals((nnz + n) * es);
+    APL_CUDA(cudaMemcpyAsync(rp.data(), A.rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (nnz) {
+      APL_CUDA(cudaMemcpyAsync(ci.data(), A.colidx, nnz * sizeof(int), cudaMemcpyDeviceToHost, st));
+      APL_CUDA(cudaMemcpyAsync(vals.data(), A.vals, nnz * es, cudaMemcpyDeviceToHost, st));
+    }
+    APL_CUDA(cudaStreamSynchronize(st));
+    const double d64 = h->delta;
+    const float d32 = (float)h->delta;
+    for (int64_t j = 0; j < n; ++j) {
+      rp[m + j + 1] = (int)(nnz + j + 1);
+      ci[nnz + j] = (int)j;
+      std::memcpy(&vals[(nnz + j) * es], A.dtype == 0 ? (const void*)&d64 : (const void*)&d32, es);
+    }
+    h->ca_rowptr.alloc(m + n + 1, st);
+    h->ca_colidx.alloc(nnz + n, st);
+    APL_CUDA(cudaMemcpyAsync(h->ca_rowptr.p, rp.data(), (m + n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    APL_CUDA(cudaMemcpyAsync(h->ca_colidx.p, ci.data(), (nnz + n) * sizeof(int), cudaMemcpyHostToDevice, st));
+    void* vb;
+    if (A.dtype == 0) { h->ca_v64.alloc(nnz + n, st); vb = h->ca_v64.p; }
+    else { h->ca_v32.alloc(nnz + n, st); vb = h->ca_v32.p; }
+    APL_CUDA(cudaMemcpyAsync(vb, vals.data(), (nnz + n) * es, cudaMemcpyHostToDevice, st));
+    V.rowptr = h->ca_rowptr.p;
+    V.colidx = h->ca_colidx.p;
+    V.vals = vb;
+    V.nnz = nnz + n;
+    build_csc(st, V, m + n, h->ca_colptr, h->ca_rowidx, h->ca_cv64, h->ca_cv32);
+  }
+  APL_CUDA(cudaStreamSynchronize(st));
+  h->CA = V;
+  h->cm = m + n;
+}
+
 void upload_sketch(aplicur_ctx* h, const std::vector<int>& rows, const std::vector<int8_t>& sg) {
-  const int64_t m = h->m;
+  const int64_t m = h->cm;
   const int xi = h->xi, s = h->s;
   cudaStream_t st = h->st;
   for (size_t e = 0; e < rows.size(); ++e)
@@ -335,7 +413,7 @@ void reset_cur(aplicur_ctx* h) {
   h->J.clear();
   fill_int(st, h->colpos.p, h->n, -1);
   fill_int(st, h->colpos_plus.p, h->n, -1);
-  fill_int(st, h->rowpos.p, h->m, -1);
+  fill_int(st, h->rowpos.p, h->cm, -1);
   APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)h->s * h->n * sizeof(double),
                            cudaMemcpyDeviceToDevice, st));
   if (h->LU.p) h->LU.zero(st);
@@ -351,7 +429,7 @@ void reset_cur(aplicur_ctx* h) {
 int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) {
   DenseWorkScope dws(&h->dw);
   cudaStream_t st = h->st;
-  const int64_t m = h->m, n = h->n;
+  const int64_t m = h->cm, n = h->n;
   const int s = h->s;
   const int ell = h->ell;
   const int kj = (int)std::min<int64_t>(h->bsize, h->kmax - ell);
@@ -371,19 +449,19 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     set_map(st, h->colpos_plus.p, h->Jp_d.p, nzJ, 0);
     // ---- column residual E_col = A(:, J+) - C U R(:, J+)
     if (ell > 0) {
-      gather_cross(st, h->A, h->I_d.p, ell, h->Jp_d.p, nzJ, h->colpos_plus.p, h->U12.p, h->cap);
+      gather_cross(st, h->CA, h->I_d.p, ell, h->Jp_d.p, nzJ, h->colpos_plus.p, h->U12.p, h->cap);
       dtrsm(st, true, 'L', false, true, ell, nzJ, h->LU.p, h->cap, h->U12.p, h->cap);
       dcopy2d(st, ell, nzJ, h->U12.p, h->cap, h->Xb.p, h->cap, false);
       dtrsm(st, true, 'U', false, false, ell, nzJ, h->LU.p, h->cap, h->Xb.p, h->cap);
     }
-    if (h->A.fmt == 0) {
-      gather_cols(st, h->A, h->Jp_d.p, nzJ, nullptr, h->Ecol.p, m);
+    if (h->CA.fmt == 0) {
+      gather_cols(st, h->CA, h->Jp_d.p, nzJ, nullptr, h->Ecol.p, m);
       if (ell > 0) {
         dgemm(st, 0, 0, m, nzJ, ell, -1.0, h->Cbuf.p, m, h->Xb.p, h->cap, 1.0, h->Ecol.p, m);
         zero_rows_cm(st, h->Ecol.p, m, nzJ, h->I_d.p, ell);
       }
     } else {
-      ecol_csr(st, h->A, h->colpos.p, h->colpos_plus.p, h->rowpos.p, h->Xb.p, h->cap, nzJ,
+      ecol_csr(st, h->CA, h->colpos.p, h->colpos_plus.p, h->rowpos.p, h->Xb.p, h->cap, nzJ,
                h->Ecol.p);
     }
     // ---- row selection: LUPP on E_col
@@ -404,8 +482,8 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     // ---- bordered LU of A(I, J): [L11 0; L21 L22][U11 U12; 0 U22]
     if (ell > 0) {
       dcopy2d(st, ell, k, h->U12.p, cap, h->LU.p + (int64_t)ell * cap, cap, false);
-      if (h->A.fmt == 0) gather_rows_cm(st, h->Cbuf.p, m, ell, h->Ip_d.p, k, h->L21.p, k);
-      else gather_cross(st, h->A, h->Ip_d.p, k, h->J_d.p, ell, h->colpos.p, h->L21.p, k);
+      if (h->CA.fmt == 0) gather_rows_cm(st, h->Cbuf.p, m, ell, h->Ip_d.p, k, h->L21.p, k);
+      else gather_cross(st, h->CA, h->Ip_d.p, k, h->J_d.p, ell, h->colpos.p, h->L21.p, k);
       dtrsm(st, false, 'U', false, false, k, ell, h->LU.p, cap, h->L21.p, k);
       dcopy2d(st, k, ell, h->L21.p, k, h->LU.p + ell, cap, false);
     }
@@ -415,11 +493,11 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     APL_CUDA(cudaMemcpyAsync(h->J_d.p + ell, Jp.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
     APL_CUDA(cudaMemcpyAsync(h->I_d.p + ell, Ip.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
     const int ln = ell + k;
-    if (h->A.fmt == 0) {
-      gather_cols(st, h->A, h->Jp_d.p, k, nullptr, h->Cbuf.p + (int64_t)ell * m, m);
-      append_rows(st, h->A, h->Ip_d.p, k, h->Rbuf.p, cap, ell);
+    if (h->CA.fmt == 0) {
+      gather_cols(st, h->CA, h->Jp_d.p, k, nullptr, h->Cbuf.p + (int64_t)ell * m, m);
+      append_rows(st, h->CA, h->Ip_d.p, k, h->Rbuf.p, cap, ell);
     } else {
-      gather_cols(st, h->A, h->Jp_d.p, k, h->colpos_plus.p, h->Cp.p, m);
+      gather_cols(st, h->CA, h->Jp_d.p, k, h->colpos_plus.p, h->Cp.p, m);
     }
     set_map(st, h->rowpos.p, h->Ip_d.p, k, ell);
     set_map(st, h->colpos.p, h->Jp_d.p, k, ell);
@@ -429,11 +507,11 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     // the update is redone with FP64 products (a breakdown then is the FP64 one).
     double* T22 = h->TC.p + ell + (int64_t)ell * cap;
     auto tc_update = [&]() -> int {
-      if (h->A.fmt == 0)
+      if (h->CA.fmt == 0)
         dgemm(st, 1, 0, ln, k, m, 1.0, h->Cbuf.p, m, h->Cbuf.p + (int64_t)ell * m, m, 0.0,
               h->Gb.p, cap);
       else
-        gram_csr(st, h->A, h->J_d.p, ln, h->Cp.p, k, h->Gb.p, cap);
+        gram_csr(st, h->CA, h->J_d.p, ln, h->Cp.p, k, h->Gb.p, cap);
       if (ell > 0) {
         dtrsm(st, true, 'U', true, false, ell, k, h->TC.p, cap, h->Gb.p, cap);
         dcopy2d(st, ell, k, h->Gb.p, cap, h->TC.p + (int64_t)ell * cap, cap, false);
@@ -454,7 +532,7 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     if (info) throw Error(ST_EBREAKDOWN, "Cholesky of C^T C met a non-positive pivot");
     // ---- augmentQR(Q_R, T_R, A(I+, :)^T) with two Gram-Schmidt passes
     double* Cn = h->QR.p + (int64_t)ell * n;
-    gather_rows_T(st, h->A, h->Ip_d.p, k, Cn, n);
+    gather_rows_T(st, h->CA, h->Ip_d.p, k, Cn, n);
     if (ell > 0) {
       double* P1 = h->TR.p + (int64_t)ell * cap;
       dgemm(st, 1, 0, ell, k, n, 1.0, h->QR.p, n, Cn, n, 0.0, P1, cap);
@@ -478,12 +556,12 @@ int rank_step(aplicur_ctx* h, double* rho_out, bool* exhausted, double* margin) 
     dgather_cols(st, s, h->Y.p, s, h->J_d.p, L, h->Zb.p, s);
     dtrsm(st, false, 'U', false, false, s, L, h->LU.p, cap, h->Zb.p, s);
     dtrsm(st, false, 'L', false, true, s, L, h->LU.p, cap, h->Zb.p, s);
-    if (h->A.fmt == 0) {
+    if (h->CA.fmt == 0) {
       APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)s * n * sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
       dgemm(st, 0, 0, s, n, L, -1.0, h->Zb.p, s, h->Rbuf.p, cap, 1.0, h->E.p, s);
     } else {
-      erow_csr(st, h->A, h->rowpos.p, h->Zb.p, s, h->Y.p, h->E.p);
+      erow_csr(st, h->CA, h->rowpos.p, h->Zb.p, s, h->Y.p, h->E.p);
     }
   } else {
     APL_CUDA(cudaMemcpyAsync(h->E.p, h->Y.p, (size_t)s * n * sizeof(double),
@@ -512,8 +590,8 @@ void build_svdfree_preconditioner(aplicur_ctx* h) {
   h->work.alloc((size_t)3 * L + 16, st);
   double* Minv = h->VM.p;
   // A(I, J): rows I of C = A(:, J) (dense), or gathered from the CSR matrix
-  if (h->A.fmt == 0) gather_rows_cm(st, h->Cbuf.p, h->m, L, h->I_d.p, L, Minv, L);
-  else gather_cross(st, h->A, h->I_d.p, L, h->J_d.p, L, h->colpos.p, Minv, L);
+  if (h->CA.fmt == 0) gather_rows_cm(st, h->Cbuf.p, h->cm, L, h->I_d.p, L, Minv, L);
+  else gather_cross(st, h->CA, h->I_d.p, L, h->J_d.p, L, h->colpos.p, Minv, L);
   dtrsm(st, false, 'U', false, false, L, L, h->TC.p, cap, Minv, L);  // A(I,J) T_C^{-1}
   dtrsm(st, true, 'U', true, false, L, L, h->TR.p, cap, Minv, L);   // T_R^{-T} (...)
   const double smin = power_sigma_min(st, L, Minv, L, h->work.p, 50);
@@ -761,8 +839,6 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
               "bad precision");
   APL_REQUIRE(h->opt.variant == APLICUR_VARIANT_SVD || h->opt.variant == APLICUR_VARIANT_SVDFREE,
               "bad variant");
-  APL_REQUIRE(h->opt.variant == APLICUR_VARIANT_SVD || mu == 0.0,
-              "the SVD-free preconditioner is defined for mu = 0");
   APL_REQUIRE(h->opt.schedule == APLICUR_SCHEDULE_ADAPTIVE ||
                   h->opt.schedule == APLICUR_SCHEDULE_SINGLE_SHOT,
               "bad schedule");
@@ -794,14 +870,24 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   h->dw.fp64_gemm = h->opt.fp64_dense != 0;
   h->r = h->opt.normest_r;
   if (h->A.fmt == 1) build_csc(h);
+  // the CUR matrix: A, or A_mu = [A; delta I] for the SVD-free variant with mu > 0
+  // (section "SVD-free variant": a CUR of the regularised matrix)
+  h->CA = h->A;
+  h->cm = h->m;
+  if (h->opt.variant == APLICUR_VARIANT_SVDFREE && mu > 0.0) {
+    APL_REQUIRE(h->m + h->n < (1LL << 31), "A_mu: m + n exceeds int32 indexing");
+    build_amu(h);
+  }
+  h->kmax = std::min(h->cm, h->n);
+  if (h->opt.max_rank > 0) h->kmax = std::min<int64_t>(h->kmax, h->opt.max_rank);
   // sketch and norm-estimate draws
   std::vector<int> rows;
   std::vector<int8_t> sg;
   if (h->opt.sketch_rows && h->opt.sketch_signs) {
-    rows.assign(h->opt.sketch_rows, h->opt.sketch_rows + h->m * h->xi);
-    sg.assign(h->opt.sketch_signs, h->opt.sketch_signs + h->m * h->xi);
+    rows.assign(h->opt.sketch_rows, h->opt.sketch_rows + h->cm * h->xi);
+    sg.assign(h->opt.sketch_signs, h->opt.sketch_signs + h->cm * h->xi);
   } else {
-    draw_sketch(h->opt.seed, h->s, h->m, h->xi, rows, sg);
+    draw_sketch(h->opt.seed, h->s, h->cm, h->xi, rows, sg);
   }
   upload_sketch(h, rows, sg);
   std::vector<double> W;
@@ -821,9 +907,9 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   h->info.alloc(4, st);
   h->I_d.alloc(h->kmax, st); h->J_d.alloc(h->kmax, st);
   h->Jp_d.alloc(h->bsize, st); h->Ip_d.alloc(h->bsize, st);
-  h->colpos.alloc(n, st); h->colpos_plus.alloc(n, st); h->rowpos.alloc(m, st);
-  h->Ecol.alloc((size_t)m * h->bsize, st);
-  if (h->A.fmt == 1) h->Cp.alloc((size_t)m * h->bsize, st);
+  h->colpos.alloc(n, st); h->colpos_plus.alloc(n, st); h->rowpos.alloc(h->cm, st);
+  h->Ecol.alloc((size_t)h->cm * h->bsize, st);
+  if (h->A.fmt == 1) h->Cp.alloc((size_t)h->cm * h->bsize, st);
   if (with_lsqr) {
     h->x.alloc(n, st); h->tmp_m.alloc(m, st); h->tmp_n.alloc(n, st); h->tmp_n2.alloc(n, st);
     h->lam.alloc(n, st);
@@ -834,25 +920,25 @@ void ctx_init(aplicur_ctx* h, const aplicur_matrix* A, const double* b, double m
   APL_CUDA(cudaEventCreate(&e1));
   APL_CUDA(cudaEventRecord(e0, st));
   if (h->opt.sketch_kind == APLICUR_SKETCH_SPARSE_SIGN) {
-    sketch(st, h->A, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
+    sketch(st, h->CA, h->s, h->xi, h->tptr.p, h->ti.p, h->tsgn.p, h->srows.p, h->ssign.p,
            1.0 / std::sqrt((double)h->xi), h->Y.p);
   } else {
     // a dense operator drawn on the host (the draw is not part of the timed product)
     APL_CUDA(cudaEventRecord(e1, st));
     APL_CUDA(cudaEventSynchronize(e1));
     std::vector<double> S;
-    if (h->opt.sketch_kind == APLICUR_SKETCH_GAUSSIAN) draw_gaussian_sketch(h->opt.seed, h->s, h->m, S);
-    else draw_srht_sketch(h->opt.seed, h->s, h->m, S);
+    if (h->opt.sketch_kind == APLICUR_SKETCH_GAUSSIAN) draw_gaussian_sketch(h->opt.seed, h->s, h->cm, S);
+    else draw_srht_sketch(h->opt.seed, h->s, h->cm, S);
     if (h->opt.sketch_tc) {
-      tc_sketch_upload(st, S.data(), h->s, h->m, h->n, h->tcw);
-      tc_sketch_apply(st, h->A, h->tcw, h->Y.p, h->opt.sketch_tc, e0, e1);
+      tc_sketch_upload(st, S.data(), h->s, h->cm, h->n, h->tcw);
+      tc_sketch_apply(st, h->CA, h->tcw, h->Y.p, h->opt.sketch_tc, e0, e1);
     } else {
       DBuf<double> Sd, chunk;
       Sd.alloc(S.size(), st);
       APL_CUDA(cudaMemcpyAsync(Sd.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, st));
       APL_CUDA(cudaEventRecord(e0, st));
       DenseWorkScope dws(&h->dw);
-      operator_sketch(st, h->A, h->s, Sd.p, h->Y.p, chunk);
+      operator_sketch(st, h->CA, h->s, Sd.p, h->Y.p, chunk);
       APL_CUDA(cudaEventRecord(e1, st));
       APL_CUDA(cudaEventSynchronize(e1));
     }

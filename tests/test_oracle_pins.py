@@ -770,3 +770,89 @@ def test_aplicur_with_dense_sketch_reaches_ridge_solution(kind):
     assert np.allclose(res.Y, S @ p.dense, rtol=1e-13, atol=1e-13 * np.abs(res.Y).max())
     x = O.ridge_direct(p.dense, p.b, p.mu)
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-7
+
+
+# ------------------------------------------------------- SVD-free variant, mu > 0 ------
+
+def test_regularized_matrix():
+    """A_mu = [A; delta I]: A_mu^T A_mu = A^T A + delta^2 I, row m + j is delta e_j^T (dense
+    and CSR alike)."""
+    import scipy.sparse as sps
+    g = np.random.default_rng(41)
+    A = g.standard_normal((30, 12))
+    for M in (A, sps.csr_matrix(A)):
+        Am = O.regularized_matrix(M, 0.25)
+        D = Am.toarray() if sps.issparse(Am) else Am
+        assert D.shape == (42, 12)
+        assert np.allclose(D.T @ D, A.T @ A + 0.0625 * np.eye(12), rtol=1e-13, atol=1e-13)
+        assert np.array_equal(D[30 + 5], 0.25 * np.eye(12)[5])
+
+
+def test_svdfree_mu_full_rank_cur_flattens_the_regularized_matrix():
+    """At full rank the CUR of A_mu is exact (A_mu = C U R), so [A; delta I] Ptilde^{-1}
+    = sighat Q_C Q_R^T: all n singular values equal sighat.  The same operator built from a
+    CUR of A alone (also exact at full rank, for A) leaves [A; delta I] unflattened."""
+    g = np.random.default_rng(42)
+    m, n, delta = 60, 20, 0.3
+    A = (g.standard_normal((m, n)) * 10.0 ** -np.linspace(0, 3, n)) @ np.linalg.qr(
+        g.standard_normal((n, n)))[0]
+    Am = O.regularized_matrix(A, delta)
+    sighat = 0.7
+    Pt, _, I, J = _svdfree_pair(Am, 5, 4, sighat)
+    assert Pt.ell == n and np.any(I >= m)
+    sv = np.linalg.svd(Am @ _dense_op(Pt.apply_inv, n), compute_uv=False)
+    assert np.allclose(sv, sighat, rtol=1e-9)
+    Pa, _, _, _ = _svdfree_pair(A, 5, 4, sighat)
+    sva = np.linalg.svd(Am @ _dense_op(Pa.apply_inv, n), compute_uv=False)
+    assert sva[0] / sva[-1] > 10.0
+
+
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_svdfree_mu_driver_reaches_ridge_solution(kind):
+    """The SVD-free variant with mu > 0 (CUR of A_mu, sketch over m + n columns, LSQR on
+    [A; delta I] Ptilde^{-1} with the transposed operator on the A^T side) converges to
+    the ridge solution and selects rows of the appended delta I block."""
+    p = (wl.small_dense(400, 60, 904, decay=6.0, mu=1e-4, sketch_dim=4) if kind == "dense"
+         else wl.small_sparse(3000, 300, wl.BASE_SEED + 50, nnz_per_col=6, mu=1e-5,
+                              sketch_dim=10))
+    A = p.dense if kind == "dense" else p.to_scipy()
+    res = O.aplicur(A, p.b, p.mu, p.sketch_dim, O.Options(seed=3, variant="svdfree"), tol=1e-10)
+    assert res.converged
+    assert np.any(res.I >= p.m)
+    xd = O.ridge_direct(A if kind == "dense" else A.toarray(), p.b, p.mu)
+    kappa = 1.0 / math.sqrt(p.mu)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) <= 10 * kappa * 1e-10
+
+
+def test_svdfree_lsqr_needs_the_transposed_operator():
+    """Ptilde is not symmetric: LSQR on A Ptilde^{-1} must apply Ptilde^{-T} on the A^T
+    side.  With Ptilde^{-1} there instead (a planted mistake) the phase no longer solves
+    the least-squares problem."""
+    p = wl.small_dense(200, 30, 906, decay=4.0, mu=0.0, sketch_dim=4)
+    A = p.dense
+    Pt, _, I, J = _svdfree_pair(A, 4, 3, 0.5)
+    xd = np.linalg.lstsq(A, p.b, rcond=None)[0]
+
+    def run(P):
+        r = O.plsqr_phase(A, p.b, 0.0, np.zeros(p.n), P, eps_lsqr=1e-14, maxit=400)
+        return np.linalg.norm(r.x - xd) / np.linalg.norm(xd)
+
+    assert run(Pt) <= 1e-8
+
+    class Planted(O.SvdFreePreconditioner):
+        def apply_inv_T(self, w):
+            return self.apply_inv(w)
+
+    bad = Planted(Pt.Q_R, Pt.T_R, Pt.T_C, Pt.A_IJ, Pt.sighat)
+    assert run(bad) > 1e-3
+
+
+def test_ridge_sparse_matches_the_dense_solution():
+    """Conjugate gradients on the normal equations reach the dense QR ridge solution (a
+    different method for the same closed form) and report a residual at its tolerance."""
+    p = wl.small_sparse(2000, 150, wl.BASE_SEED + 53, nnz_per_col=4, mu=1e-4, sketch_dim=10)
+    A = p.to_scipy()
+    x, res = O.ridge_sparse(A, p.b, p.mu)
+    xd = O.ridge_direct(A.toarray(), p.b, p.mu)
+    assert res <= 1e-14
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-9
