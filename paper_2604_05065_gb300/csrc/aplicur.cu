@@ -187,6 +187,8 @@ struct aplicur_ctx {
   LuppWork lw;
   // preconditioner
   DBuf<double> Mb, VM, sigma, coef, coef2;
+  DBuf<double> Wprev, Wnext;  // rotation of the last build's FP32 Jacobi stage (warm start)
+  int64_t wl = 0;             // its order (0: none)
   PrecondDev P;
   double sighat = 1.0;
   std::vector<double> sig_host;
@@ -419,6 +421,7 @@ void reset_cur(aplicur_ctx* h) {
   if (h->LU.p) h->LU.zero(st);
   if (h->TR.p) h->TR.zero(st);
   if (h->TC.p) h->TC.zero(st);
+  h->wl = 0;
   h->P = PrecondDev{};
   h->steps.clear();
   h->phases.clear();
@@ -637,7 +640,15 @@ void build_preconditioner(aplicur_ctx* h) {
   // M^T = X^T T_C^T; the Jacobi sweep on the columns of M^T gives the singular values
   // and right singular vectors of M
   dgemm(st, 1, 1, L, L, L, 1.0, X, L, h->TC.p, cap, 0.0, h->Mb.p, L);
-  jacobi_left(st, L, h->Mb.p, L, h->VM.p, L, h->sigma.p, h->info.p);
+  // the leading block of this M is close to the last build's M (the same leading
+  // columns of Q_C and Q_R, both CURs accurate there): its Jacobi rotation warm-starts
+  // this one
+  h->Wnext.alloc((size_t)L * L, st);
+  int64_t wl_new = 0;
+  jacobi_left(st, L, h->Mb.p, L, h->VM.p, L, h->sigma.p, h->info.p,
+              h->wl > 0 ? h->Wprev.p : nullptr, h->wl, h->Wnext.p, &wl_new);
+  h->Wprev.swap(h->Wnext);
+  h->wl = wl_new;
   h->sig_host.resize(L);
   APL_CUDA(cudaMemcpyAsync(h->sig_host.data(), h->sigma.p, L * sizeof(double),
                            cudaMemcpyDeviceToHost, st));

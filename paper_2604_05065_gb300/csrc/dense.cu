@@ -1315,12 +1315,24 @@ double power_sigma_min(cudaStream_t st, int64_t L, const double* Minv, int64_t l
 }
 
 int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
-                double* sigma, int* flag_dev) {
+                double* sigma, int* flag_dev, const double* W0, int64_t l0, double* Wout,
+                int64_t* wout_l) {
+  if (wout_l) *wout_l = 0;
   if (l <= 0) return 0;
   const int64_t N = (l % 2) ? l + 1 : l;
   int sweeps = 0;
   const size_t smem = ((size_t)JW2 * jac32_ld(l) + JW2 * JW2) * sizeof(float);
   if (l > 1 && smem <= (size_t)kJac32SmemCap) {
+    // warm start: B(:, 0:l0) <- B(:, 0:l0) W0 with the orthogonal W0 of an earlier
+    // factorisation whose matrix was close to this one's leading block (singular values
+    // unchanged, the sweeps start nearly converged on those columns)
+    const bool warm = W0 && l0 > 0 && l0 <= l;
+    if (warm) {
+      DenseWork& wk0 = dense_work();
+      wk0.jtmp.alloc(l * l, st);
+      dgemm(st, 0, 0, l, l0, l0, 1.0, B, ldb, W0, l0, 0.0, wk0.jtmp.p, l);
+      dcopy2d(st, l, l0, wk0.jtmp.p, l, B, ldb, false);
+    }
     // Stage 1 (FP32): sweeps on an FP32 copy that accumulate the rotation W until the
     // columns are orthogonal to FP32 accuracy; then B <- B W in FP64.  Skipped when the
     // CTA's two column blocks do not fit in shared memory (l above about 3600).
@@ -1388,6 +1400,16 @@ int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, i
     }
     dgemm(st, 0, 0, l, l, l, 1.0, B, ldb, Wd, l, 0.0, G, l);
     dcopy2d(st, l, l, G, l, B, ldb, false);
+    if (Wout) {
+      // the whole rotation of this stage, diag(W0, I) Wd, for the next warm start
+      if (warm) {
+        dgemm(st, 0, 0, l0, l, l0, 1.0, W0, l0, Wd, l, 0.0, Wout, l);
+        if (l > l0) dcopy2d(st, l - l0, l, Wd + l0, l, Wout + l0, l, false);
+      } else {
+        dcopy2d(st, l, l, Wd, l, Wout, l, false);
+      }
+      if (wout_l) *wout_l = l;
+    }
   }
   const size_t smem_df = (size_t)JW2 * jacdf_ld(l) * sizeof(float2);
   if (l > 1 && !dense_work().fp64_gemm && smem_df <= (size_t)kJac32SmemCap) {

@@ -28,10 +28,15 @@ bool cholqr2(cudaStream_t st, int64_t n, int64_t k, double* E, int64_t lde, doub
 // sigma receives the singular values of B in descending order and U (l x l, ldu) the
 // matching left singular vectors (normalised columns).  With B = M^T these are the
 // singular values and right singular vectors of M.  flag_dev is device scratch of at
-// least 3 ints.  Returns the sweep count; throws ST_ETIMEOUT when a bounded wait of a
-// sweep kernel gave up.
+// least 3 ints.  Warm start: W0 (l0 x l0, ld l0, orthogonal, l0 <= l) pre-rotates the first
+// l0 columns of B (the FP32 stage then starts from them nearly orthogonal when B's leading
+// block is close to the matrix W0 came from).  Wout (l x l, ld l), when given, receives
+// the FP32 stage's whole rotation (orthogonal to FP64 accuracy) and *wout_l its order, or
+// 0 when that stage did not run.  Returns the sweep count; throws ST_ETIMEOUT when a
+// bounded wait of a sweep kernel gave up.
 int jacobi_left(cudaStream_t st, int64_t l, double* B, int64_t ldb, double* U, int64_t ldu,
-                double* sigma, int* flag_dev);
+                double* sigma, int* flag_dev, const double* W0 = nullptr, int64_t l0 = 0,
+                double* Wout = nullptr, int64_t* wout_l = nullptr);
 
 // sigma_min(M) = 1 / ||M^{-1}||_2 for M^{-1} (L x L, column-major, ld ldm) by `iters` steps
 // of power iteration on M^{-T} M^{-1} from a fixed start vector; work holds 3 L + 1
