@@ -506,7 +506,8 @@ ALU = {3: (DF32_PEAK_TFLOPS, "derived compensated-FP32 ceiling: 152 SMs x 128 la
 def batched_measure(args, dev):
     """The batched workload (uneven dense and CSR FP32 problems, 16 right-hand sides each,
     mu 1e-5, sketch dimension 50): one warm-up and one timed APLICUR batch solve to the
-    time-to-tol target, then the same batch by plain LSQR with the same grouped kernels.
+    time-to-tol target, one timed solve followed by its adjoint (gradients in b, mu and A
+    of every pair), then the same batch by plain LSQR with the same grouped kernels.
     Throughput counts solved (problem, right-hand side) pairs per second."""
     import torch
 
@@ -552,6 +553,24 @@ def batched_measure(args, dev):
                ms_build=round(st["time_build_ms"], 1), ms_lsqr=round(st["time_lsqr_ms"], 1),
                tuned={"rows_per_warp": st["rows_per_warp"], "cols_per_lane": st["cols_per_lane"]},
                launches_per_iter=st["launches_per_iter"])
+    # with adjoint: the solve and the backward of 0.5 sum ||x - t||^2 (t = 0: dL/dx = x),
+    # dL/db, dL/dmu and dL/dA for every pair
+    xs = s.solve(TOL, args.maxit)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    xs = s.solve(TOL, args.maxit)
+    s.backward(xs, TOL, args.maxit, want_A=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    asecs = e0.elapsed_time(e1) / 1000.0
+    ast = s.stats()
+    out["with_adjoint"] = {"solve_and_backward_s": round(asecs, 3),
+                           "solves_per_s": round(nprob * R / asecs, 2),
+                           "backward_converged": ast["converged"], "backward_ne_max": ast["ne_max"],
+                           "backward_iters_max": ast["iters_max"]}
+    del xs
     if not args.no_plain:
         psecs = timed(s.plain_lsqr, warm=False)  # kernels already warm from the solves
         pst = s.stats()

@@ -425,7 +425,24 @@ aplicur_status aplicur_batch_solve(aplicur_batch_handle h, double tol, int64_t m
 aplicur_status aplicur_batch_plain_lsqr(aplicur_batch_handle h, double tol, int64_t maxit,
                                         double* const* x_out);
 
-/* Result of pair (p, r) of the last solve; any output may be NULL. */
+/* Adjoint of the last aplicur_batch_solve / aplicur_batch_plain_lsqr (Section "adjoint"
+ * of the single-problem entry, per pair): with the incoming gradients g_{p,r} = dL/dx_{p,r}
+ * (grad_x: nprob device pointers, each n_p x nrhs FP64 column-major; borrowed), solves
+ * (A_p^T A_p + mu I) lambda = g with the preconditioners the solve built (batched
+ * correction-form phases to the normal-equation residual tol relative to ||g||), then
+ * writes, for every output that is not NULL:
+ *   grad_b[p]  (m_p x nrhs FP64 column-major, device)  dL/db = A_p lambda;
+ *   grad_mu    (nprob * nrhs FP64, device, index p * nrhs + r)  dL/dmu = -lambda^T x;
+ *   grad_A[p]  (m_p x n_p FP32 row-major, device; dense problems only)  dL/dA_p =
+ *              sum_r r_r lambda_r^T - (A_p lambda_r) x_r^T,  r_r = b_r - A_p x_r.
+ * The forward solutions stay in place (aplicur_batch_get_pair and the statistics then
+ * report the adjoint solves).  ENOTCONV when a pair missed tol (outputs still written);
+ * EINVAL without a prior solve or for grad_A of a CSR problem. */
+aplicur_status aplicur_batch_backward(aplicur_batch_handle h, const double* const* grad_x,
+                                     double tol, int64_t maxit, double* const* grad_b,
+                                     double* grad_mu, float* const* grad_A);
+
+/* Result of pair (p, r) of the last solve (or adjoint); any output may be NULL. */
 aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t r,
                                       int64_t* iters, double* ne_res, int32_t* converged);
 

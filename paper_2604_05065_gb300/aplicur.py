@@ -107,6 +107,7 @@ SIGNATURES = {
                                        _I32, C.POINTER(Options), _VP]),
     "aplicur_batch_solve": (C.c_int, [_VP, _D, _I64, _VP]),
     "aplicur_batch_plain_lsqr": (C.c_int, [_VP, _D, _I64, _VP]),
+    "aplicur_batch_backward": (C.c_int, [_VP, _VP, _D, _I64, _VP, _VP, _VP]),
     "aplicur_batch_get_pair": (C.c_int, [_VP, _I32, _I32, C.POINTER(_I64), C.POINTER(_D), _PI32]),
     "aplicur_batch_get_problem": (C.c_int, [_VP, _I32, _PI32, _PI32, _PI32, _PI32, _VP, _VP]),
     "aplicur_batch_get_stats": (C.c_int, [_VP, C.POINTER(BatchStats)]),
@@ -586,8 +587,10 @@ class BatchSolver:
         self.shapes = []
         R = None
         bptr = (C.c_void_p * len(mats))()
+        self._dense = []
         for p, (A, b) in enumerate(zip(mats, rhs)):
             mat, keep, _ = _marshal_matrix(torch, A)
+            self._dense.append(mat.format == 0)
             self._keep += keep
             arr[p] = mat
             b2 = b.reshape(b.shape[0], -1).to(torch.float64)
@@ -647,6 +650,40 @@ class BatchSolver:
 
     def plain_lsqr(self, tol: float = 1e-8, maxit: int = 100000):
         return self._run(self._lib.aplicur_batch_plain_lsqr, tol, maxit)
+
+    def backward(self, grad_x, tol: float = 1e-8, maxit: int = 100000, want_A: bool = True):
+        """Adjoint of the last solve.  grad_x: list of (n_p, R) CUDA tensors dL/dx.
+        Returns (grad_b: list of (m_p, R) float64, grad_mu: (nprob, R) float64,
+        grad_A: list of (m_p, n_p) float32 for dense problems, None for CSR ones, or
+        None when want_A is False)."""
+        torch = _torch()
+        npb = len(self.shapes)
+        if len(grad_x) != npb:
+            raise ValueError("need one gradient block per problem")
+        keep, gptr = [], (C.c_void_p * npb)()
+        for p, (g, (m, n)) in enumerate(zip(grad_x, self.shapes)):
+            g2 = g.reshape(n, -1).to(device=self.device, dtype=torch.float64)
+            if g2.shape[1] != self.R:
+                raise ValueError("gradients must be (n_p, R)")
+            gt = g2.t().contiguous()  # column-major n x R
+            keep.append(gt)
+            gptr[p] = gt.data_ptr()
+        gb = [torch.empty(self.R, m, dtype=torch.float64, device=self.device)
+              for (m, _) in self.shapes]
+        bptr = (C.c_void_p * npb)(*[x.data_ptr() for x in gb])
+        gmu = torch.empty(npb * self.R, dtype=torch.float64, device=self.device)
+        gA, aptr = None, None
+        if want_A:
+            gA = [torch.empty(m, n, dtype=torch.float32, device=self.device) if self._dense[p]
+                  else None for p, (m, n) in enumerate(self.shapes)]
+            aptr = (C.c_void_p * npb)(*[x.data_ptr() if x is not None else None for x in gA])
+        st = self._lib.aplicur_batch_backward(self._h, gptr, float(tol), int(maxit), bptr,
+                                              C.c_void_p(gmu.data_ptr()), aptr)
+        if st != 0 and st != 4:
+            raise AplicurError(st, self._lib.aplicur_batch_last_error(self._h).decode(),
+                               self.allocator)
+        self.last_status = st
+        return [x.t() for x in gb], gmu.reshape(npb, self.R), gA
 
     def pair(self, p: int, r: int) -> dict:
         it, ne, cv = C.c_int64(), C.c_double(), C.c_int32()

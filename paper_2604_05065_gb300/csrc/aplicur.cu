@@ -1379,6 +1379,8 @@ struct aplicur_batch_ctx {
   std::vector<double> ne;
   std::vector<char> conv;
   std::vector<char> broke;       // per problem: a rank step or build broke down
+  bool solved = false;           // a solve has left forward solutions in the engine
+  std::vector<const double*> bsrc;  // right-hand sides (m_p x R column-major, borrowed)
   Allocator alloc_;              // caller's device allocator (empty: cudaMallocAsync)
   aplicur_batch_stats stats{};
   std::string err;
@@ -1462,6 +1464,8 @@ void batch_phase(aplicur_batch_ctx* h, const std::vector<char>& mask, const std:
     h->conv[e] = ne[e] <= tol ? 1 : 0;
   }
 }
+
+void refine_pairs(aplicur_batch_ctx* h, double tol, long long maxit, PairBook& bk, bool plain);
 
 int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
   using clk = std::chrono::steady_clock;
@@ -1584,28 +1588,11 @@ int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
     }
   }
   // final phases without the dynamic test (the last phase of the driver continued, or
-  // the plain solve): until tol, the iteration budget, or a phase that halves the
-  // residual no more
-  // FP32 recurrences end each phase after a smaller true gain than the FP64 driver's
-  // (the estimate runs ahead of the residual), so the batch allows 4x the phases
-  for (int rep = 0; rep <= 4 * o.max_extra_phases; ++rep) {
-    std::vector<char> mask(npairs, 0);
-    bool any = false;
-    for (size_t e = 0; e < npairs; ++e)
-      if (!bk.stopped[e] && h->iters[e] < maxit) { mask[e] = 1; any = true; }
-    if (!any) break;
-    std::vector<double> nu(np, INFINITY);
-    auto t0 = clk::now();
-    batch_phase(h, mask, nu, tol, maxit, it);
-    h->stats.time_lsqr_ms += ms_since(t0);
-    for (size_t e = 0; e < npairs; ++e) {
-      if (!mask[e]) continue;
-      // a refinement phase that no longer gains 10% ends the pair's solve
-      const bool stag = !plain || rep > 0 ? (it[e] == 0 || h->ne[e] > 0.9 * bk.prev[e]) : false;
-      if (h->conv[e] || h->iters[e] >= maxit || stag) bk.stopped[e] = 1;
-      bk.prev[e] = h->ne[e];
-    }
-  }
+  // the plain solve).  FP32 recurrences end each phase after a smaller true gain than the
+  // FP64 driver's (the estimate runs ahead of the residual), so the batch allows 4x the
+  // phases
+  refine_pairs(h, tol, maxit, bk, plain);
+  h->solved = true;
   int nconv = 0;
   long long imax = 0, isum = 0;
   double nmax = 0;
@@ -1623,6 +1610,182 @@ int batch_solve(aplicur_batch_ctx* h, double tol, long long maxit, bool plain) {
   h->stats.rows_per_warp = h->eng.tuned_rw();
   h->stats.cols_per_lane = h->eng.tuned_cw();
   h->stats.launches_per_iter = h->eng.launches_per_iter();
+  return nconv == (int)npairs ? ST_OK : ST_ENOTCONV;
+}
+
+// Y (m x R, column-major) = A X (X: n x R column-major) with FP64 sums of the stored
+// FP32 values, or, with Bsub, Y = Bsub - A X; one warp per row.
+__global__ void batch_ax_kernel(int fmt, int64_t m, int64_t n, int64_t ld, const float* vals,
+                                const int* rowptr, const int* colidx, const double* X, int R,
+                                const double* Bsub, double* Y) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double acc[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+  if (fmt == 0) {
+    for (int64_t j = lane; j < n; j += 32) {
+      const double a = (double)vals[i * ld + j];
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (r < R) acc[r] = fma(a, X[j + (int64_t)r * n], acc[r]);
+    }
+  } else {
+    for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+      const double a = (double)vals[e];
+      const int64_t j = colidx[e];
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (r < R) acc[r] = fma(a, X[j + (int64_t)r * n], acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if (r >= R) break;
+    double v = acc[r];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) Y[i + (int64_t)r * m] = Bsub ? Bsub[i + (int64_t)r * m] - v : v;
+  }
+}
+
+// out[r] = -lambda_r^T x_r  (the gradient in mu of each pair), one block per pair
+__global__ void batch_gmu_kernel(int64_t n, const double* lam, const double* x, double* out) {
+  __shared__ double sh[32];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+    s = fma(lam[j + (int64_t)r * n], x[j + (int64_t)r * n], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[r] = -s;
+}
+
+// G(i, j) = sum_r res(i, r) lambda(j, r) - (A lambda)(i, r) x(j, r), FP32 row-major ld n
+__global__ void batch_gA_kernel(int64_t m, int64_t n, int R, const double* res,
+                                const double* al, const double* lam, const double* x, float* G) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    double g = 0.0;
+    for (int r = 0; r < R; ++r)
+      g += res[i + (int64_t)r * m] * lam[j + (int64_t)r * n] -
+           al[i + (int64_t)r * m] * x[j + (int64_t)r * n];
+    G[e] = (float)g;
+  }
+}
+
+// Phases without the dynamic test (nu = infinity) for every pair not stopped, until tol,
+// the iteration budget, or a phase that no longer gains 10% (the final phases of the
+// driver, and the adjoint solves).
+void refine_pairs(aplicur_batch_ctx* h, double tol, long long maxit, PairBook& bk, bool plain) {
+  using clk = std::chrono::steady_clock;
+  const size_t npairs = (size_t)h->np * h->R;
+  const aplicur_options& o = h->pc[0]->opt;
+  std::vector<long long> it;
+  for (int rep = 0; rep <= 4 * o.max_extra_phases; ++rep) {
+    std::vector<char> mask(npairs, 0);
+    bool any = false;
+    for (size_t e = 0; e < npairs; ++e)
+      if (!bk.stopped[e] && h->iters[e] < maxit) { mask[e] = 1; any = true; }
+    if (!any) break;
+    std::vector<double> nu(h->np, INFINITY);
+    auto t0 = clk::now();
+    batch_phase(h, mask, nu, tol, maxit, it);
+    h->stats.time_lsqr_ms += std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    for (size_t e = 0; e < npairs; ++e) {
+      if (!mask[e]) continue;
+      const bool stag = !plain || rep > 0 ? (it[e] == 0 || h->ne[e] > 0.9 * bk.prev[e]) : false;
+      if (h->conv[e] || h->iters[e] >= maxit || stag) bk.stopped[e] = 1;
+      bk.prev[e] = h->ne[e];
+    }
+  }
+}
+
+// Adjoint of the batched solves: lambda_{p,r} = (A_p^T A_p + mu I)^{-1} g_{p,r} with the
+// preconditioners of the last solve, then d/db = A lambda, d/dmu = -lambda^T x and, for
+// dense problems, d/dA = r lambda^T - (A lambda) x^T summed over the right-hand sides.
+int batch_backward(aplicur_batch_ctx* h, const double* const* gx, double tol, long long maxit,
+                   double* const* gb, double* gmu, float* const* gA) {
+  APL_REQUIRE(h->solved, "batched backward: run aplicur_batch_solve first");
+  const int np = h->np, R = h->R;
+  const size_t npairs = (size_t)np * R;
+  cudaStream_t st = h->st;
+  for (int p = 0; p < np; ++p) {
+    APL_REQUIRE(gx[p] != nullptr, "batched backward: grad_x[p] NULL");
+    APL_REQUIRE(!(gA && gA[p]) || h->pc[p]->A.fmt == 0, "grad_A is only produced for dense A");
+  }
+  std::vector<DBuf<double>> xs(np), lam(np);
+  for (int p = 0; p < np; ++p) {
+    xs[p].alloc((size_t)h->pc[p]->n * R, st);
+    h->eng.get_x(p, xs[p].p);
+  }
+  h->eng.begin_adjoint(std::vector<const double*>(gx, gx + np));
+  h->iters.assign(npairs, 0);
+  h->ne.assign(npairs, INFINITY);
+  h->conv.assign(npairs, 0);
+  h->stats.time_lsqr_ms = 0.0;
+  PairBook bk;
+  bk.stopped.assign(npairs, 0);
+  bk.prev.assign(npairs, INFINITY);
+  for (int p = 0; p < np; ++p)
+    for (int r = 0; r < R; ++r)
+      if (h->eng.norm_ref(p, r) == 0.0) {
+        const size_t e = (size_t)p * R + r;
+        h->ne[e] = 0.0; h->conv[e] = 1; bk.stopped[e] = 1;
+      }
+  try {
+    refine_pairs(h, tol, maxit, bk, false);
+    for (int p = 0; p < np; ++p) {
+      lam[p].alloc((size_t)h->pc[p]->n * R, st);
+      h->eng.get_x(p, lam[p].p);
+    }
+  } catch (...) {
+    h->eng.end_adjoint();
+    throw;
+  }
+  h->eng.end_adjoint();
+  for (int p = 0; p < np; ++p) {
+    const aplicur_ctx* c = h->pc[p];
+    const MatView& A = c->A;
+    const int64_t m = c->m, n = c->n;
+    const unsigned rows_blocks = (unsigned)cdiv(m * 32, 256);
+    DBuf<double> al;
+    double* alp = gb ? gb[p] : nullptr;
+    if (!alp) { al.alloc((size_t)m * R, st); alp = al.p; }
+    batch_ax_kernel<<<rows_blocks, 256, 0, st>>>(A.fmt, m, n, A.ld, (const float*)A.vals, A.rowptr,
+                                                 A.colidx, lam[p].p, R, nullptr, alp);
+    APL_LAUNCH_CHECK();
+    if (gmu) {
+      batch_gmu_kernel<<<R, 256, 0, st>>>(n, lam[p].p, xs[p].p, gmu + (size_t)p * R);
+      APL_LAUNCH_CHECK();
+    }
+    if (gA && gA[p]) {
+      DBuf<double> res;
+      res.alloc((size_t)m * R, st);
+      batch_ax_kernel<<<rows_blocks, 256, 0, st>>>(A.fmt, m, n, A.ld, (const float*)A.vals,
+                                                   A.rowptr, A.colidx, xs[p].p, R, h->bsrc[p],
+                                                   res.p);
+      APL_LAUNCH_CHECK();
+      batch_gA_kernel<<<(unsigned)std::min<int64_t>(cdiv(m * n, 256), 4096), 256, 0, st>>>(
+          m, n, R, res.p, alp, lam[p].p, xs[p].p, gA[p]);
+      APL_LAUNCH_CHECK();
+    }
+  }
+  APL_CUDA(cudaStreamSynchronize(st));
+  int nconv = 0;
+  long long imax = 0, isum = 0;
+  double nmax = 0;
+  for (size_t e = 0; e < npairs; ++e) {
+    nconv += h->conv[e];
+    imax = std::max(imax, h->iters[e]);
+    isum += h->iters[e];
+    nmax = std::max(nmax, h->ne[e]);
+  }
+  h->stats.pairs = (int32_t)npairs;
+  h->stats.converged = nconv;
+  h->stats.iters_max = imax;
+  h->stats.iters_sum = isum;
+  h->stats.ne_max = nmax;
   return nconv == (int)npairs ? ST_OK : ST_ENOTCONV;
 }
 
@@ -1687,6 +1850,7 @@ aplicur_status aplicur_batch_create(aplicur_batch_handle* out, int32_t nprob,
     });
     std::vector<BatchSrc> src(nprob);
     for (int p = 0; p < nprob; ++p) src[p] = BatchSrc{h->pc[p]->A, b[p]};
+    h->bsrc.assign(b, b + nprob);
     h->eng.setup(h->st, src, nrhs, mu);
     h->eng.autotune();
     h->stats.time_setup_ms =
@@ -1725,6 +1889,16 @@ aplicur_status aplicur_batch_solve(aplicur_batch_handle h, double tol, int64_t m
 aplicur_status aplicur_batch_plain_lsqr(aplicur_batch_handle h, double tol, int64_t maxit,
                                         double* const* x_out) {
   return batch_run(h, tol, maxit, x_out, true);
+}
+
+aplicur_status aplicur_batch_backward(aplicur_batch_handle h, const double* const* grad_x,
+                                     double tol, int64_t maxit, double* const* grad_b,
+                                     double* grad_mu, float* const* grad_A) {
+  if (!h || !grad_x) return APLICUR_EINVAL;
+  return bguarded(h, [&]() -> int {
+    cudaSetDevice(h->device);
+    return batch_backward(h, grad_x, tol, maxit, grad_b, grad_mu, grad_A);
+  });
 }
 
 aplicur_status aplicur_batch_get_pair(aplicur_batch_handle h, int32_t p, int32_t r,

@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(BT) res_kernel(const BItem* __restrict__ items
           df_fma(acc, P.vals[k], P.Xh[j * NR + r], P.Xl[j * NR + r]);
         }
       }
-      const double v = P.B[i * NR + r] - df_val(acc);
+      const double v = (P.B ? P.B[i * NR + r] : 0.0) - df_val(acc);
       const float h = __double2float_rn(v);
       P.Rh[i * NR + r] = h;
       P.Rl[i * NR + r] = __double2float_rn(v - (double)h);
@@ -561,7 +561,8 @@ __global__ void __launch_bounds__(BT) gtr_kernel(const BItem* __restrict__ items
         df_fma(acc, P.cvals[k], P.Rh[i * NR + r], P.Rl[i * NR + r]);
       }
     }
-    const double h = df_val(acc) - P.mu * P.X[j * NR + r];
+    double h = df_val(acc) - P.mu * P.X[j * NR + r];
+    if (P.Gx) h += P.Gx[j * NR + r];
     if (init) P.U[(P.m + j) * NR + r] = (float)(h / P.delta);
     sq += h * h;
   }
@@ -726,6 +727,53 @@ void BatchEngine::setup(cudaStream_t st, const std::vector<BatchSrc>& src, int R
   ne_residual(all, nb);
   for (int p = 0; p < np; ++p)
     for (int r = 0; r < R_; ++r) norm_ref_[(size_t)p * RS_ + r] = nb[(size_t)p * R_ + r];
+}
+
+void BatchEngine::begin_adjoint(const std::vector<const double*>& gx) {
+  const int np = nprob();
+  APL_REQUIRE((int)gx.size() == np, "adjoint: one gradient per problem");
+  if (!adj_) adj_.reset(new DBuf<double>[np]);
+  saved_ref_ = norm_ref_;
+  saved_b_.assign(np, nullptr);
+  for (int p = 0; p < np; ++p) {
+    BProb& P = hp_[p];
+    const int64_t n = P.n, rs = RS_;
+    adj_[p].alloc((size_t)2 * n * rs, st_);
+    double* sx = adj_[p].p;
+    double* g = adj_[p].p + n * rs;
+    APL_CUDA(cudaMemcpyAsync(sx, P.X, n * rs * sizeof(double), cudaMemcpyDeviceToDevice, st_));
+    pack_rhs<<<(unsigned)cdiv(n * rs, 256), 256, 0, st_>>>(n, R_, RS_, gx[p], g);
+    APL_LAUNCH_CHECK();
+    saved_b_[p] = P.B;
+    P.B = nullptr;
+    P.Gx = g;
+    // ||g|| per pair as the residual reference (host copy: n x R values per problem)
+    std::vector<double> hg((size_t)n * R_);
+    APL_CUDA(cudaMemcpyAsync(hg.data(), gx[p], hg.size() * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    APL_CUDA(cudaStreamSynchronize(st_));
+    for (int r = 0; r < R_; ++r) {
+      double ss = 0.0;
+      for (int64_t j = 0; j < n; ++j) ss += hg[j + (size_t)r * n] * hg[j + (size_t)r * n];
+      norm_ref_[(size_t)p * RS_ + r] = std::sqrt(ss);
+    }
+  }
+  zero_x();
+  APL_CUDA(cudaStreamSynchronize(st_));
+}
+
+void BatchEngine::end_adjoint() {
+  const int np = nprob();
+  if (saved_b_.empty()) return;
+  for (int p = 0; p < np; ++p) {
+    BProb& P = hp_[p];
+    APL_CUDA(cudaMemcpyAsync(P.X, adj_[p].p, (size_t)P.n * RS_ * sizeof(double),
+                             cudaMemcpyDeviceToDevice, st_));
+    P.B = saved_b_[p];
+    P.Gx = nullptr;
+  }
+  norm_ref_ = saved_ref_;
+  saved_b_.clear();
+  APL_CUDA(cudaStreamSynchronize(st_));
 }
 
 void BatchEngine::set_precond(int p, const PrecondDev& Pd) {

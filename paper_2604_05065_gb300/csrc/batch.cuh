@@ -52,7 +52,9 @@ struct BProb {
   float* s = nullptr;   // ell x RS, VM t
   double* X = nullptr;  // n x RS solution
   double* D = nullptr;  // n x RS search direction in x space
-  const double* B = nullptr;  // m x RS right-hand sides
+  const double* B = nullptr;  // m x RS right-hand sides (NULL: zero, the adjoint solves)
+  const double* Gx = nullptr; // n x RS forcing added to A^T (b - A x) - mu x (adjoint: the
+                              // incoming gradient), or NULL
   float* Xh = nullptr;  // n x RS hi/lo FP32 split of X
   float* Xl = nullptr;
   float* Rh = nullptr;  // m x RS hi/lo FP32 split of the residual
@@ -107,6 +109,13 @@ class BatchEngine {
   void ne_residual(const std::vector<char>& mask, std::vector<double>& ne);
   double norm_ref(int p, int r) const { return norm_ref_[(size_t)p * RS_ + r]; }
   void get_x(int p, double* x_out) const;  // n x R column-major, device
+  // Adjoint mode: the phases solve (A^T A + mu I) lambda = g for the incoming gradients
+  // g of every problem (gx[p]: n x R column-major FP64, device) with the preconditioners
+  // in place: b is taken as zero, g is added to the normal-equation residual, x restarts
+  // at zero and the residuals are relative to ||g||.  end_adjoint restores the forward
+  // right-hand sides, solutions and references.
+  void begin_adjoint(const std::vector<const double*>& gx);
+  void end_adjoint();
   // Picks the dense tile shapes by timing the candidates on this batch.
   void autotune();
   int tuned_rw() const { return rw_; }
@@ -137,6 +146,9 @@ class BatchEngine {
   int n_apass_ = 0, n_gta_ = 0, n_gtq_ = 0, n_gtqv_ = 0, n_gtv_ = 0, n_gnv_ = 0, n_exp_ = 0,
       n_expz_ = 0, n_vec_ = 0, n_res_ = 0, n_gtr_ = 0;
   std::vector<double> norm_ref_;    // per pair, index p * RS + r
+  std::vector<double> saved_ref_;   // forward references during the adjoint
+  std::unique_ptr<DBuf<double>[]> adj_;  // per problem: saved X (n x RS), then g (n x RS)
+  std::vector<const double*> saved_b_;
   std::vector<double> normP_, sig_ell_;  // per problem
   int rw_ = 4, cw_ = 2;
   size_t gn_smem_ = 0;

@@ -137,3 +137,47 @@ def test_batch_sixteen_rhs_matches_the_direct_solution():
         for r in range(16):
             _check_solution(x[:, r], A64, prob.b[:, r], MU, sol.pair(p, r)["ne_res"])
     sol.close()
+
+
+def test_batch_backward_matches_oracle_gradients():
+    """aplicur_batch_backward: for the loss 0.5 sum_r ||x_r - t_r||^2 of every problem,
+    dL/db, dL/dmu per pair and dL/dA (dense problems, summed over the right-hand sides)
+    against the oracle's ridge gradients at the oracle's direct solution (FP32-storage
+    gate 1e-5); CSR problems get no dL/dA."""
+    import torch
+    probs = _batch(nrhs=3, nprob=6, seed=9)
+    sol = _solver(probs)
+    xs = sol.solve(1e-10)
+    g = np.random.default_rng(12)
+    targets = [g.standard_normal((q.n, 3)) for q in probs]
+    grads = [xs[p] - torch.from_numpy(targets[p]).cuda() for p in range(len(probs))]
+    gb, gmu, gA = sol.backward(grads, tol=1e-10)
+    assert sol.stats()["converged"] == sol.stats()["pairs"]
+    gmu = gmu.cpu().numpy()
+    for p, prob in enumerate(probs):
+        A64 = _dense64(prob)
+        gA_o = np.zeros_like(A64)
+        for r in range(3):
+            xd = O.ridge_direct(A64, prob.b[:, r], MU)
+            lam, gb_o, gmu_o, gA_r = O.ridge_gradients(A64, prob.b[:, r], MU, xd,
+                                                       xd - targets[p][:, r])
+            assert rel(gb[p][:, r].cpu().numpy(), gb_o) <= 1e-5
+            assert abs(gmu[p, r] - gmu_o) <= 1e-5 * abs(gmu_o)
+            gA_o += gA_r
+        if prob.fmt == "dense":
+            assert rel(gA[p].double().cpu().numpy(), gA_o) <= 1e-5
+        else:
+            assert gA[p] is None
+    sol.close()
+
+
+def test_batch_backward_needs_a_solve():
+    import torch
+
+    import paper_2604_05065_gb300 as pkg
+    probs = _batch(nrhs=1, nprob=2, seed=5)
+    sol = _solver(probs)
+    with pytest.raises(pkg.AplicurError) as e:
+        sol.backward([torch.zeros(q.n, 1, dtype=torch.float64, device="cuda") for q in probs])
+    assert e.value.status == 1
+    sol.close()
