@@ -153,6 +153,8 @@ def test_svdfree_mu_apply_matches_oracle(name):
     Minv = np.column_stack([Pt.minv(e) for e in np.eye(Pt.ell)])
     smin = 1.0 / np.linalg.svd(Minv, compute_uv=False)[0]
     assert smin * (1 - 1e-12) <= sighat <= smin * (1 + 1e-3), (sighat, smin)
+    # the same 50 steps from the same start vector in the oracle
+    assert sighat == pytest.approx(O.svdfree_smallest_sigma(Pt, iters=50), rel=1e-10)
     w = np.random.default_rng(6).standard_normal(p.n)
     out = s.apply_preconditioner(torch.from_numpy(w).cuda()).cpu().numpy()
     assert rel(out, Pt.apply_inv(w)) <= 1e-9
