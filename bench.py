@@ -248,17 +248,25 @@ def gpu_arm(args, rank, world, local_rank):
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        # per step: the copies and the whole step (the region's own timing is f0 .. f1)
+        marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                  torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         f0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
+            marks[k][0].record(stream)
             Ae.copy_(A_host, non_blocking=True)
             be.copy_(b_host, non_blocking=True)
+            marks[k][1].record(stream)
             xh = one_solve(Ae, be)[0].to("cpu")
+            marks[k][2].record(stream)
         f1.record(stream)
         torch.cuda.synchronize()
         _, e2e_value = aggregate(f0.elapsed_time(f1), args.steps, world, dev)
         e2e = {"value": e2e_value, "unit": "solves/s",
                "h2d_bytes_per_step": int(A_host.numel() * A_host.element_size() + b_host.numel() * 8),
-               "d2h_bytes_per_step": int(p.n * 8)}
+               "d2h_bytes_per_step": int(p.n * 8),
+               "steps_ms": [round(a.elapsed_time(c), 1) for a, _, c in marks],
+               "copy_ms": [round(a.elapsed_time(b_), 2) for a, b_, _ in marks]}
         del Ae, be
 
     # ---- plain (unpreconditioned) LSQR on the same GPU, same kernels
