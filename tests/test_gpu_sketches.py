@@ -237,3 +237,23 @@ def test_tensor_core_sketch_full_size_rbf():
     print("rbf20000 sketch: " + "; ".join(line), flush=True)
     del acc
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind", list(KINDS))
+def test_dense_operator_on_the_regularized_matrix(kind):
+    """SVD-free variant with mu > 0: the dense operator has m + n columns (it sketches
+    A_mu = [A; sqrt(mu) I]); replaying the oracle's schedule gives its indices."""
+    p = PROBS["dense64"]
+    A = oracle_matrix(p)
+    cm = p.m + p.n
+    S = _operator(kind, O.sketch_rows(p.sketch_dim), cm)
+    ref = O.aplicur(A, p.b, p.mu, p.sketch_dim, O.Options(seed=SEED, variant="svdfree"),
+                    tol=1e-10, S=S)
+    s = _solver(p, kind, variant=1, replay=schedule(ref))
+    Y = s.sketch().cpu().numpy()
+    Am = O.regularized_matrix(A, math.sqrt(p.mu))
+    Yo = O.dense_sketch(Am, S)
+    assert np.all(np.abs(Y - Yo) <= 1e-12 * O.dense_sketch(abs(Am), np.abs(S)) + 1e-300)
+    s.solve(1e-10)
+    I, J = s.indices()
+    assert np.array_equal(I, ref.I) and np.array_equal(J, ref.J)
