@@ -245,12 +245,36 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   // split K when the output tiles alone cannot fill the GPU (tall inner dimension)
   const int64_t tiles = (int64_t)grid.x * grid.y;
   int64_t splits = 1;
+  const bool fp64 = dense_work().fp64_gemm;
   if (tiles < 2 * 152 && K >= 256) {
     splits = std::min<int64_t>(cdiv(4 * 152, tiles), K / 128);
     splits = std::min<int64_t>(splits, 64);
     splits = std::max<int64_t>(1, std::min<int64_t>(splits, (int64_t)(1 << 24) / (M * N)));
+  } else if (!fp64 && K >= 512) {
+    // a few waves of tiles: split K when that fills the last wave much better (the grid
+    // runs in waves of `resident` blocks; split-K costs a partial write and a reduction)
+    static const int64_t resident = [] {
+      int dev = 0, nsm = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, df32gemm_kernel, 256, 0);
+      return (int64_t)std::max(1, nsm * std::max(per, 1));
+    }();
+    auto fill = [&](int64_t sp) {
+      const int64_t b = tiles * sp;
+      return (double)b / (double)(cdiv(b, resident) * resident);
+    };
+    const double f1 = fill(1);
+    if (f1 < 0.8) {
+      int64_t best = 1;
+      double bf = f1;
+      for (int64_t sp = 2; sp <= 4 && K / sp >= 256; ++sp) {
+        const double f = fill(sp);
+        if (f > bf + 0.05) { best = sp; bf = f; }
+      }
+      if ((int64_t)(1 << 24) / (M * N) >= best) splits = best;
+    }
   }
-  const bool fp64 = dense_work().fp64_gemm;
   const int tok = prof_begin(st);
   // compensated FP32: operands split once into compact hi / lo arrays
   const float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
