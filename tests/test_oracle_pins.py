@@ -856,3 +856,18 @@ def test_ridge_sparse_matches_the_dense_solution():
     xd = O.ridge_direct(A.toarray(), p.b, p.mu)
     assert res <= 1e-14
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-9
+
+
+def test_rank_step_breakdown_ends_rank_growth():
+    """Past the exact rank (rank 9, blocks of 4) the third block's columns make C^T C
+    singular: the oracle drops that step, ends rank growth at rank 8 and still reaches the
+    ridge solution with the last preconditioner."""
+    p = wl.small_dense(200, 30, 902, rank=9, decay=2.0, mu=1e-6, sketch_dim=4)
+    s = O.sketch_rows(4)
+    rows, signs = orng.sparse_sign(5, s, p.m, O.sketch_xi(s))
+    W = orng.gaussian_w(5, p.n, 10)
+    res = O.aplicur(p.dense, p.b, p.mu, 4, tol=1e-9, srows=rows, signs=signs, W=W)
+    assert res.rank_breakdown and len(res.I) == 8 and len(res.rank_steps) == 2
+    assert res.converged
+    xd = O.ridge_direct(p.dense, p.b, p.mu)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) <= 1e-6
