@@ -1131,6 +1131,7 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
     h->stats.nphases = (int)h->phases.size();
     h->stats.ell = 0;
     h->stats.nsteps = 0;
+    h->stats.rank_breakdown = 0;
     h->solved = true;
     APL_CUDA(cudaMemcpyAsync(x_out, h->x.p, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     APL_CUDA(cudaStreamSynchronize(h->st));
