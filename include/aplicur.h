@@ -224,7 +224,10 @@ typedef struct {
   int32_t nphases;      /* LSQR phases run */
   int32_t nsteps;       /* rank steps taken */
   int32_t converged;    /* explicit relative residual <= tol */
-  double ne_res;        /* ||A^T(b - A x) - mu x|| / ||A^T b|| at exit (FP64) */
+  double ne_res;        /* ||A^T(b - A x) - mu x|| / ||A^T b|| at exit, formed with FP64
+                         * products; with FP32 values in the MIXED and DF32 forms a value
+                         * above 100 tol may come from compensated FP32 products (about 44
+                         * significant bits per sum), which decide no comparison with tol */
   double rho;           /* last norm estimate */
   double time_setup_ms; /* sketch and creation work (device time) */
   double time_solve_ms; /* aplicur_solve wall time */
@@ -304,7 +307,8 @@ aplicur_status aplicur_get_stats(aplicur_handle h, aplicur_stats* st);
  * 6 tol, 7 maxit, 9 drift: the recurrence estimate passed tol but the FP64
  * residual did not, so the phase ends and the next one restarts from an
  * exactly formed residual; 10 inner: FP32-sum inner solve reduced its residual
- * estimate by 1e-4), relative normal-equation residual at the phase end. */
+ * estimate by 1e-4), relative normal-equation residual at the phase end (evaluated as
+ * the statistic ne_res is). */
 aplicur_status aplicur_get_phase(aplicur_handle h, int32_t k, int32_t* ell, int64_t* iters,
                                  int32_t* reason, double* ne_res);
 

@@ -688,6 +688,8 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
   a.eps = h->opt.eps_lsqr;
   a.nu = nu;
   a.tol = h->replay ? 0.0 : tol;
+  // the solve starts from x = 0, so the first phase needs no product for its residual
+  a.x_zero = h->phases.empty();
   a.norm_ref = h->norm_Atb;
   a.mu = h->mu;
   a.fixed_len = fixed;
@@ -715,6 +717,7 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
     a.rhs_top = h->zm.p;
     a.rhs_bot = h->rbot.p;
     a.x = h->dx.p;
+    a.x_zero = true;
     // the Paige-Saunders tests must not end a phase short of tol
     if (a.tol > 0.0) a.eps = std::min(a.eps, a.tol / 100.0);
   }
@@ -723,7 +726,7 @@ double run_phase(aplicur_ctx* h, double nu, double tol, long long maxit, int fix
     axpy_kernel<<<(unsigned)cdiv(h->n, 256), 256, 0, h->st>>>(h->n, 1.0, h->dx.p, h->x.p);
     APL_LAUNCH_CHECK();
   }
-  const double ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
+  const double ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb, a.tol);
   h->phases.push_back(PhaseRec{h->P.ell, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
   *it = r.iters;
   *reason = r.reason;
@@ -1119,9 +1122,10 @@ aplicur_status aplicur_plain_lsqr(aplicur_handle h, double tol, int64_t maxit, d
     double ne = INFINITY;
     for (int rep = 0; rep <= h->opt.max_extra_phases && total < maxit; ++rep) {
       a.maxit = maxit - total;
+      a.x_zero = rep == 0;
       PhaseResult r = h->eng.run_phase(I, a);
       total += r.iters;
-      ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb);
+      ne = h->eng.ne_residual(h->b, nullptr, h->x.p, h->delta, h->norm_Atb, tol);
       h->phases.push_back(PhaseRec{0, r.iters, r.reason == R_CHECK ? R_TOL : r.reason, ne});
       if ((r.reason != R_DRIFT && r.reason != R_INNER) || ne <= tol) break;
     }
@@ -1173,10 +1177,11 @@ aplicur_status aplicur_backward(aplicur_handle h, const double* grad_x, double t
       ne = INFINITY;
       for (int rep = 0; rep <= h->opt.max_extra_phases && total < maxit; ++rep) {
         a.maxit = maxit - total;
+        a.x_zero = rep == 0;
         PhaseResult r = h->eng.run_phase(h->P, a);
         total += r.iters;
         const double prev = ne;
-        ne = h->eng.ne_residual(h->tmp_m.p, h->tmp_n2.p, h->lam.p, h->delta, gnorm);
+        ne = h->eng.ne_residual(h->tmp_m.p, h->tmp_n2.p, h->lam.p, h->delta, gnorm, tol);
         if (ne <= tol || r.iters == 0 || ne > 0.5 * prev) break;
       }
     }

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(NT, sizeof(TA) == 4 ? 5 : 1) k1_dense(int64_t 
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  // init == 2: z is known to be zero, so every row product is zero and A is not read
+  const int64_t np = init == 2 ? 0 : n;
   double ss = 0.0;
   for (int64_t i0 = (int64_t)K1_RPW * warp; i0 < m; i0 += (int64_t)K1_RPW * nwarps) {
     const int nr = (int)(m - i0 < K1_RPW ? m - i0 : K1_RPW);
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(NT, sizeof(TA) == 4 ? 5 : 1) k1_dense(int64_t 
     Acc<MODE> s[K1_RPW];
     int64_t jt = 0;
     if constexpr (VEC && MODE != 0 && sizeof(TA) == 4) {
-      const int64_t n4 = n >> 2;
+      const int64_t n4 = np >> 2;
       const float4* hv = reinterpret_cast<const float4*>(zh);
       const float4* lv = reinterpret_cast<const float4*>(zl);
       // one stretch of every row per pass, all loads issued first: 2 KB of A in flight per
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(NT, sizeof(TA) == 4 ? 5 : 1) k1_dense(int64_t 
       }
       jt = n4 << 2;
     }
-    for (int64_t j = jt + lane; j < n; j += 32) {
+    for (int64_t j = jt + lane; j < np; j += 32) {
       if constexpr (MODE == 0) {
         const double zj = z[j];
 #pragma unroll
@@ -239,8 +241,10 @@ __global__ void __launch_bounds__(NT) k1_csr(int64_t m, int64_t n, const int* __
     double val;
     if (i < m) {
       Acc<MODE> acc;
-      const int e1 = rowptr[i + 1];
-      for (int e = rowptr[i]; e < e1; ++e) {
+      // init == 2: z is known to be zero (no product)
+      const int e0 = rowptr[i];
+      const int e1 = init == 2 ? e0 : rowptr[i + 1];
+      for (int e = e0; e < e1; ++e) {
         const int c = colidx[e];
         if constexpr (MODE == 0) acc.add(widen(vals[e]), z[c], 0.f, 0.f);
         else acc.add((float)vals[e], 0.0, zh[c], MODE == 2 ? zl[c] : 0.f);
@@ -799,20 +803,22 @@ void LsqrEngine::launch_fused(const double* z, bool fused_v) {
 }
 
 void LsqrEngine::launch_k1(bool init, const double* z) {
-  // the residual that starts a phase is always formed with FP64 products; in the FP32
-  // modes it also writes the split of u' for the following A^T pass
+  // the residual that starts a phase is always formed with FP64 products (none when x0 is
+  // known to be zero: the residual is then the right-hand side itself); in the FP32 modes
+  // it also writes the split of u' for the following A^T pass
   float* uh = mode_ ? uh_.p : nullptr;
   float* ul = mode_ ? ul_.p : nullptr;
   const int md = init ? 0 : mode_;
+  const int ik = init ? (x0_zero_ ? 2 : 1) : 0;
   if (md == 0)
     launch_k1_mode<0>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
-                      init);
+                      ik);
   else if (md == 1)
     launch_k1_mode<1>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
-                      init);
+                      ik);
   else
     launch_k1_mode<2>(st_, A_, vec_, k1_blocks_, z, zh_.p, zl_.p, u_.p, uh, ul, ctl_.p, red_.p,
-                      init);
+                      ik);
   APL_LAUNCH_CHECK();
 }
 
@@ -935,6 +941,7 @@ void LsqrEngine::flush_x() {
 PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   PhaseResult res;
   x_ = a.x;
+  x0_zero_ = a.x_zero;
   const bool pre = P.ell > 0;
   if (pre) {
     q1_.alloc(P.ell, st_);
@@ -974,6 +981,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
   h.inner = (mode_ == 1 && a.fixed_len < 0) ? 1e-4 : 0.0;
   APL_CUDA(cudaMemcpyAsync(ctl_.p, &h, sizeof(LsqrCtl), cudaMemcpyHostToDevice, st_));
   launch_iteration(P, true);
+  x0_zero_ = false;
   APL_CUDA(cudaMemcpyAsync(&h, ctl_.p, sizeof(LsqrCtl), cudaMemcpyDeviceToHost, st_));
   APL_CUDA(cudaStreamSynchronize(st_));
   if (h.done) {
@@ -1069,7 +1077,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
       if (launches > max_launch) { res.reason = R_MAXIT; break; }
       if (mode_ == 1 && a.tol > 0.0 && a.fixed_len < 0 && h.it >= next_periodic) {
         if (h.pending == 2) { flush_x(); h.pending = 3; }
-        const double ne = ne_residual(a.rhs_top, a.rhs_bot, x_, sqrt(a.mu), a.norm_ref);
+        const double ne = ne_residual(a.rhs_top, a.rhs_bot, x_, sqrt(a.mu), a.norm_ref, a.tol);
         res.checks++;
         res.ne_res = ne;
         if (ne <= a.tol) { res.reason = R_TOL; break; }
@@ -1081,7 +1089,7 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
     }
     if (h.reason == R_CHECK) {
       if (h.pending == 2) { flush_x(); h.pending = 3; }
-      const double ne = ne_residual(a.rhs_top, a.rhs_bot, x_, sqrt(a.mu), a.norm_ref);
+      const double ne = ne_residual(a.rhs_top, a.rhs_bot, x_, sqrt(a.mu), a.norm_ref, a.tol);
       res.checks++;
       res.ne_res = ne;
       if (ne <= a.tol) { res.reason = R_TOL; break; }
@@ -1114,7 +1122,13 @@ PhaseResult LsqrEngine::run_phase(const PrecondDev& P, const PhaseArgs& a) {
 
 void LsqrEngine::matvec(int trans, const double* x, double* y, double alpha, double beta,
                         bool fp64) {
-  const int md = fp64 ? 0 : mode_;
+  matvec_md(trans, x, y, alpha, beta, fp64 ? 0 : mode_);
+}
+
+void LsqrEngine::matvec_md(int trans, const double* x, double* y, double alpha, double beta,
+                           int md) {
+  if (A_.dtype == 0) md = 0;
+  APL_REQUIRE(md == 0 || mode_ != 0, "matvec: FP32 products need the FP32 split buffers");
   const int64_t len = trans ? m_ : n_;
   if (md != 0) {
     split_kernel<<<(unsigned)cdiv(len, NT), NT, 0, st_>>>(len, x, uh_.p, ul_.p);
@@ -1202,14 +1216,29 @@ double LsqrEngine::norm2(const double* v, int64_t n) {
   return out;
 }
 
-double LsqrEngine::ne_residual(const double* rhs_top, const double* rhs_bot, const double* x,
-                               double delta, double norm_ref) {
+double LsqrEngine::ne_residual_md(const double* rhs_top, const double* rhs_bot,
+                                  const double* x, double delta, double norm_ref, int md) {
   APL_CUDA(cudaMemcpyAsync(r_.p, rhs_top, m_ * sizeof(double), cudaMemcpyDeviceToDevice, st_));
-  matvec(0, x, r_.p, -1.0, 1.0, true);
-  matvec(1, r_.p, q_.p, 1.0, 0.0, true);
+  matvec_md(0, x, r_.p, -1.0, 1.0, md);
+  matvec_md(1, r_.p, q_.p, 1.0, 0.0, md);
   ne_tail_kernel<<<(unsigned)cdiv(n_, NT), NT, 0, st_>>>(n_, q_.p, rhs_bot, x, delta);
   APL_LAUNCH_CHECK();
   return norm2(q_.p, n_) / norm_ref;
+}
+
+double LsqrEngine::ne_residual(const double* rhs_top, const double* rhs_bot, const double* x,
+                               double delta, double norm_ref, double screen_tol) {
+  // FP32 values in an FP32-product form: a first evaluation with compensated FP32 products
+  // (A read at FP32 speed, about 44 significant bits per sum instead of one FP64 FMA per
+  // element at GB300's FP64 rate) settles every residual far above tol; one within
+  // kScreen * tol of it is formed again with FP64 products, so every comparison with tol
+  // is made on the FP64 value.
+  constexpr double kScreen = 100.0;
+  if (screen_tol > 0.0 && mode_ != 0) {
+    const double est = ne_residual_md(rhs_top, rhs_bot, x, delta, norm_ref, 2);
+    if (est > kScreen * screen_tol) return est;
+  }
+  return ne_residual_md(rhs_top, rhs_bot, x, delta, norm_ref, 0);
 }
 
 void LsqrEngine::correction_rhs(const double* b, const double* x, double delta,

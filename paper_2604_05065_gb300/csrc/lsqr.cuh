@@ -91,6 +91,7 @@ struct PhaseArgs {
   int fixed_len = -1;
   long long maxit = 1000000;
   int check_gap = 10;
+  bool x_zero = false;  // x0 is zero: the phase-start residual is the right-hand side
 };
 
 struct PhaseResult {
@@ -111,9 +112,11 @@ class LsqrEngine {
   void set_profile(bool on) { profile_ = on; }
   KernelProfile prof;
   PhaseResult run_phase(const PrecondDev& P, const PhaseArgs& a);
-  // ||A_delta^T (rhs - A_delta x)|| / norm_ref in FP64 (rhs_bot NULL = 0).
+  // ||A_delta^T (rhs - A_delta x)|| / norm_ref in FP64 (rhs_bot NULL = 0).  With
+  // screen_tol > 0 and FP32 values in an FP32-product form, a value above 100 screen_tol
+  // may come from compensated FP32 products; every value at or below it is FP64.
   double ne_residual(const double* rhs_top, const double* rhs_bot, const double* x, double delta,
-                     double norm_ref);
+                     double norm_ref, double screen_tol = 0.0);
   // y = alpha A x + beta y (trans 0) or y = A^T x (trans 1), FP64 or mixed products.
   void matvec(int trans, const double* x, double* y, double alpha, double beta, bool fp64);
   double norm2(const double* v, int64_t n);
@@ -133,6 +136,9 @@ class LsqrEngine {
   void launch_pre(const PrecondDev& P, const double* w, double* o1, double* o2, bool in_phase,
                   bool init);
   void flush_x();
+  void matvec_md(int trans, const double* x, double* y, double alpha, double beta, int md);
+  double ne_residual_md(const double* rhs_top, const double* rhs_bot, const double* x,
+                        double delta, double norm_ref, int md);
 
   cudaStream_t st_ = nullptr;
   MatView A_;
@@ -148,6 +154,7 @@ class LsqrEngine {
   FusedPlan fused_;
   DBuf<int> ferr_;  // set by the fused pass when a bounded wait gave up
   double* x_ = nullptr;
+  bool x0_zero_ = false;  // the phase being started has x0 = 0
   bool profile_ = false;
   std::vector<cudaEvent_t> ev_;
   int kernels_per_iter_ = 0;
