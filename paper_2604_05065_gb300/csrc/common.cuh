@@ -156,6 +156,7 @@ struct DenseWork {
   DBuf<double> splitk, qrtmp, jw64, jtmp, jw2;
   DBuf<float> jb32, jw32;
   DBuf<float> gah, gal, gbh, gbl;  // hi / lo operands of the compensated GEMM
+  DBuf<float> tth, ttl;            // hi / lo of the triangle of a compensated solve
   bool fp64_gemm = false;  // GEMMs on the FP64 units instead of compensated FP32
 };
 DenseWork& dense_work();  // the workspace installed on the calling thread (throws if none)

@@ -167,20 +167,24 @@ __device__ __forceinline__ void df_mul(float& xh, float& xl, float rh, float rl)
   df_two_sum(p, lo, xh, xl);
 }
 
+// The FP32 hi / lo parts of T come split once per triangular solve (Thg, Tlg, element
+// (r, c) at r * trs2 + c * tcs2): every block of the grid would otherwise repeat the FP64
+// split of the whole diagonal block, at GB300's FP64 rate.
 __global__ void __launch_bounds__(256) trsv_block_df_kernel(int64_t nvec, int len,
                                                             double* __restrict__ X,
                                                             int64_t vstride, int64_t estride,
                                                             const double* __restrict__ Tm,
                                                             int64_t trs, int64_t tcs, int lower,
-                                                            int unit) {
+                                                            int unit,
+                                                            const float* __restrict__ Thg,
+                                                            const float* __restrict__ Tlg,
+                                                            int64_t trs2, int64_t tcs2) {
   __shared__ float Th[TNB][TNB + 1], Tl[TNB][TNB + 1];
   __shared__ float Rh[TNB], Rl[TNB];
   for (int e = threadIdx.x; e < len * len; e += blockDim.x) {
     const int r = e % len, c = e / len;
-    const double v = Tm[r * trs + c * tcs];
-    const float h = __double2float_rn(v);
-    Th[r][c] = h;
-    Tl[r][c] = __double2float_rn(v - (double)h);
+    Th[r][c] = Thg[r * trs2 + c * tcs2];
+    Tl[r][c] = Tlg[r * trs2 + c * tcs2];
   }
   if (threadIdx.x < len) {
     const double rv = unit ? 1.0 : 1.0 / Tm[threadIdx.x * trs + threadIdx.x * tcs];
@@ -230,27 +234,43 @@ void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t
   const bool effLower = (uplo == 'L') != trans;  // shape of op(A)
   const int64_t dim = left ? M : N;
   const int64_t nblk = cdiv(dim, TNB);
+  const bool fp64 = dense_work().fp64_gemm;
+  // compensated form: the dim x dim triangle split once into compact FP32 hi / lo arrays
+  const float *Th = nullptr, *Tl = nullptr;
+  if (!fp64) {
+    DenseWork& wk = dense_work();
+    wk.tth.alloc((size_t)dim * dim, st);
+    wk.ttl.alloc((size_t)dim * dim, st);
+    split_hilo(st, dim, dim, A, lda, wk.tth.p, wk.ttl.p);
+    Th = wk.tth.p;
+    Tl = wk.ttl.p;
+  }
   auto diag = [&](int64_t k0, int64_t kb) {
-    // element (r, c) of op(A)_kk
+    // element (r, c) of op(A)_kk; the same element of the compact split at r rs2 + c cs2
     const double* base = A + k0 + k0 * lda;
-    int64_t rs = trans ? lda : 1, cs = trans ? 1 : lda;
+    const int64_t rs = trans ? lda : 1, cs = trans ? 1 : lda;
+    const int64_t rs2 = trans ? dim : 1, cs2 = trans ? 1 : dim;
+    const float* bh = fp64 ? nullptr : Th + k0 + k0 * dim;
+    const float* bl = fp64 ? nullptr : Tl + k0 + k0 * dim;
     if (left) {
       const int64_t nvec = N;
-      if (dense_work().fp64_gemm)
+      if (fp64)
         trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
             nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
       else
         trsv_block_df_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
-            nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0);
+            nvec, (int)kb, B + k0, ldb, 1, base, rs, cs, effLower ? 1 : 0, unit ? 1 : 0, bh,
+            bl, rs2, cs2);
     } else {
       // X T = B  <=>  T^T x^T = b^T : matrix element (r, c) of T^T = T(c, r)
       const int64_t nvec = M;
-      if (dense_work().fp64_gemm)
+      if (fp64)
         trsv_block_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
             nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
       else
         trsv_block_df_kernel<<<(unsigned)cdiv(nvec * 32, 256), 256, 0, st>>>(
-            nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0);
+            nvec, (int)kb, B + k0 * ldb, 1, ldb, base, cs, rs, effLower ? 0 : 1, unit ? 1 : 0,
+            bh, bl, cs2, rs2);
     }
     APL_LAUNCH_CHECK();
   };

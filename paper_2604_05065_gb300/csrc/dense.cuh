@@ -10,6 +10,11 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
            double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
            double beta, double* C, int64_t ldc);
 
+// hi[r + c rows] = fl32(A(r, c)), lo = fl32(A(r, c) - hi): the compensated-FP32 operand
+// split of a rows x cols block of A (leading dimension ld) into compact arrays.
+void split_hilo(cudaStream_t st, int64_t rows, int64_t cols, const double* A, int64_t ld,
+                float* hi, float* lo);
+
 // Solve op(A) X = B (left) or X op(A) = B (right) in place of B (M x N).
 // uplo: 'L' or 'U' as stored; unit: unit diagonal assumed.
 void dtrsm(cudaStream_t st, bool left, char uplo, bool trans, bool unit, int64_t M, int64_t N,

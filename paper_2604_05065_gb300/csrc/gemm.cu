@@ -87,12 +87,13 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int transA, int transB, int6
 }
 
 // The same tiling with compensated FP32 arithmetic.  Every FP64 operand is split once per
-// call into FP32 hi + lo arrays (split_kernel; hi + lo keeps 48 of its 53 bits), a product
-// is formed exactly in its hi * hi part (an FMA gives the rounding error) plus the two
-// cross terms, and the running sum is an unevaluated FP32 pair updated by Knuth's TwoSum.
-// The result is accurate to about 2^-46 relative to sum |a_i b_i| and the inner loop has
-// only FP32 instructions, which GB300 issues at 64 times its FP64 rate.  The operands
-// arrive compact: op(A) source rows x cols with leading dimension = rows (same for B).
+// call into FP32 hi + lo arrays (split2_kernel, both operands in one launch; hi + lo keeps
+// 48 of its 53 bits), a product is formed exactly in its hi * hi part (an FMA gives the
+// rounding error) plus the two cross terms, and the running sum is an unevaluated FP32 pair
+// updated by Knuth's TwoSum.  The result is accurate to about 2^-46 relative to
+// sum |a_i b_i| and the inner loop has only FP32 instructions, which GB300 issues at over
+// 64 times its FP64 rate.  The operands arrive compact: op(A) source rows x cols with
+// leading dimension = rows (same for B).
 __global__ void split_kernel(int64_t rows, int64_t cols, const double* __restrict__ src,
                              int64_t ld, float* __restrict__ hi, float* __restrict__ lo) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,6 +105,38 @@ __global__ void split_kernel(int64_t rows, int64_t cols, const double* __restric
   lo[e] = __double2float_rn(v - (double)h);
 }
 
+// Both operands of one product in one launch: elements below ar * ac are op(A)'s source
+// block, the rest B's (the same split as split_kernel).
+__global__ void split2_kernel(int64_t ar, int64_t ac, const double* __restrict__ A,
+                              int64_t lda, float* __restrict__ ah, float* __restrict__ al,
+                              int64_t br, int64_t bc, const double* __restrict__ B,
+                              int64_t ldb, float* __restrict__ bh, float* __restrict__ bl) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t na = ar * ac;
+  double v;
+  float *hi, *lo;
+  if (e < na) {
+    v = A[e % ar + (e / ar) * lda];
+    hi = ah;
+    lo = al;
+  } else {
+    e -= na;
+    if (e >= br * bc) return;
+    v = B[e % br + (e / br) * ldb];
+    hi = bh;
+    lo = bl;
+  }
+  const float h = __double2float_rn(v);
+  hi[e] = h;
+  lo[e] = __double2float_rn(v - (double)h);
+}
+
+// R x R outputs per thread on a 16 x 16 thread grid: a (16 R) x (16 R) output tile.  R = 4
+// (64 x 64 tiles) is the default; R = 2 (32 x 32) serves launches whose 64 x 64 tiles would
+// not fill one wave of the GPU (the small updates of the blocked triangular solve and
+// Cholesky), with four times as many blocks.  Each output's sum runs over k in the same
+// order in both, so the two give bitwise the same result.
+template <int R>
 __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, int64_t M,
                                                        int64_t N, int64_t K, double alpha,
                                                        const float* __restrict__ Ahi,
@@ -115,26 +148,29 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
                                                        double* __restrict__ C, int64_t ldc,
                                                        int64_t kchunk,
                                                        double* __restrict__ part) {
-  __shared__ float Ah[GBK][GBM + 1], Al[GBK][GBM + 1];
-  __shared__ float Bh[GBK][GBN + 1], Bl[GBK][GBN + 1];
+  constexpr int TM = 16 * R;                     // tile rows = tile columns
+  constexpr int LG = R == 4 ? 6 : (R == 2 ? 5 : 4);  // log2(TM)
+  static_assert(TM == (1 << LG), "tile size");
+  __shared__ float Ah[GBK][TM + 1], Al[GBK][TM + 1];
+  __shared__ float Bh[GBK][TM + 1], Bl[GBK][TM + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
-  float s[4][4], c[4][4];
+  const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TM;
+  float s[R][R], c[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
+    for (int j = 0; j < R; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
 
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
   // the next K chunk is fetched into registers while the current one is multiplied
-  float pah[4], pal[4], pbh[4], pbl[4];
+  float pah[R], pal[R], pbh[R], pbl[R];
   auto fetch = [&](int64_t k0) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < R; ++e) {
       const int lin = threadIdx.x + e * 256;
       int mm, kk;
-      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
+      if (!transA) { mm = lin & (TM - 1); kk = lin >> LG; } else { kk = lin & 15; mm = lin >> 4; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
       pah[e] = 0.f;
       pal[e] = 0.f;
@@ -144,7 +180,7 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
         pal[e] = Alo[o];
       }
       int nn;
-      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
+      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & (TM - 1); kk = lin >> LG; }
       const int64_t gn = n0 + nn, gk2 = k0 + kk;
       pbh[e] = 0.f;
       pbl[e] = 0.f;
@@ -158,14 +194,14 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
   if (kbeg < kend) fetch(kbeg);
   for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < R; ++e) {
       const int lin = threadIdx.x + e * 256;
       int mm, kk;
-      if (!transA) { mm = lin & 63; kk = lin >> 6; } else { kk = lin & 15; mm = lin >> 4; }
+      if (!transA) { mm = lin & (TM - 1); kk = lin >> LG; } else { kk = lin & 15; mm = lin >> 4; }
       Ah[kk][mm] = pah[e];
       Al[kk][mm] = pal[e];
       int nn;
-      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & 63; kk = lin >> 6; }
+      if (!transB) { kk = lin & 15; nn = lin >> 4; } else { nn = lin & (TM - 1); kk = lin >> LG; }
       Bh[kk][nn] = pbh[e];
       Bl[kk][nn] = pbl[e];
     }
@@ -173,15 +209,15 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
     if (k0 + GBK < kend) fetch(k0 + GBK);
 #pragma unroll 4
     for (int kk = 0; kk < GBK; ++kk) {
-      float ah[4], al[4], bh[4], bl[4];
+      float ah[R], al[R], bh[R], bl[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { ah[i] = Ah[kk][ty + 16 * i]; al[i] = Al[kk][ty + 16 * i]; }
+      for (int i = 0; i < R; ++i) { ah[i] = Ah[kk][ty + 16 * i]; al[i] = Al[kk][ty + 16 * i]; }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { bh[j] = Bh[kk][tx + 16 * j]; bl[j] = Bl[kk][tx + 16 * j]; }
+      for (int j = 0; j < R; ++j) { bh[j] = Bh[kk][tx + 16 * j]; bl[j] = Bl[kk][tx + 16 * j]; }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
           const float p = __fmul_rn(ah[i], bh[j]);
           float x = __fmaf_rn(ah[i], bh[j], -p);
           x = __fmaf_rn(ah[i], bl[j], x);
@@ -196,11 +232,11 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int64_t gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       const double acc = (double)s[i][j] + (double)c[i][j];
@@ -212,6 +248,17 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
       }
     }
   }
+}
+
+// SMs of the device current at the first call (a launch-shape heuristic only).
+int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+  }();
+  return n;
 }
 
 // C = alpha * sum_z part[z] + beta * C, summing the splits in a fixed order.
@@ -227,6 +274,13 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const dou
 }
 
 }  // namespace
+
+void split_hilo(cudaStream_t st, int64_t rows, int64_t cols, const double* A, int64_t ld,
+                float* hi, float* lo) {
+  if (rows <= 0 || cols <= 0) return;
+  split_kernel<<<(unsigned)cdiv(rows * cols, 256), 256, 0, st>>>(rows, cols, A, ld, hi, lo);
+  APL_LAUNCH_CHECK();
+}
 
 void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_t K,
            double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
@@ -254,11 +308,9 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
     // a few waves of tiles: split K when that fills the last wave much better (the grid
     // runs in waves of `resident` blocks; split-K costs a partial write and a reduction)
     static const int64_t resident = [] {
-      int dev = 0, nsm = 0, per = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, df32gemm_kernel, 256, 0);
-      return (int64_t)std::max(1, nsm * std::max(per, 1));
+      int per = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, df32gemm_kernel<4>, 256, 0);
+      return (int64_t)std::max(1, sm_count() * std::max(per, 1));
     }();
     auto fill = [&](int64_t sp) {
       const int64_t b = tiles * sp;
@@ -287,9 +339,8 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
     wk.gal.alloc((size_t)ar * ac, st);
     wk.gbh.alloc((size_t)br * bc, st);
     wk.gbl.alloc((size_t)br * bc, st);
-    split_kernel<<<(unsigned)cdiv(ar * ac, 256), 256, 0, st>>>(ar, ac, A, lda, wk.gah.p, wk.gal.p);
-    APL_LAUNCH_CHECK();
-    split_kernel<<<(unsigned)cdiv(br * bc, 256), 256, 0, st>>>(br, bc, B, ldb, wk.gbh.p, wk.gbl.p);
+    split2_kernel<<<(unsigned)cdiv(ar * ac + br * bc, 256), 256, 0, st>>>(
+        ar, ac, A, lda, wk.gah.p, wk.gal.p, br, bc, B, ldb, wk.gbh.p, wk.gbl.p);
     APL_LAUNCH_CHECK();
     Ah = wk.gah.p; Al = wk.gal.p; Bh = wk.gbh.p; Bl = wk.gbl.p;
     lda2 = ar;
@@ -304,8 +355,9 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
       dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, A, lda, B, ldb, 0.0, C,
                                          ldc, kchunk, dense_work().splitk.p);
     else
-      df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, Ah, Al, lda2, Bh, Bl,
-                                            ldb2, 0.0, C, ldc, kchunk, dense_work().splitk.p);
+      df32gemm_kernel<4><<<grid, 256, 0, st>>>(transA, transB, M, N, K, 1.0, Ah, Al, lda2, Bh,
+                                               Bl, ldb2, 0.0, C, ldc, kchunk,
+                                               dense_work().splitk.p);
     APL_LAUNCH_CHECK();
     splitk_reduce_kernel<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, (int)splits,
                                                                      dense_work().splitk.p, alpha, beta, C,
@@ -313,9 +365,14 @@ void dgemm(cudaStream_t st, int transA, int transB, int64_t M, int64_t N, int64_
   } else if (fp64) {
     dgemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C,
                                        ldc, K, nullptr);
+  } else if (tiles < sm_count()) {
+    // less than one wave of 64 x 64 tiles: 32 x 32 tiles, four times the blocks
+    const dim3 g2((unsigned)cdiv(M, 32), (unsigned)cdiv(N, 32));
+    df32gemm_kernel<2><<<g2, 256, 0, st>>>(transA, transB, M, N, K, alpha, Ah, Al, lda2, Bh, Bl,
+                                           ldb2, beta, C, ldc, K, nullptr);
   } else {
-    df32gemm_kernel<<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, Ah, Al, lda2, Bh, Bl,
-                                          ldb2, beta, C, ldc, K, nullptr);
+    df32gemm_kernel<4><<<grid, 256, 0, st>>>(transA, transB, M, N, K, alpha, Ah, Al, lda2, Bh,
+                                             Bl, ldb2, beta, C, ldc, K, nullptr);
   }
   APL_LAUNCH_CHECK();
   prof_end(st, tok, PROF_GEMM, 2.0 * (double)M * (double)N * (double)K);
