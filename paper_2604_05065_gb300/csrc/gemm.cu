@@ -131,7 +131,26 @@ __global__ void split2_kernel(int64_t ar, int64_t ac, const double* __restrict__
   lo[e] = __double2float_rn(v - (double)h);
 }
 
-// R x R outputs per thread on a 16 x 16 thread grid: a (16 R) x (16 R) output tile.  R = 4
+// R consecutive floats of a hi row and of a lo row of a shared tile (one 16-byte load each
+// for R = 4, one 8-byte load for R = 2).
+template <int R>
+__device__ __forceinline__ void load_row(const float* h, const float* l, float* oh, float* ol) {
+  if constexpr (R == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(h);
+    const float4 b = *reinterpret_cast<const float4*>(l);
+    oh[0] = a.x; oh[1] = a.y; oh[2] = a.z; oh[3] = a.w;
+    ol[0] = b.x; ol[1] = b.y; ol[2] = b.z; ol[3] = b.w;
+  } else {
+    static_assert(R == 2, "R is 2 or 4");
+    const float2 a = *reinterpret_cast<const float2*>(h);
+    const float2 b = *reinterpret_cast<const float2*>(l);
+    oh[0] = a.x; oh[1] = a.y;
+    ol[0] = b.x; ol[1] = b.y;
+  }
+}
+
+// R x R outputs per thread on a 16 x 16 thread grid: a (16 R) x (16 R) output tile, thread
+// (tx, ty) owning rows ty R ... ty R + R - 1 and columns tx R ... tx R + R - 1.  R = 4
 // (64 x 64 tiles) is the default; R = 2 (32 x 32) serves launches whose 64 x 64 tiles would
 // not fill one wave of the GPU (the small updates of the blocked triangular solve and
 // Cholesky), with four times as many blocks.  Each output's sum runs over k in the same
@@ -151,8 +170,13 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
   constexpr int TM = 16 * R;                     // tile rows = tile columns
   constexpr int LG = R == 4 ? 6 : (R == 2 ? 5 : 4);  // log2(TM)
   static_assert(TM == (1 << LG), "tile size");
-  __shared__ float Ah[GBK][TM + 1], Al[GBK][TM + 1];
-  __shared__ float Bh[GBK][TM + 1], Bl[GBK][TM + 1];
+  // rows padded by 4 floats: each thread reads its R consecutive entries of a row with one
+  // 16-byte (R = 4) or 8-byte (R = 2) load
+  constexpr int TP = TM + 4;
+  __shared__ __align__(16) float Ah[GBK][TP];
+  __shared__ __align__(16) float Al[GBK][TP];
+  __shared__ __align__(16) float Bh[GBK][TP];
+  __shared__ __align__(16) float Bl[GBK][TP];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TM;
   float s[R][R], c[R][R];
@@ -210,10 +234,8 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
 #pragma unroll 4
     for (int kk = 0; kk < GBK; ++kk) {
       float ah[R], al[R], bh[R], bl[R];
-#pragma unroll
-      for (int i = 0; i < R; ++i) { ah[i] = Ah[kk][ty + 16 * i]; al[i] = Al[kk][ty + 16 * i]; }
-#pragma unroll
-      for (int j = 0; j < R; ++j) { bh[j] = Bh[kk][tx + 16 * j]; bl[j] = Bl[kk][tx + 16 * j]; }
+      load_row<R>(&Ah[kk][ty * R], &Al[kk][ty * R], ah, al);
+      load_row<R>(&Bh[kk][tx * R], &Bl[kk][tx * R], bh, bl);
 #pragma unroll
       for (int i = 0; i < R; ++i)
 #pragma unroll
@@ -233,11 +255,11 @@ __global__ void __launch_bounds__(256) df32gemm_kernel(int transA, int transB, i
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int64_t gm = m0 + ty + 16 * i;
+    const int64_t gm = m0 + ty * R + i;
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const int64_t gn = n0 + tx + 16 * j;
+      const int64_t gn = n0 + tx * R + j;
       if (gn >= N) continue;
       const double acc = (double)s[i][j] + (double)c[i][j];
       if (part) {
