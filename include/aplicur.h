@@ -54,7 +54,8 @@ enum { APLICUR_F64 = 0, APLICUR_F32 = 1 };
  *        starts from g = A^T (b - A x) - mu x formed with FP64 products, solves
  *        [A; delta I] dx ~ [0; g / delta] (the normal equations of the paper's warm
  *        start) and adds dx to x in FP64; it ends once its estimate of ||Abar^T rbar||
- *        fell by 1e-4, or when an FP64 check shows the residual no longer falling.
+ *        fell by 1e-4, or when an explicit residual check (formed as the statistic
+ *        ne_res is) shows the residual no longer falling.
  *        The stopping tests use the paper's residual estimate.  (mu = 0: the phase
  *        starts from the FP64 residual [b - A x; 0] instead.)
  *  DF32  compensated FP32: operand vectors split into FP32 hi + lo parts, exact
